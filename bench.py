@@ -1,0 +1,439 @@
+#!/usr/bin/env python
+"""Benchmark of the VSA-OGM hot path on one GB300 (or N, one map per GPU).
+
+One step = the whole hot path over the paper-scale synthetic workload: reset
+the 32 tile memories, encode + bundle the 100-scan trajectory (2.27M labelled
+points, D = 8192, 4 x 4 tiles), decode all 400 x 400 cells for both classes,
+and run the entropy / softmax / signed-difference pass.  Inputs are resident
+in HBM before timing starts; L2 is flushed (a 256 MB write) between timed
+steps, outside the step's own events.
+
+Prints one JSON line.  `value` is points bundled per second over whole steps
+(all ranks); cells decoded per second and p50/p99 step latency sit beside it.
+`--impl reference` times the FP64 CPU oracle on bounded samples of the same
+workload instead (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+# GB300 figures used for the rooflines (see the design doc for their derivation).
+SMS = 152
+SM_MAX_MHZ = 2070.0
+MUFU_PER_SM_CLK = 16          # sin/cos ops per SM per clock (measured 15.2 at max clock)
+FP32_FMA_PER_SM_CLK = 128
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+CLOCK_FIELDS = ("index,pci.bus_id,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+
+def parse_args():
+    p = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=100)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--no-cpu-baseline", action="store_true",
+                   help="skip the oracle timing (for quick runs)")
+    return p.parse_args()
+
+
+def measured_peaks() -> dict:
+    try:
+        with open(PEAKS_FILE) as f:
+            d = json.load(f)
+        return {"hbm_gbs": float(d["hbm_gbs"]), "bf16_tflops": float(d["bf16_tflops"]),
+                "source": "measured"}
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "source": "fallback"}
+
+
+class Dist:
+    """Rank bookkeeping; a process group only when launched with WORLD_SIZE > 1."""
+
+    def __init__(self, backend: str | None):
+        self.world = int(os.environ.get("WORLD_SIZE", "1"))
+        self.rank = int(os.environ.get("RANK", "0"))
+        self.local = int(os.environ.get("LOCAL_RANK", "0"))
+        self.pg = False
+        if self.world > 1 and backend:
+            import torch.distributed as dist
+            dist.init_process_group(backend=backend)
+            self.pg = True
+
+    def barrier(self):
+        if self.pg:
+            import torch.distributed as dist
+            dist.barrier()
+
+    def max(self, v: float) -> float:
+        if not self.pg:
+            return v
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([v], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def sum(self, v: float) -> float:
+        if not self.pg:
+            return v
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([v], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+        return float(t.item())
+
+    def close(self):
+        if self.pg:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples every 200 ms while running."""
+
+    def __init__(self, bus_id: str | None):
+        self.bus_id = (bus_id or "").lower()
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={CLOCK_FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-f", self.path], stdout=subprocess.DEVNULL,
+                stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 10:
+                    continue
+                if self.bus_id and self.bus_id not in parts[1].lower() and \
+                        parts[1].lower() not in self.bus_id:
+                    continue
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        mx = [float(r[3]) for r in rows if r[3].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[6 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows),
+                "power_w_max": max(float(r[4]) for r in rows
+                                   if r[4].replace(".", "").isdigit()) if rows else None}
+
+
+def percentile(xs, q):
+    s = sorted(xs)
+    if not s:
+        return None
+    i = min(len(s) - 1, max(0, int(round(q / 100.0 * (len(s) - 1)))))
+    return s[i]
+
+
+# --------------------------------------------------------------------------- oracle (CPU)
+def _oracle_setup(wl):
+    import numpy as np
+
+    import oracle
+    f32 = lambda v: float(np.float32(v))
+    g = oracle.Grid(W=wl.W, H=wl.H, res=f32(wl.res), x_min=f32(wl.x_min), y_min=f32(wl.y_min),
+                    tiles_x=wl.tiles_x, tiles_y=wl.tiles_y)
+    nx, ny = oracle.draw_nu(wl.seed, wl.D, f32(wl.length_scale))
+    return oracle, g, nx, ny
+
+
+def oracle_step_time(wl, n_pts: int, n_cells: int, rng, r_occ=3, r_emp=3):
+    """Times the oracle on a bounded sample of one step: encode + bundle n_pts
+    random points with all D frequencies, decode n_cells random cells, and the
+    entropy / softmax pass over the full grid; extrapolates to the whole step
+    (cost is linear in points and in cells).  Returns (seconds, parts)."""
+    import numpy as np
+    oracle, g, nx, ny = _oracle_setup(wl)
+    idx = rng.choice(wl.n, n_pts, replace=False)
+    t0 = time.perf_counter()
+    om = oracle.memories(g, nx, ny, wl.xy[idx], wl.labels[idx], "tile")
+    t_enc = time.perf_counter() - t0
+    cells = np.stack([rng.integers(0, wl.W, n_cells), rng.integers(0, wl.H, n_cells)], 1)
+    t0 = time.perf_counter()
+    oracle.decode_cells(g, nx, ny, om, cells.astype(np.int32), "tile")
+    t_dec = time.perf_counter() - t0
+    Ph = rng.uniform(0.0, 1.0, (2, wl.H, wl.W))
+    t0 = time.perf_counter()
+    H0 = oracle.entropy(Ph[0], r_emp)
+    H1 = oracle.entropy(Ph[1], r_occ)
+    oracle.softmax_psd(H0, H1)
+    t_ent = time.perf_counter() - t0
+    total = t_enc * wl.n / n_pts + t_dec * (wl.W * wl.H) / n_cells + t_ent
+    return total, {"encode_s": t_enc, "decode_s": t_dec, "entropy_s": t_ent}
+
+
+def calibrate_oracle(wl, budget_s: float, rng):
+    """Sample sizes whose oracle time is about budget_s (half encode, half decode):
+    two bounded probes, then a linear estimate (cost is linear in both)."""
+    n_pts, n_cells = 2048, 512
+    for _ in range(2):
+        _, parts = oracle_step_time(wl, n_pts, n_cells, rng)
+        per_pt = max(parts["encode_s"], 1e-4) / n_pts
+        per_cell = max(parts["decode_s"], 1e-4) / n_cells
+        n_pts = int(min(wl.n, max(256, 0.5 * budget_s / per_pt)))
+        n_cells = int(min(wl.W * wl.H, max(64, 0.5 * budget_s / per_cell)))
+        if parts["encode_s"] > 0.05 * budget_s and parts["decode_s"] > 0.05 * budget_s:
+            break
+        n_pts, n_cells = min(n_pts, 8 * 2048), min(n_cells, 8 * 512)
+    return n_pts, n_cells
+
+
+def cpu_baseline(wl, budget_s: float = 12.0) -> dict:
+    import numpy as np
+
+    import oracle
+    rng = np.random.default_rng(7)
+    n_pts, n_cells = calibrate_oracle(wl, budget_s, rng)
+    t_step, parts = oracle_step_time(wl, n_pts, n_cells, rng)
+    return {"value": wl.n / t_step, "unit": "points/s", "cores": oracle.num_threads(),
+            "kind": "oracle",
+            "sample": (f"FP64 oracle (memory-vector form) on {n_pts} random points x all "
+                       f"{wl.D} frequencies and {n_cells} random cells, plus the full-grid "
+                       f"entropy pass; extrapolated linearly to {wl.n} points and "
+                       f"{wl.W * wl.H} cells per step"),
+            "step_s_extrapolated": t_step, "sample_parts_s": parts}
+
+
+def run_reference(args):
+    """The FP64 CPU oracle on the same workload, bounded samples per step."""
+    import numpy as np
+
+    import oracle
+    from paper_2408_09066_gb300 import synth
+    if int(os.environ.get("RANK", "0")) != 0:
+        return 0
+    oracle.build()
+    wl = synth.paper_trajectory()
+    rng = np.random.default_rng(11)
+    n_pts, n_cells = calibrate_oracle(wl, 2.0, rng)
+    for _ in range(args.warmup):
+        oracle_step_time(wl, n_pts, n_cells, rng)
+    steps = [oracle_step_time(wl, n_pts, n_cells, rng)[0] for _ in range(args.steps)]
+    mean_s = sum(steps) / len(steps)
+    value = wl.n / mean_s
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "points/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": mean_s * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": DATA,
+        "config": workload_config(wl, "fp64 oracle"),
+        "cells_per_s": wl.W * wl.H / mean_s,
+        "p50_ms": percentile(steps, 50) * 1e3, "p99_ms": percentile(steps, 99) * 1e3,
+        "e2e": {"value": value, "unit": "points/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+        "cpu_baseline": {"value": value, "unit": "points/s", "cores": oracle.num_threads(),
+                         "kind": "oracle",
+                         "sample": (f"each step: {n_pts} random points x {wl.D} frequencies, "
+                                    f"{n_cells} random cells, full-grid entropy; extrapolated "
+                                    f"to {wl.n} points and {wl.W * wl.H} cells")},
+        "gpu_launches": 0,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# --------------------------------------------------------------------------- GPU (ours)
+METRIC = "points bundled/s + grid cells decoded/s at D=8192 vs FP32 plain; p50/p99 ms"
+DATA = ("synthetic: seeded 100-scan lidar trajectory in a walled 40 m world with 40 "
+        "obstacles (1080 beams, 30 m range, sigma 0.03 m, 20 empty samples per beam)")
+
+# DRAM traffic of one encode launch on this workload from an ncu capture, valid
+# only for the kernel source it was taken on (sha1 of csrc/encode.cu).
+ENCODE_TRAFFIC = {"sha1": None, "bytes": None}
+
+
+def workload_config(wl, decode: str) -> dict:
+    return {"workload": f"paper-scale map {wl.W}x{wl.H} cells at {wl.res} m, "
+                        f"{wl.tiles_x}x{wl.tiles_y} tiles, D={wl.D}, {wl.n} points",
+            "grid": [wl.W, wl.H], "tiles": [wl.tiles_x, wl.tiles_y], "D": wl.D,
+            "points_per_step": wl.n, "cells_per_step": wl.W * wl.H, "decode": decode,
+            "l2": "flushed between timed steps (256 MB device write outside the step events)",
+            "parallelism": "one independent map per GPU"}
+
+
+def _sha1(path):
+    with open(path, "rb") as f:
+        return hashlib.sha1(f.read()).hexdigest()
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    from paper_2408_09066_gb300 import build, synth
+    from paper_2408_09066_gb300 import vsaogm as V
+    d = Dist("nccl" if int(os.environ.get("WORLD_SIZE", "1")) > 1 else None)
+    torch.cuda.set_device(d.local)
+    if d.local == 0:
+        build.build()
+    d.barrier()
+    dev = torch.device("cuda", d.local)
+    wl = synth.paper_trajectory(seed=1002 + d.rank)
+    cfg = V.default_config(D=wl.D, grid_w=wl.W, grid_h=wl.H, resolution=wl.res, x_min=wl.x_min,
+                           y_min=wl.y_min, tiles_x=wl.tiles_x, tiles_y=wl.tiles_y,
+                           length_scale=wl.length_scale, seed=wl.seed)
+    m = V.Map(cfg)
+    xy = torch.from_numpy(wl.xy).to(dev)
+    lab = torch.from_numpy(wl.labels).to(dev)
+    heat = torch.empty((2, wl.H, wl.W), dtype=torch.float32, device=dev)
+    occ = torch.empty((wl.H, wl.W), dtype=torch.float32, device=dev)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > L2
+    stream = torch.cuda.current_stream()
+
+    def step():
+        m.reset()
+        m.encode_bundle(xy, lab)
+        m.query(heat, occ)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    m.set_timing(True)
+    m.stage_times(reset=True)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    bus = None
+    try:
+        bus = torch.cuda.get_device_properties(dev).pci_bus_id
+    except Exception:
+        pass
+    clocks = ClockSampler(bus)
+    d.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    t_wall = time.perf_counter()
+    for i in range(args.steps):
+        flush.fill_(float(i))
+        ev[i][0].record(stream)
+        step()
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    d.barrier()
+    t_wall = time.perf_counter() - t_wall
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    stages = m.stage_times(reset=True)
+    m.set_timing(False)
+    total_s = d.max(sum(step_ms) / 1e3)
+    points_all = d.sum(float(wl.n * args.steps))
+    value = points_all / total_s
+    ms_per_step = total_s / args.steps * 1e3
+
+    # end to end through the host entry point: pinned inputs in, occupancy out
+    xy_h = torch.from_numpy(wl.xy).pin_memory()
+    lab_h = torch.from_numpy(wl.labels).pin_memory()
+    occ_h = torch.empty((wl.H, wl.W), dtype=torch.float32).pin_memory()
+    xy_n, lab_n, occ_n = xy_h.numpy(), lab_h.numpy(), occ_h.numpy()
+    for _ in range(max(1, args.warmup)):
+        m.reset()
+        m.update_query_host(xy_n, lab_n, occ_n)
+    e2e_s = []
+    d.barrier()
+    for i in range(args.steps):
+        flush.fill_(float(i))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        m.reset()
+        m.update_query_host(xy_n, lab_n, occ_n)
+        e2e_s.append(time.perf_counter() - t0)
+    e2e_total = d.max(sum(e2e_s))
+    e2e_value = points_all / e2e_total
+
+    # roofline of the dominant kernel (encode + bundle: two MUFU ops per exponential)
+    enc_ms, enc_n = stages["encode"]
+    exps = float(wl.n) * wl.D
+    enc_avg_s = enc_ms / 1e3 / max(enc_n, 1)
+    achieved = exps / enc_avg_s / 1e9
+    peak_gexp = SMS * MUFU_PER_SM_CLK / 2.0 * SM_MAX_MHZ * 1e6 / 1e9
+    src = os.path.join(ROOT, "paper_2408_09066_gb300", "csrc", "encode.cu")
+    traffic = ENCODE_TRAFFIC["bytes"] if ENCODE_TRAFFIC["sha1"] == _sha1(src) else None
+    roofline = {"bound": "alu", "kernel": "encode_chunk_kernel", "achieved": achieved,
+                "peak": peak_gexp, "unit": "Gexp/s", "frac": achieved / peak_gexp,
+                "traffic": traffic,
+                "peak_basis": "152 SMs x 16 MUFU sin/cos per SM-clock / 2 per complex "
+                              "exponential x 2070 MHz (max SM clock)"}
+    peaks = measured_peaks()
+    cells = wl.W * wl.H
+    dec_ms, dec_n = stages["decode"]
+    ent_ms, ent_n = stages["entropy"]
+    dec_tflops = 8.0 * cells * wl.D / (dec_ms / 1e3 / max(dec_n, 1)) / 1e12
+    fp32_peak = SMS * FP32_FMA_PER_SM_CLK * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    ent_gbs = (2 * 4 + 4) * cells / (ent_ms / 1e3 / max(ent_n, 1)) / 1e9
+    other = {
+        "decode_fp32_simt": {"bound": "alu", "achieved": dec_tflops, "peak": fp32_peak,
+                             "unit": "TFLOP/s", "frac": dec_tflops / fp32_peak},
+        "entropy": {"bound": "hbm", "achieved": ent_gbs, "peak": peaks["hbm_gbs"],
+                    "unit": "GB/s", "frac": ent_gbs / peaks["hbm_gbs"],
+                    "peak_source": peaks["source"]},
+    }
+    launches = sum(n for _, n in stages.values())
+    line = {
+        "metric": METRIC, "value": value, "unit": "points/s", "n_gpus": d.world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": DATA, "config": workload_config(wl, "fp32"),
+        "cells_per_s": d.sum(float(cells * args.steps)) / total_s,
+        "p50_ms": percentile(step_ms, 50), "p99_ms": percentile(step_ms, 99),
+        "stage_ms_per_step": {k: v[0] / args.steps for k, v in stages.items()},
+        "e2e": {"value": e2e_value, "unit": "points/s",
+                "h2d_bytes_per_step": int(wl.xy.nbytes + wl.labels.nbytes),
+                "d2h_bytes_per_step": int(cells * 4),
+                "p50_ms": percentile(e2e_s, 50) * 1e3, "p99_ms": percentile(e2e_s, 99) * 1e3},
+        "roofline": roofline, "rooflines_other": other,
+        "gpu_launches": int(launches), "clocks": clk, "wall_s_timed": t_wall,
+    }
+    m.close()
+    if d.rank == 0 and d.world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(wl)
+    if d.rank == 0:
+        print(json.dumps(line), flush=True)
+    d.close()
+    return 0
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,203 @@
+/*
+ * vsaogm.h - C ABI of libvsaogm.so, the GB300 (sm_103a) hot path of VSA-OGM
+ * (Snyder et al., "Brain Inspired Probabilistic Occupancy Grid Mapping with
+ * Vector Symbolic Architectures", arXiv 2408.09066).
+ *
+ * The library encodes labelled 2D points as FHRR hypervectors and bundles them
+ * into per-tile, per-class memories (Sec. III-B4), decodes the memories over
+ * the grid cells (Sec. III-B5) and turns the class maps into occupancy
+ * probabilities with the disk-mask entropy filter, softmax and probabilistic
+ * signed difference (Algorithm 2, Eqs. softmax, psd, classification).
+ *
+ * Conventions used by every call
+ *  - Pointers named *_dev are CUDA device pointers (or managed memory); *_host
+ *    are host pointers (pinned memory is fastest).  The caller owns every
+ *    buffer it passes; the library owns the map, its memories, its frequency
+ *    tables and its scratch.
+ *  - `stream` is a cudaStream_t passed as void*; NULL is the legacy default
+ *    stream.  Calls only enqueue work on that stream and return; results are
+ *    valid once the stream has reached them.  Consecutive calls on one map
+ *    must use one stream, or the caller must order them.  A map is not
+ *    thread-safe; distinct maps are independent.
+ *  - Return value: VSAOGM_OK (0) or a negative VSAOGM_E_* code.  Nothing else
+ *    crosses the ABI; vsaogm_last_error() describes the last failure of the
+ *    calling thread.  A failed call enqueues nothing.
+ *  - Layouts are row-major with x fastest.  A class map is float [H][W]
+ *    (row j = y index, column i = x index); two class maps are [2][H][W] with
+ *    class 0 = empty (psi = 0) first and class 1 = occupied (psi = 1) second.
+ *    Points are float32 pairs (x, y) in metres, [n][2]; labels are uint8 [n].
+ *  - Memories are complex64 (interleaved re, im) [2T][D], memory 2*beta + psi
+ *    for tile beta = by * tiles_x + bx (Algorithm 1).  They are kept in the
+ *    tile-centred frame: memory 2*beta + psi equals the paper's memory times
+ *    the unit phasor exp(-i 2 pi nu . mu_beta), mu_beta the tile centre, which
+ *    cancels exactly in the similarity of Eq. loc-query.
+ */
+#ifndef VSAOGM_H
+#define VSAOGM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Return codes. */
+#define VSAOGM_OK 0
+#define VSAOGM_E_INVAL -1   /* bad argument or configuration            */
+#define VSAOGM_E_NOMEM -2   /* a device or host allocation failed         */
+#define VSAOGM_E_CUDA -3    /* a CUDA call failed (message has details)   */
+#define VSAOGM_E_TIMEOUT -4 /* a bounded device-side wait gave up         */
+#define VSAOGM_E_DATA -5    /* input data rejected (checked mode only)    */
+
+/* Arithmetic of the decode contraction (Eq. loc-query). */
+#define VSAOGM_DECODE_FP32 0   /* FP32 SIMT, the reference GPU path          */
+#define VSAOGM_DECODE_BF16X3 1 /* tensor cores, split hi/lo bf16, FP32 accum */
+#define VSAOGM_DECODE_FP16X3 2 /* tensor cores, split hi/lo fp16, FP32 accum */
+
+/* vsaogm_config.flags */
+#define VSAOGM_FLAG_CHECKED 1u /* encode synchronises and reports rejected points */
+#define VSAOGM_FLAG_ATOMIC 2u  /* bundle with atomics (no partial-sum scratch,
+                                  result not bitwise reproducible)             */
+
+/* Map parameters (Sec. III-B2 Initialization, Sec. III-B3 tiling, Table of
+ * VSA-OGM parameters).  Memory per map: 2 * tiles_x * tiles_y * D * 8 bytes. */
+typedef struct {
+    int32_t D;            /* FHRR dimension (complex elements per memory), >= 1 */
+    int32_t grid_w;       /* cells along x, >= 1                                  */
+    int32_t grid_h;       /* cells along y, >= 1                                  */
+    float resolution;     /* cell edge in metres, > 0                             */
+    float x_min, y_min;   /* lower-left corner of the map in metres               */
+    int32_t tiles_x;      /* delta along x (evenly sized tiles), >= 1             */
+    int32_t tiles_y;      /* delta along y, >= 1; tiles_x * tiles_y <= 1024       */
+    float length_scale;   /* l of Eq. fb-with-ls-1d in metres, > 0                */
+    int32_t r_occ;        /* disk radius r(psi = 1) in cells, 0..16              */
+    int32_t r_emp;        /* disk radius r(psi = 0) in cells, 0..16              */
+    float rho;            /* decision threshold of Eq. classification             */
+    uint64_t seed;        /* SplitMix64 seed of the axis frequencies              */
+    int32_t decode_prec;  /* VSAOGM_DECODE_*                                      */
+    uint32_t flags;       /* VSAOGM_FLAG_*                                        */
+} vsaogm_config;
+
+typedef struct vsaogm_map vsaogm_map;
+
+/* Fills *cfg with defaults: D 8192, 400 x 400 cells of 0.1 m from (-20, -20),
+ * 4 x 4 tiles, l = 0.1 m, r_occ = r_emp = 3, rho = 0, seed 0, FP32 decode. */
+void vsaogm_config_default(vsaogm_config *cfg);
+
+/* Creates a map (Sec. III-B2, III-B3): validates *cfg, draws the axis
+ * frequencies and allocates zeroed memories on the current CUDA device.
+ * Axis frequencies: nu_x[k] and nu_y[k] (cycles per metre, float32) are
+ * f32((2u - 1) / (2 l)) with u the top 53 bits / 2^53 of SplitMix64 outputs
+ * 2k and 2k + 1 for `seed`, i.e. theta = 2 pi l nu uniform on (-pi, pi).
+ * Synchronous.  Errors: E_INVAL (bad config, NULL), E_NOMEM, E_CUDA.        */
+int vsaogm_create(const vsaogm_config *cfg, vsaogm_map **out);
+
+/* Frees the map and everything it owns.  Synchronises the device first.
+ * NULL is accepted.                                                         */
+int vsaogm_destroy(vsaogm_map *map);
+
+/* Sets every memory to zero (asynchronous on `stream`). */
+int vsaogm_reset(vsaogm_map *map, void *stream);
+
+/* Encoding and bundling (Eq. fb-with-ls-2d, Eq. bundling, Algorithm 1):
+ * for each point p with label psi, the nearest tile centre beta is found
+ * (ties go to the lower tile, points outside the map go to the nearest edge
+ * tile) and phi_k(p) = exp(i 2 pi (nu_x[k] p_x + nu_y[k] p_y)) is added to
+ * memory 2 beta + psi for all k < D.
+ * xy_dev: float [n][2], 8-byte aligned; labels_dev: uint8 [n], values 0 or 1.  n = 0 is a
+ * no-op.  Points with a label above 1 or a non-finite coordinate are not
+ * bundled; they are counted (see vsaogm_rejected) and, with
+ * VSAOGM_FLAG_CHECKED, the call synchronises and returns E_DATA.
+ * Uses library-owned scratch that grows on demand (a growing call allocates
+ * and synchronises).  Errors: E_INVAL (NULL with n > 0, n < 0), E_NOMEM,
+ * E_CUDA, E_DATA.                                                           */
+int vsaogm_encode_bundle(vsaogm_map *map, const float *xy_dev, const uint8_t *labels_dev,
+                         int64_t n, void *stream);
+
+/* Decoding (Eqs. vector-normalization, loc-query, non-linearities):
+ * heat_dev (float [2][H][W]) receives P_hat(psi | cell) =
+ * (P / max_map P)^2 with P = Re sum_k conj(w_k) phi_k(cell) / ||w|| for the
+ * memory w of the cell's tile and class; the maximum runs over the whole map.
+ * A class whose maximum is <= 0 (or whose memories are all zero) gives 0.
+ * Errors: E_INVAL, E_CUDA.                                                  */
+int vsaogm_decode(vsaogm_map *map, float *heat_dev, void *stream);
+
+/* Entropy extraction, softmax, signed difference and classification
+ * (Algorithm 2, Eqs. entropy-mask, softmax, psd, classification) applied to
+ * P_hat from vsaogm_decode: H(psi | x, y) = -sum over in-grid cells within
+ * Euclidean distance r(psi) (cells, inclusive) of P_hat ln P_hat (0 ln 0 = 0);
+ * occ_dev (float [H][W]) = Pr(psi = 1); ogm_dev (float [H][W], nullable) =
+ * Pr(1) - Pr(0); cls_dev (uint8 [H][W], nullable) = 1 where OGM >= rho.
+ * Errors: E_INVAL, E_CUDA.                                                  */
+int vsaogm_entropy(vsaogm_map *map, const float *heat_dev, float *occ_dev, float *ogm_dev,
+                   uint8_t *cls_dev, void *stream);
+
+/* Decode and entropy in one call, with the non-linearity fused into the
+ * entropy pass.  heat_dev (float [2][H][W]) is caller-provided scratch that
+ * receives the normalised similarity P (before the non-linearity).  Outputs
+ * as vsaogm_entropy.  Errors: E_INVAL, E_CUDA.                               */
+int vsaogm_query(vsaogm_map *map, float *heat_dev, float *occ_dev, float *ogm_dev,
+                 uint8_t *cls_dev, void *stream);
+
+/* End-to-end call on host buffers: copies xy_host/labels_host to the device,
+ * bundles them, runs vsaogm_query and copies Pr(psi = 1) back into occ_host
+ * (float [H][W]); returns after the stream has finished.  Device staging is
+ * owned by the map and grows on demand.  Errors: as the calls it makes.     */
+int vsaogm_update_query_host(vsaogm_map *map, const float *xy_host, const uint8_t *labels_host,
+                             int64_t n, float *occ_host, void *stream);
+
+/* Number of points rejected by vsaogm_encode_bundle since the last reset
+ * (synchronises `stream`).                                                  */
+int vsaogm_rejected(vsaogm_map *map, int64_t *count, void *stream);
+
+/* Synchronises `stream` and reports device-side failures recorded since the
+ * last call: E_TIMEOUT if a kernel gave up on a bounded wait (its outputs are
+ * then invalid), else VSAOGM_OK.  Clears the record.                        */
+int vsaogm_status(vsaogm_map *map, void *stream);
+
+/* Copies the memories (complex64 [2T][D], tile-centred frame) to omega_dev. */
+int vsaogm_get_memory(const vsaogm_map *map, float *omega_dev, void *stream);
+
+/* Replaces the memories with omega_dev (complex64 [2T][D]). */
+int vsaogm_set_memory(vsaogm_map *map, const float *omega_dev, void *stream);
+
+/* Multi-map fusion (Algorithm 3): adds src's memories into dst's.  Both maps
+ * must share the axis vectors (D, seed, length scale), the tiling and the
+ * grid; otherwise E_INVAL.  Maps must be on the same device.              */
+int vsaogm_fuse(vsaogm_map *dst, const vsaogm_map *src, void *stream);
+
+/* Copies the axis frequencies (cycles per metre) into host arrays of D floats. */
+int vsaogm_get_axis_frequencies(const vsaogm_map *map, float *nu_x_host, float *nu_y_host);
+
+/* Geometry of the map: number of tiles and memories. */
+int vsaogm_get_shape(const vsaogm_map *map, int32_t *n_tiles, int32_t *n_memories);
+
+/* Stage timing (tracing).  Stages of the calls above, in order: */
+#define VSAOGM_STAGE_SORT 0      /* tile assignment + counting sort (4 kernels)  */
+#define VSAOGM_STAGE_ENCODE 1    /* FHRR encode + bundle of the chunks           */
+#define VSAOGM_STAGE_REDUCE 2    /* fixed-order sum of partial memories          */
+#define VSAOGM_STAGE_NORMS 3     /* memory norms (Eq. vector-normalization)      */
+#define VSAOGM_STAGE_DECODE 4    /* similarity contraction (Eq. loc-query) + max */
+#define VSAOGM_STAGE_NONLINEAR 5 /* (P / max P)^2 in place (vsaogm_decode only)  */
+#define VSAOGM_STAGE_ENTROPY 6   /* entropy stencil + softmax + PSD + threshold  */
+#define VSAOGM_N_STAGES 7
+
+/* Turns stage timing on or off for `map`.  When on, each stage is bracketed
+ * by two CUDA events recorded on the call's stream (a few microseconds of
+ * overhead per stage).  Kernel launches are counted whether timing is on or
+ * not.  Errors: E_INVAL, E_CUDA.                                            */
+int vsaogm_set_timing(vsaogm_map *map, int enable);
+
+/* Accumulated device milliseconds (ms[VSAOGM_N_STAGES], nullable) and kernel
+ * launch counts (launches[VSAOGM_N_STAGES], nullable) per stage since the last
+ * reset; resets the counters when `reset` is non-zero.  Synchronises with
+ * every stream the timed calls used.  Errors: E_INVAL, E_CUDA.               */
+int vsaogm_stage_times(vsaogm_map *map, double *ms, int64_t *launches, int reset);
+
+/* Description of the last error on the calling thread ("" if none). */
+const char *vsaogm_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* VSAOGM_H */

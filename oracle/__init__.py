@@ -77,6 +77,8 @@ def _load():
             build()
             lib = ctypes.CDLL(_LIB)
             P = ctypes.POINTER
+            lib.orc_num_threads.restype = ctypes.c_int32
+            lib.orc_num_threads.argtypes = []
             lib.orc_splitmix64_at.restype = ctypes.c_uint64
             lib.orc_splitmix64_at.argtypes = [ctypes.c_uint64, ctypes.c_uint64]
             lib.orc_draw_nu.argtypes = [ctypes.c_uint64, ctypes.c_int32, ctypes.c_double,
@@ -126,6 +128,11 @@ def _frame(frame: str) -> int:
 
 
 # --------------------------------------------------------------------------
+def num_threads() -> int:
+    """Threads the oracle's parallel loops use."""
+    return int(_load().orc_num_threads())
+
+
 def splitmix64_at(seed: int, i: int) -> int:
     """Output number ``i`` (0-based) of the SplitMix64 stream seeded with ``seed``."""
     return int(_load().orc_splitmix64_at(seed, i))

@@ -42,6 +42,20 @@ typedef struct {
     int32_t tiles_y;     /* delta along y */
 } orc_grid;
 
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* Threads the parallel loops below use (1 without OpenMP). */
+int32_t orc_num_threads(void)
+{
+#ifdef _OPENMP
+    return (int32_t)omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
 /* ------------------------------------------------------------------------ */
 /* SplitMix64 (Steele, Lea and Flood, "Fast splittable pseudorandom number
  * generators", OOPSLA 2014): the state advances by the golden-ratio gamma

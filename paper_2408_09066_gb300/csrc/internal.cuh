@@ -1,0 +1,174 @@
+// Internal declarations shared by the translation units of libvsaogm.so.
+// Nothing here is part of the C ABI (include/vsaogm.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "vsaogm.h"
+
+namespace vsaogm_impl {
+
+constexpr int kMaxTiles = 1024;      // tiles_x * tiles_y
+constexpr int kMaxRadius = 16;       // disk radius in cells
+constexpr int kSortBlock = 2048;     // points per block of the counting sort
+constexpr int kSortWarps = 8;        // warps per sort block (256 points each)
+constexpr int kMaxChunk = 2048;      // points per encode chunk (upper bound)
+constexpr int64_t kMaxBatch = 1 << 26;  // points per internal encode batch
+
+// Geometry of one axis as the kernels see it.
+struct AxisDev {
+    int n_tiles;
+    const float *bnd_lo;    // [n_tiles - 1]: largest float <= x_min + a * tile_w, a = 1..
+    const double *centre;   // [n_tiles]: tile centres, FP64
+};
+
+// Cell table of one axis: the tile of each cell (Algorithm 1's rule applied to
+// the cell centre) and the cell centre relative to that tile's centre.
+struct CellAxisDev {
+    const int *tile;        // [cells]
+    const float *offset;    // [cells] f32(cell centre - tile centre), metres
+};
+
+// One CTA's worth of decode work: a block of cells inside one tile.
+struct DecodeBlock {
+    int tile;       // beta
+    int i0, j0;     // first column / row of the block
+    int i1, j1;     // one past the last column / row (clipped to the tile)
+};
+
+// Grow-on-demand device buffer owned by a map.
+struct DevBuf {
+    void *ptr = nullptr;
+    size_t bytes = 0;
+};
+
+struct Scratch {
+    DevBuf blk_hist;     // int [nb][S + 1] histogram, then in-place column offsets
+    DevBuf seg_meta;     // int: seg_total[S+1], seg_base[S+2], chunk_begin[S+1], n_chunks[1]
+    DevBuf chunks;       // int4 [max_chunks]: (segment, begin, end, 0)
+    DevBuf sorted;       // float2 [n]: tile-centred coordinates sorted by segment
+    DevBuf partial;      // float2 [max_chunks][D]: per-chunk partial memories
+    DevBuf stage_xy;     // host-entry staging: float [n][2]
+    DevBuf stage_lab;    // uint8 [n]
+    DevBuf stage_heat;   // float [2][H][W]
+    DevBuf stage_occ;    // float [H][W]
+    DevBuf dec_partial;  // float [slices][2][H][W]: tensor-core decode partial maps
+};
+
+// CUDA-event timing of the stages of each call (tracing) and launch counts.
+struct StageTimer {
+    bool enabled = false;
+    std::vector<cudaEvent_t> free_events;
+    struct Pending {
+        int stage;
+        cudaEvent_t a, b;
+    };
+    std::vector<Pending> pending;
+    double ms[VSAOGM_N_STAGES] = {};
+    long long launches[VSAOGM_N_STAGES] = {};
+};
+
+}  // namespace vsaogm_impl
+
+struct vsaogm_map {
+    vsaogm_config cfg;
+    int device;
+    int T, S;                    // tiles, memories (2T)
+    double tile_w, tile_h;
+    // device state owned by the map
+    float *nu;                   // [2][D]: nu_x then nu_y, cycles per metre
+    float nu_max[2];             // max_k |nu_x[k]|, max_k |nu_y[k]|
+    float2 *omega;               // [S][D]
+    float *inv_norm;             // [S]: 1 / ||omega||, 0 for an all-zero memory
+    unsigned *maxima;            // [2]: order-preserving encoding of max P per class
+    unsigned long long *rejected;  // [1]: points rejected by encode since reset
+    float *bnd_x_lo, *bnd_y_lo;  // [tiles - 1]
+    double *centre_x, *centre_y; // [tiles]
+    int *col_tile, *row_tile;    // [W], [H]
+    float *col_off, *row_off;    // [W], [H]
+    vsaogm_impl::DecodeBlock *dblocks;     // 64 x 64 blocks (FP32 SIMT decode)
+    int n_dblocks;
+    vsaogm_impl::DecodeBlock *tcblocks;    // <= 128 x 128 blocks (tensor-core decode)
+    int n_tcblocks;
+    int tc_n;                              // MMA N: widest block rounded up to 16
+    int *status;                           // first error code recorded by a kernel
+    int r_hw[2][2 * vsaogm_impl::kMaxRadius + 1];  // disk half-widths per class and dy
+    vsaogm_impl::Scratch ws;
+    vsaogm_impl::StageTimer timer;
+    float *host_nu;              // [2][D] host copy
+};
+
+namespace vsaogm_impl {
+
+// Error reporting (thread-local message; see vsaogm_last_error).
+int set_error(int code, const char *fmt, ...);
+int cuda_error(cudaError_t e, const char *what);
+int ensure(DevBuf &b, size_t bytes);
+
+// Brackets one stage: records a start event on `st` when timing is on and,
+// on end(), the stop event and `kernels` launches for the stage.
+class StageScope {
+  public:
+    StageScope(vsaogm_map *m, int stage, cudaStream_t st);
+    void end(int kernels);
+    ~StageScope();
+
+  private:
+    vsaogm_map *m_;
+    int stage_;
+    cudaStream_t st_;
+    cudaEvent_t a_ = nullptr;
+    bool done_ = false;
+};
+
+inline AxisDev axis_x(const vsaogm_map *m) { return {m->cfg.tiles_x, m->bnd_x_lo, m->centre_x}; }
+inline AxisDev axis_y(const vsaogm_map *m) { return {m->cfg.tiles_y, m->bnd_y_lo, m->centre_y}; }
+
+// encode.cu
+int encode_bundle(vsaogm_map *m, const float *xy, const uint8_t *lab, int64_t n, cudaStream_t st);
+
+// decode.cu
+int decode_raw(vsaogm_map *m, float *heat, cudaStream_t st);         // P and maxima
+int apply_nonlinearity(vsaogm_map *m, float *heat, cudaStream_t st); // P -> P_hat in place
+int memory_norms(vsaogm_map *m, cudaStream_t st);
+// decode_tc.cu: split-precision tensor-core decode (P and maxima)
+int decode_tensor_cores(vsaogm_map *m, float *heat, cudaStream_t st);
+
+// entropy.cu
+// raw_input: heat holds P (the non-linearity is applied on load with the
+// map's maxima); otherwise heat holds P_hat.
+int entropy(vsaogm_map *m, const float *heat, bool raw_input, float *occ, float *ogm,
+            uint8_t *cls, cudaStream_t st);
+
+// misc kernels (decode.cu)
+int add_memories(float2 *dst, const float2 *src, int64_t count, cudaStream_t st);
+
+// Order-preserving map from float to unsigned (for atomicMax of floats).
+__host__ __device__ inline unsigned float_to_ordered(float f)
+{
+    unsigned u;
+#ifdef __CUDA_ARCH__
+    u = __float_as_uint(f);
+#else
+    memcpy(&u, &f, 4);
+#endif
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__host__ __device__ inline float ordered_to_float(unsigned o)
+{
+    unsigned u = (o & 0x80000000u) ? (o & 0x7fffffffu) : ~o;
+    float f;
+#ifdef __CUDA_ARCH__
+    f = __uint_as_float(u);
+#else
+    memcpy(&f, &u, 4);
+#endif
+    return f;
+}
+
+}  // namespace vsaogm_impl

@@ -1,0 +1,186 @@
+"""Seeded synthetic 2D lidar data shaped like the paper's workloads.
+
+Input generator only: it builds worlds, scans and trajectories and labels the
+points with the raycast heuristic of Sec. III-B1 (a beam that ends before its
+maximum range gives an occupied point; the max-range end point and points
+interpolated along the beam are empty).  It holds none of the mapping
+method's arithmetic and is used by the tests, the benchmark and the examples
+to feed both the CUDA path and the oracle the same arrays.
+
+The paper's datasets (ToySim, Intel Map, EviLOG) are not available, so these
+seeded stand-ins follow the workload shapes named for this library:
+  * small   : 64 x 64 cells at 0.1 m (6.4 m square), one tile, D = 1024,
+              one 360-beam scan from the centre, max range 6 m, sigma 0.02 m,
+              10 empty samples per beam (about 3.96k points);
+  * paper   : 400 x 400 cells at 0.1 m (40 m square), 4 x 4 tiles, D = 8192,
+              100 scans along a 0.5 m-step random walk, 1080 beams, max range
+              30 m, sigma 0.03 m, 20 empty samples per beam (about 2.27M points).
+"""
+from __future__ import annotations
+
+import dataclasses
+
+import numpy as np
+
+
+@dataclasses.dataclass
+class World:
+    half: float            # the world is the square [-half, half]^2, walled
+    rects: np.ndarray      # [n][4] axis-aligned boxes (x0, y0, x1, y1)
+    discs: np.ndarray      # [n][3] discs (cx, cy, r)
+
+    def inside_obstacle(self, p: np.ndarray, margin: float = 0.0) -> np.ndarray:
+        p = np.atleast_2d(p)
+        x, y = p[:, 0:1], p[:, 1:2]
+        r = self.rects
+        in_r = ((x >= r[:, 0] - margin) & (x <= r[:, 2] + margin)
+                & (y >= r[:, 1] - margin) & (y <= r[:, 3] + margin)).any(1)
+        d = self.discs
+        in_d = (((x - d[:, 0]) ** 2 + (y - d[:, 1]) ** 2) <= (d[:, 2] + margin) ** 2).any(1)
+        out = (np.abs(p[:, 0]) > self.half - margin) | (np.abs(p[:, 1]) > self.half - margin)
+        return in_r | in_d | out
+
+
+def make_world(rng: np.random.Generator, half: float, n_rect: int, n_disc: int,
+               rect_size: tuple, disc_r: tuple, keep_free=(0.0, 0.0), free_r: float = 0.5) -> World:
+    """Random axis-aligned rectangles and discs; none covers the disc of radius
+    ``free_r`` around ``keep_free`` (rejection sampling)."""
+    kx, ky = keep_free
+    rects, discs = [], []
+    while len(rects) < n_rect:
+        w, h = rng.uniform(*rect_size, size=2)
+        cx, cy = rng.uniform(-half + w / 2, half - w / 2), rng.uniform(-half + h / 2, half - h / 2)
+        box = (cx - w / 2, cy - h / 2, cx + w / 2, cy + h / 2)
+        nx = min(max(kx, box[0]), box[2])
+        ny = min(max(ky, box[1]), box[3])
+        if (nx - kx) ** 2 + (ny - ky) ** 2 > free_r ** 2:
+            rects.append(box)
+    while len(discs) < n_disc:
+        r = rng.uniform(*disc_r)
+        cx, cy = rng.uniform(-half + r, half - r, size=2)
+        if (cx - kx) ** 2 + (cy - ky) ** 2 > (r + free_r) ** 2:
+            discs.append((cx, cy, r))
+    return World(half, np.array(rects, np.float64).reshape(-1, 4),
+                 np.array(discs, np.float64).reshape(-1, 3))
+
+
+def raycast(world: World, origin, angles: np.ndarray) -> np.ndarray:
+    """Distance from ``origin`` to the first surface along each angle."""
+    ox, oy = float(origin[0]), float(origin[1])
+    dx, dy = np.cos(angles)[:, None], np.sin(angles)[:, None]
+    best = np.full((len(angles), 1), np.inf)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        # boundary walls and rectangles: slab test against each box
+        boxes = np.concatenate([world.rects,
+                                np.array([[-world.half, -world.half, world.half, world.half]])])
+        tx0 = (boxes[:, 0] - ox) / dx
+        tx1 = (boxes[:, 2] - ox) / dx
+        ty0 = (boxes[:, 1] - oy) / dy
+        ty1 = (boxes[:, 3] - oy) / dy
+        tmin = np.maximum(np.minimum(tx0, tx1), np.minimum(ty0, ty1))
+        tmax = np.minimum(np.maximum(tx0, tx1), np.maximum(ty0, ty1))
+        # entering hit for obstacles; the wall box is hit from the inside (tmax)
+        t_obs = np.where((tmax >= tmin) & (tmin > 0), tmin, np.inf)[:, :-1]
+        t_wall = tmax[:, -1:]
+        best = np.minimum(best, t_wall)
+        if t_obs.shape[1]:
+            best = np.minimum(best, t_obs.min(1, keepdims=True))
+        if len(world.discs):
+            fx = ox - world.discs[:, 0]
+            fy = oy - world.discs[:, 1]
+            b = fx * dx + fy * dy
+            c = fx * fx + fy * fy - world.discs[:, 2] ** 2
+            disc = b * b - c
+            t = -b - np.sqrt(np.where(disc >= 0, disc, np.nan))
+            t = np.where((disc >= 0) & (t > 0), t, np.inf)
+            best = np.minimum(best, t.min(1, keepdims=True))
+    return best[:, 0]
+
+
+def scan(world: World, origin, n_beams: int, max_range: float, sigma: float, n_empty: int,
+         rng: np.random.Generator):
+    """One labelled scan: per beam the end point (occupied if the beam hit a
+    surface within max range, else the empty max-range point) followed by
+    ``n_empty`` empty points at u * range, u ~ U(0, 1)."""
+    ang = np.arange(n_beams) * (2 * np.pi / n_beams)
+    rng_true = raycast(world, origin, ang)
+    hit = rng_true <= max_range
+    meas = np.where(hit, rng_true + rng.normal(0.0, sigma, n_beams), max_range)
+    meas = np.maximum(meas, 0.0)
+    u = rng.uniform(0.0, 1.0, (n_beams, n_empty))
+    rr = np.concatenate([meas[:, None], u * meas[:, None]], 1)  # [beams][1 + n_empty]
+    lab = np.zeros(rr.shape, np.uint8)
+    lab[:, 0] = hit.astype(np.uint8)
+    x = origin[0] + rr * np.cos(ang)[:, None]
+    y = origin[1] + rr * np.sin(ang)[:, None]
+    xy = np.stack([x.ravel(), y.ravel()], 1).astype(np.float32)
+    return xy, lab.ravel()
+
+
+def trajectory(world: World, start, n_steps: int, step: float, rng: np.random.Generator,
+               margin: float = 0.3) -> np.ndarray:
+    """Random walk of ``n_steps`` poses with fixed step length, rejecting steps
+    that end inside an obstacle (or within ``margin`` of one)."""
+    poses = [np.asarray(start, np.float64)]
+    heading = rng.uniform(0, 2 * np.pi)
+    while len(poses) < n_steps:
+        for _ in range(64):
+            h = heading + rng.normal(0.0, 0.6)
+            cand = poses[-1] + step * np.array([np.cos(h), np.sin(h)])
+            if not world.inside_obstacle(cand, margin)[0]:
+                heading = h
+                poses.append(cand)
+                break
+        else:
+            heading = rng.uniform(0, 2 * np.pi)
+    return np.array(poses)
+
+
+@dataclasses.dataclass
+class Workload:
+    name: str
+    xy: np.ndarray          # float32 [n][2]
+    labels: np.ndarray      # uint8 [n]
+    W: int
+    H: int
+    res: float
+    x_min: float
+    y_min: float
+    tiles_x: int
+    tiles_y: int
+    D: int
+    length_scale: float
+    seed: int
+    world: World
+
+    @property
+    def n(self) -> int:
+        return len(self.labels)
+
+
+def small_scan(seed: int = 1001, D: int = 1024) -> Workload:
+    """One 360-beam scan in a walled 6.4 m square with 5 boxes and 3 discs."""
+    rng = np.random.default_rng(seed)
+    w = make_world(rng, 3.2, 5, 3, (0.3, 1.5), (0.2, 0.6))
+    xy, lab = scan(w, (0.0, 0.0), 360, 6.0, 0.02, 10, rng)
+    return Workload("small_64x64_1tile", xy, lab, 64, 64, 0.1, -3.2, -3.2, 1, 1, D, 0.1, seed, w)
+
+
+def paper_trajectory(seed: int = 1002, D: int = 8192, n_scans: int = 100) -> Workload:
+    """100 scans of 1080 beams along a random walk in a walled 40 m square
+    with 40 obstacles (25 boxes of 1-5 m, 15 discs of radius 0.5-2 m)."""
+    rng = np.random.default_rng(seed)
+    w = make_world(rng, 20.0, 25, 15, (1.0, 5.0), (0.5, 2.0), free_r=1.0)
+    poses = trajectory(w, (0.0, 0.0), n_scans, 0.5, rng)
+    parts = [scan(w, p, 1080, 30.0, 0.03, 20, rng) for p in poses]
+    xy = np.concatenate([p[0] for p in parts])
+    lab = np.concatenate([p[1] for p in parts])
+    return Workload("paper_400x400_4x4tiles", xy, lab, 400, 400, 0.1, -20.0, -20.0, 4, 4, D,
+                    0.1, seed, w)
+
+
+def ground_truth(world: World, W: int, H: int, res: float, x_min: float, y_min: float) -> np.ndarray:
+    """Occupancy of each cell centre (1 inside an obstacle or outside the walls)."""
+    j, i = np.meshgrid(np.arange(H), np.arange(W), indexing="ij")
+    c = np.stack([x_min + (i.ravel() + 0.5) * res, y_min + (j.ravel() + 0.5) * res], 1)
+    return world.inside_obstacle(c).reshape(H, W).astype(np.uint8)

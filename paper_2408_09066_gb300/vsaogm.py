@@ -1,0 +1,239 @@
+"""Thin ctypes binding of libvsaogm.so (C ABI in include/vsaogm.h).
+
+Argument marshalling only: every step of the hot path runs in the library's
+CUDA kernels.  PyTorch supplies device memory and the current CUDA stream.
+If the library has not been built, loading it raises: there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libvsaogm.so")
+
+STAGES = ("sort", "encode", "reduce", "norms", "decode", "nonlinear", "entropy")
+OK, E_INVAL, E_NOMEM, E_CUDA, E_TIMEOUT, E_DATA = 0, -1, -2, -3, -4, -5
+DECODE_FP32, DECODE_BF16X3, DECODE_FP16X3 = 0, 1, 2
+FLAG_CHECKED, FLAG_ATOMIC = 1, 2
+
+
+class VsaogmError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"vsaogm error {code}: {msg}")
+        self.code = code
+
+
+class Config(ctypes.Structure):
+    """Mirror of ``vsaogm_config``."""
+    _fields_ = [("D", ctypes.c_int32), ("grid_w", ctypes.c_int32), ("grid_h", ctypes.c_int32),
+                ("resolution", ctypes.c_float), ("x_min", ctypes.c_float),
+                ("y_min", ctypes.c_float), ("tiles_x", ctypes.c_int32),
+                ("tiles_y", ctypes.c_int32), ("length_scale", ctypes.c_float),
+                ("r_occ", ctypes.c_int32), ("r_emp", ctypes.c_int32), ("rho", ctypes.c_float),
+                ("seed", ctypes.c_uint64), ("decode_prec", ctypes.c_int32),
+                ("flags", ctypes.c_uint32)]
+
+
+_lib = None
+_lock = threading.Lock()
+_V = ctypes.c_void_p
+_SIGNATURES = {
+    "vsaogm_config_default": (None, [_V]),
+    "vsaogm_create": (ctypes.c_int, [_V, _V]),
+    "vsaogm_destroy": (ctypes.c_int, [_V]),
+    "vsaogm_reset": (ctypes.c_int, [_V, _V]),
+    "vsaogm_encode_bundle": (ctypes.c_int, [_V, _V, _V, ctypes.c_int64, _V]),
+    "vsaogm_decode": (ctypes.c_int, [_V, _V, _V]),
+    "vsaogm_entropy": (ctypes.c_int, [_V, _V, _V, _V, _V, _V]),
+    "vsaogm_query": (ctypes.c_int, [_V, _V, _V, _V, _V, _V]),
+    "vsaogm_update_query_host": (ctypes.c_int, [_V, _V, _V, ctypes.c_int64, _V, _V]),
+    "vsaogm_rejected": (ctypes.c_int, [_V, _V, _V]),
+    "vsaogm_get_memory": (ctypes.c_int, [_V, _V, _V]),
+    "vsaogm_set_memory": (ctypes.c_int, [_V, _V, _V]),
+    "vsaogm_fuse": (ctypes.c_int, [_V, _V, _V]),
+    "vsaogm_get_axis_frequencies": (ctypes.c_int, [_V, _V, _V]),
+    "vsaogm_get_shape": (ctypes.c_int, [_V, _V, _V]),
+    "vsaogm_status": (ctypes.c_int, [_V, _V]),
+    "vsaogm_set_timing": (ctypes.c_int, [_V, ctypes.c_int]),
+    "vsaogm_stage_times": (ctypes.c_int, [_V, _V, _V, ctypes.c_int]),
+    "vsaogm_last_error": (ctypes.c_char_p, []),
+}
+
+
+def lib():
+    """The loaded library (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"{LIB_PATH} is missing: run __graft_entry__.build() or "
+                                   "python paper_2408_09066_gb300/build.py")
+            L = ctypes.CDLL(LIB_PATH)
+            for name, (res, args) in _SIGNATURES.items():
+                f = getattr(L, name)
+                f.restype = res
+                f.argtypes = args
+            _lib = L
+    return _lib
+
+
+def _check(rc: int):
+    if rc != OK:
+        raise VsaogmError(rc, lib().vsaogm_last_error().decode())
+
+
+def default_config(**kw) -> Config:
+    c = Config()
+    lib().vsaogm_config_default(ctypes.byref(c))
+    for k, v in kw.items():
+        if not hasattr(c, k):
+            raise AttributeError(k)
+        setattr(c, k, v)
+    return c
+
+
+def _stream(stream):
+    import torch
+    if stream is None:
+        return _V(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return _V(stream)
+    return _V(stream.cuda_stream)
+
+
+def _dev(t, dtype, shape=None, name="tensor"):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} must have shape {tuple(shape)}, got {tuple(t.shape)}")
+    return _V(t.data_ptr())
+
+
+class Map:
+    """One occupancy map: memories, axis frequencies and scratch on the device."""
+
+    def __init__(self, config: Config | None = None, **kw):
+        self.config = config if config is not None else default_config(**kw)
+        h = _V()
+        _check(lib().vsaogm_create(ctypes.byref(self.config), ctypes.byref(h)))
+        self._h = h
+        self.W, self.H, self.D = self.config.grid_w, self.config.grid_h, self.config.D
+        T, S = ctypes.c_int32(), ctypes.c_int32()
+        _check(lib().vsaogm_get_shape(self._h, ctypes.byref(T), ctypes.byref(S)))
+        self.n_tiles, self.n_memories = T.value, S.value
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _check(lib().vsaogm_destroy(self._h))
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    @property
+    def handle(self):
+        return self._h
+
+    # -- hot path ---------------------------------------------------------
+    def reset(self, stream=None):
+        _check(lib().vsaogm_reset(self._h, _stream(stream)))
+
+    def encode_bundle(self, xy, labels, stream=None):
+        import torch
+        n = labels.shape[0]
+        _check(lib().vsaogm_encode_bundle(self._h, _dev(xy, torch.float32, (n, 2), "xy"),
+                                          _dev(labels, torch.uint8, (n,), "labels"), n,
+                                          _stream(stream)))
+
+    def decode(self, heat, stream=None):
+        import torch
+        _check(lib().vsaogm_decode(self._h, _dev(heat, torch.float32, (2, self.H, self.W), "heat"),
+                                   _stream(stream)))
+
+    def entropy(self, heat, occ, ogm=None, cls=None, stream=None):
+        import torch
+        hw = (self.H, self.W)
+        _check(lib().vsaogm_entropy(
+            self._h, _dev(heat, torch.float32, (2,) + hw, "heat"), _dev(occ, torch.float32, hw, "occ"),
+            _dev(ogm, torch.float32, hw, "ogm") if ogm is not None else None,
+            _dev(cls, torch.uint8, hw, "cls") if cls is not None else None, _stream(stream)))
+
+    def query(self, heat, occ, ogm=None, cls=None, stream=None):
+        import torch
+        hw = (self.H, self.W)
+        _check(lib().vsaogm_query(
+            self._h, _dev(heat, torch.float32, (2,) + hw, "heat"), _dev(occ, torch.float32, hw, "occ"),
+            _dev(ogm, torch.float32, hw, "ogm") if ogm is not None else None,
+            _dev(cls, torch.uint8, hw, "cls") if cls is not None else None, _stream(stream)))
+
+    def update_query_host(self, xy: np.ndarray, labels: np.ndarray, occ: np.ndarray, stream=None):
+        """Host arrays in and out: xy float32 [n][2], labels uint8 [n], occ float32 [H][W]."""
+        for a, dt in ((xy, np.float32), (labels, np.uint8), (occ, np.float32)):
+            if a.dtype != dt or not a.flags.c_contiguous:
+                raise TypeError("host arrays must be C-contiguous with the documented dtypes")
+        if occ.shape != (self.H, self.W) or xy.shape != (len(labels), 2):
+            raise ValueError("bad host array shapes")
+        _check(lib().vsaogm_update_query_host(self._h, _V(xy.ctypes.data), _V(labels.ctypes.data),
+                                              len(labels), _V(occ.ctypes.data), _stream(stream)))
+
+    # -- state --------------------------------------------------------------
+    def rejected(self, stream=None) -> int:
+        v = ctypes.c_int64()
+        _check(lib().vsaogm_rejected(self._h, ctypes.byref(v), _stream(stream)))
+        return v.value
+
+    def get_memory(self, out=None, stream=None):
+        import torch
+        if out is None:
+            out = torch.empty((self.n_memories, self.D), dtype=torch.complex64, device="cuda")
+        _check(lib().vsaogm_get_memory(self._h, _dev(out, torch.complex64,
+                                                     (self.n_memories, self.D), "omega"),
+                                       _stream(stream)))
+        return out
+
+    def set_memory(self, omega, stream=None):
+        import torch
+        _check(lib().vsaogm_set_memory(self._h, _dev(omega, torch.complex64,
+                                                     (self.n_memories, self.D), "omega"),
+                                       _stream(stream)))
+
+    def fuse(self, other: "Map", stream=None):
+        _check(lib().vsaogm_fuse(self._h, other._h, _stream(stream)))
+
+    def status(self, stream=None):
+        """Raises VsaogmError(E_TIMEOUT) if a kernel gave up on a bounded wait."""
+        _check(lib().vsaogm_status(self._h, _stream(stream)))
+
+    def set_timing(self, enable: bool = True):
+        _check(lib().vsaogm_set_timing(self._h, 1 if enable else 0))
+
+    def stage_times(self, reset: bool = False):
+        """{stage: (milliseconds, kernel launches)} accumulated since the last reset."""
+        ms = (ctypes.c_double * len(STAGES))()
+        cnt = (ctypes.c_int64 * len(STAGES))()
+        _check(lib().vsaogm_stage_times(self._h, ms, cnt, 1 if reset else 0))
+        return {s: (ms[i], cnt[i]) for i, s in enumerate(STAGES)}
+
+    def axis_frequencies(self):
+        nx = np.empty(self.D, np.float32)
+        ny = np.empty(self.D, np.float32)
+        _check(lib().vsaogm_get_axis_frequencies(self._h, _V(nx.ctypes.data), _V(ny.ctypes.data)))
+        return nx, ny

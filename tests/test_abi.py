@@ -1,0 +1,94 @@
+"""The C ABI library: builds, loads, exports every symbol of include/vsaogm.h,
+and validates its arguments on the host (no GPU needed for any of this)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2408_09066_gb300 import build as build_mod
+from paper_2408_09066_gb300 import vsaogm as V
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "vsaogm.h")
+
+
+@pytest.fixture(scope="module")
+def L():
+    build_mod.build()
+    return V.lib()
+
+
+def _declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(vsaogm_\w+)\s*\(", src)))
+
+
+def test_header_declares_the_hot_path_entry_points():
+    names = _declared_functions()
+    for must in ("vsaogm_create", "vsaogm_encode_bundle", "vsaogm_decode", "vsaogm_entropy",
+                 "vsaogm_destroy", "vsaogm_last_error"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol(L):
+    missing = [n for n in _declared_functions() if not hasattr(L, n)]
+    assert not missing, missing
+    assert set(V._SIGNATURES) >= set(_declared_functions())
+
+
+def test_config_layout_and_defaults(L):
+    assert ctypes.sizeof(V.Config) == 64
+    c = V.default_config()
+    assert (c.D, c.grid_w, c.grid_h, c.tiles_x, c.tiles_y, c.r_occ, c.r_emp) == (8192, 400, 400, 4, 4, 3, 3)
+    assert abs(c.resolution - 0.1) < 1e-7 and abs(c.length_scale - 0.1) < 1e-7
+    assert c.decode_prec == V.DECODE_FP32 and c.flags == 0
+
+
+@pytest.mark.parametrize("field,value,msg", [
+    ("D", 0, "D must"), ("grid_w", 0, "grid_w"), ("resolution", 0.0, "resolution"),
+    ("resolution", float("nan"), "resolution"), ("tiles_x", 0, "tiles"),
+    ("tiles_x", 401, "tiles"), ("length_scale", -1.0, "length_scale"), ("r_occ", -1, "radii"),
+    ("r_emp", 17, "radii"), ("decode_prec", 9, "decode_prec"), ("flags", 64, "flags"),
+    ("x_min", float("inf"), "x_min")])
+def test_create_rejects_bad_config_before_touching_the_gpu(L, field, value, msg):
+    c = V.default_config(**{field: value})
+    h = ctypes.c_void_p()
+    rc = L.vsaogm_create(ctypes.byref(c), ctypes.byref(h))
+    assert rc == V.E_INVAL and not h.value
+    assert msg in L.vsaogm_last_error().decode()
+
+
+def test_too_many_tiles_rejected(L):
+    c = V.default_config(grid_w=2048, grid_h=2048, tiles_x=64, tiles_y=32)
+    h = ctypes.c_void_p()
+    assert L.vsaogm_create(ctypes.byref(c), ctypes.byref(h)) == V.E_INVAL
+
+
+def test_null_arguments_rejected(L):
+    assert L.vsaogm_create(None, None) == V.E_INVAL
+    assert L.vsaogm_encode_bundle(None, None, None, 0, None) == V.E_INVAL
+    assert L.vsaogm_decode(None, None, None) == V.E_INVAL
+    assert L.vsaogm_entropy(None, None, None, None, None, None) == V.E_INVAL
+    assert L.vsaogm_query(None, None, None, None, None, None) == V.E_INVAL
+    assert L.vsaogm_fuse(None, None, None) == V.E_INVAL
+    assert L.vsaogm_destroy(None) == V.OK
+
+
+def test_create_without_a_gpu_fails_cleanly(L):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    c = V.default_config(D=64, grid_w=8, grid_h=8, tiles_x=1, tiles_y=1)
+    h = ctypes.c_void_p()
+    rc = L.vsaogm_create(ctypes.byref(c), ctypes.byref(h))
+    assert rc in (V.E_CUDA, V.E_NOMEM) and not h.value
+    assert L.vsaogm_last_error().decode()
+
+
+def test_binding_refuses_missing_library(monkeypatch, tmp_path):
+    monkeypatch.setattr(V, "LIB_PATH", str(tmp_path / "nope.so"))
+    monkeypatch.setattr(V, "_lib", None)
+    with pytest.raises(RuntimeError, match="missing"):
+        V.lib()

@@ -1,0 +1,84 @@
+"""Parity of the split-precision tensor-core decode (tcgen05, BF16x3 / FP16x3)
+with the FP64 oracle, and agreement with the FP32 SIMT path on the same GPU.
+
+Tolerances stated for the low-precision paths: normalised heat maps P_hat
+<= 1e-2 normwise, occupancy Pr(psi = 1) <= 1e-3 absolute.  The split products
+carry about 16 significant bits, so the raw maps P are also held to the FP32
+path's 1e-4 here.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from helpers import config_for, normwise, oracle_grid, run_gpu
+from paper_2408_09066_gb300 import synth
+from paper_2408_09066_gb300 import vsaogm as V
+
+pytestmark = pytest.mark.gpu
+
+PRECS = [V.DECODE_BF16X3, V.DECODE_FP16X3]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    from paper_2408_09066_gb300 import build
+    build.build()
+
+
+def _oracle(cfg, xy, lab):
+    g = oracle_grid(cfg)
+    nx, ny = oracle.draw_nu(cfg.seed, cfg.D, float(np.float32(cfg.length_scale)))
+    return oracle.pipeline(g, nx, ny, xy, lab, cfg.r_occ, cfg.r_emp, cfg.rho, "tile")
+
+
+def _check(got, want):
+    assert normwise(got["P"], want["P"]) <= 1e-4
+    assert normwise(got["Phat"], want["Phat"]) <= 1e-2
+    assert np.abs(got["occ"] - want["pr1"]).max() <= 1e-3
+    assert np.array_equal(got["occ_query"], got["occ"])
+    assert np.array_equal(got["cls"], oracle.classify_f32(got["ogm"], 0.0))
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_small_scan(prec):
+    wl = synth.small_scan()
+    cfg = config_for(wl, decode_prec=prec)
+    _check(run_gpu(cfg, wl.xy, wl.labels), _oracle(cfg, wl.xy, wl.labels))
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("D", [4096, 8192, 16384])
+def test_precision_configs(prec, D):
+    """The small map and scan at the dimensions of the precision study."""
+    wl = synth.small_scan(D=D)
+    cfg = config_for(wl, decode_prec=prec)
+    _check(run_gpu(cfg, wl.xy, wl.labels), _oracle(cfg, wl.xy, wl.labels))
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_ragged_blocks_and_slices(prec):
+    """Tiles wider than one 128-cell block, ragged block edges, D not a multiple
+    of the 32-frequency stage."""
+    rng = np.random.default_rng(5)
+    n = 20000
+    xy = rng.uniform(-9.0, 9.0, (n, 2)).astype(np.float32)
+    lab = rng.integers(0, 2, n).astype(np.uint8)
+    cfg = V.default_config(D=1000, grid_w=300, grid_h=170, resolution=0.06, x_min=-9.0,
+                           y_min=-5.1, tiles_x=2, tiles_y=1, length_scale=0.15, seed=9,
+                           decode_prec=prec)
+    _check(run_gpu(cfg, xy, lab), _oracle(cfg, xy, lab))
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_matches_fp32_path_on_paper_scale(prec):
+    """400 x 400 cells, 4 x 4 tiles, D = 8192, 2.27M points: the tensor-core maps
+    agree with the FP32 SIMT maps (which the oracle pins) to the FP32 tolerance."""
+    wl = synth.paper_trajectory()
+    ref = run_gpu(config_for(wl), wl.xy, wl.labels)
+    got = run_gpu(config_for(wl, decode_prec=prec), wl.xy, wl.labels)
+    assert normwise(got["P"], ref["P"]) <= 1e-4
+    assert normwise(got["Phat"], ref["Phat"]) <= 1e-3
+    assert np.abs(got["occ"] - ref["occ"]).max() <= 1e-3
