@@ -21,6 +21,7 @@
 #include <algorithm>
 
 #include "internal.cuh"
+#include "sm100.cuh"
 
 namespace vsaogm_impl {
 namespace {
@@ -238,12 +239,15 @@ __global__ void __launch_bounds__(256) seg_scatter_kernel(const float2 *__restri
 //    2 pi f are taken.
 //    Fast reduction (every |nu dx|, |nu dy| of the chunk below 32 turns):
 //      p1 = fl(nu_x dx), p2 = fl(nu_y dy), r = rint(p1 + p2),
-//      f = fl(fl(p1 - r) + p2); p1 - r is exact (both are multiples of
-//      ulp(p1) and |p1 - r| <= |p2| + 1/2), so the only phase errors are the
-//      two product roundings, at most ulp(32)/2 = 2^-19 turns each.
+//      f = fl(fl(p1 - r) + p2).  Errors: the two product roundings (at most
+//      2^-20 turns each) and the rounding of p1 - r when |p1 - r| outgrows
+//      |p1| (at most ulp(32.5)/2 = 2^-19 turns); about 4e-6 turns (2.5e-5
+//      rad) in the worst case, far less on average.
 //    Exact reduction (points far from their tile centre, e.g. outside the
-//      map): the product errors e1, e2 are recovered with FMA (TwoProduct)
-//      and added after the reduction, leaving an error of about 2^-24 turns.
+//      map): each product is reduced on its own, f_i = p_i - rint(p_i), which
+//      is exact; the product errors e_i = nu d - p_i are recovered with FMA
+//      (TwoProduct); g = (f1 + f2) + (e1 + e2) is reduced once more to
+//      [-1/2, 1/2].  The phase error is about 2^-24 turns.
 template <int KPT, bool EXACT>
 __device__ __forceinline__ void encode_points(const float2 *sp, int len, const float (&nx)[KPT],
                                               const float (&ny)[KPT], float (&ar)[KPT],
@@ -258,12 +262,17 @@ __device__ __forceinline__ void encode_points(const float2 *sp, int len, const f
         for (int j = 0; j < KPT; ++j) {
             float p1 = __fmul_rn(nx[j], q.x);
             float p2 = __fmul_rn(ny[j], q.y);
-            float r = __fsub_rn(__fadd_rn(__fadd_rn(p1, p2), kMagic), kMagic);
-            float f = __fadd_rn(__fsub_rn(p1, r), p2);
+            float f;
             if (EXACT) {
                 float e1 = fmaf(nx[j], q.x, -p1);
                 float e2 = fmaf(ny[j], q.y, -p2);
-                f = __fadd_rn(f, __fadd_rn(e1, e2));
+                float f1 = __fsub_rn(p1, __fsub_rn(__fadd_rn(p1, kMagic), kMagic));
+                float f2 = __fsub_rn(p2, __fsub_rn(__fadd_rn(p2, kMagic), kMagic));
+                float g = __fadd_rn(__fadd_rn(f1, f2), __fadd_rn(e1, e2));
+                f = __fsub_rn(g, __fsub_rn(__fadd_rn(g, kMagic), kMagic));
+            } else {
+                float r = __fsub_rn(__fadd_rn(__fadd_rn(p1, p2), kMagic), kMagic);
+                f = __fadd_rn(__fsub_rn(p1, r), p2);
             }
             float s, co;
             __sincosf(__fmul_rn(f, kTwoPi), &s, &co);
@@ -337,6 +346,155 @@ __global__ void __launch_bounds__(256) encode_chunk_kernel(const float2 *__restr
     }
 }
 
+// 5'. The same encode + bundle with packed FP32 pairs (two frequencies per
+//     instruction) and part of the unit phasors evaluated on the FMA pipe.
+//     Of the NP frequency pairs a thread holds, NPOLY pairs use
+//     exp(i 2 pi f) = (exp(i pi f))^2 with exp(i pi f) from its Taylor series
+//     on |pi f| <= pi/2 (sin to x^11, cos to x^12: truncation below 6e-8),
+//     squared as a complex number; the other pairs use MUFU sin/cos.  The
+//     phase reduction is the one of encode_points, lane by lane.
+__device__ __forceinline__ sm100::f32x2 neg2(sm100::f32x2 a) { return a ^ 0x8000000080000000ull; }
+
+template <int NP, int NPOLY, bool EXACT>
+__device__ __forceinline__ void encode_points_x2(const float2 *sp, int len,
+                                                 const sm100::f32x2 (&nx)[NP],
+                                                 const sm100::f32x2 (&ny)[NP],
+                                                 sm100::f32x2 (&ac)[NP], sm100::f32x2 (&as)[NP])
+{
+    using namespace sm100;
+    const f32x2 kM = pack2(12582912.0f, 12582912.0f);
+    const f32x2 kTwoPi = pack2(6.28318530717958647692f, 6.28318530717958647692f);
+    const f32x2 kPi = pack2(3.14159265358979323846f, 3.14159265358979323846f);
+    const f32x2 kOne = pack2(1.0f, 1.0f);
+    // Taylor coefficients: sin x = x sum (-1)^n x^2n / (2n+1)!, cos x = sum (-1)^n x^2n / (2n)!
+    const f32x2 s3 = pack2(-1.0f / 6.0f, -1.0f / 6.0f), s5 = pack2(1.0f / 120.0f, 1.0f / 120.0f);
+    const f32x2 s7 = pack2(-1.0f / 5040.0f, -1.0f / 5040.0f);
+    const f32x2 s9 = pack2(1.0f / 362880.0f, 1.0f / 362880.0f);
+    const f32x2 s11 = pack2(-1.0f / 39916800.0f, -1.0f / 39916800.0f);
+    const f32x2 c2 = pack2(-0.5f, -0.5f), c4 = pack2(1.0f / 24.0f, 1.0f / 24.0f);
+    const f32x2 c6 = pack2(-1.0f / 720.0f, -1.0f / 720.0f);
+    const f32x2 c8 = pack2(1.0f / 40320.0f, 1.0f / 40320.0f);
+    const f32x2 c10 = pack2(-1.0f / 3628800.0f, -1.0f / 3628800.0f);
+    const f32x2 c12 = pack2(1.0f / 479001600.0f, 1.0f / 479001600.0f);
+#pragma unroll 2
+    for (int p = 0; p < len; ++p) {
+        const float2 q = sp[p];
+        const f32x2 qx = pack2(q.x, q.x), qy = pack2(q.y, q.y);
+#pragma unroll
+        for (int j = 0; j < NP; ++j) {
+            f32x2 p1 = mul2(nx[j], qx), p2 = mul2(ny[j], qy);
+            f32x2 f;
+            if (EXACT) {
+                f32x2 e1 = fma2(nx[j], qx, neg2(p1));
+                f32x2 e2 = fma2(ny[j], qy, neg2(p2));
+                f32x2 f1 = sub2(p1, sub2(add2(p1, kM), kM));
+                f32x2 f2 = sub2(p2, sub2(add2(p2, kM), kM));
+                f32x2 g = add2(add2(f1, f2), add2(e1, e2));
+                f = sub2(g, sub2(add2(g, kM), kM));
+            } else {
+                f32x2 r = sub2(add2(add2(p1, p2), kM), kM);
+                f = add2(sub2(p1, r), p2);
+            }
+            f32x2 cr, si;
+            if (j < NPOLY) {
+                f32x2 x = mul2(f, kPi), x2 = mul2(x, x);
+                f32x2 s = fma2(x2, s11, s9);
+                s = fma2(x2, s, s7);
+                s = fma2(x2, s, s5);
+                s = fma2(x2, s, s3);
+                s = fma2(x2, s, kOne);
+                s = mul2(s, x);
+                f32x2 c = fma2(x2, c12, c10);
+                c = fma2(x2, c, c8);
+                c = fma2(x2, c, c6);
+                c = fma2(x2, c, c4);
+                c = fma2(x2, c, c2);
+                c = fma2(x2, c, kOne);
+                cr = mul2(sub2(c, s), add2(c, s));  // cos 2x = (c - s)(c + s)
+                si = mul2(add2(c, c), s);           // sin 2x = 2 c s
+            } else {
+                float2 a = unpack2(mul2(f, kTwoPi));
+                float s0, c0, s1, c1;
+                __sincosf(a.x, &s0, &c0);
+                __sincosf(a.y, &s1, &c1);
+                cr = pack2(c0, c1);
+                si = pack2(s0, s1);
+            }
+            ac[j] = add2(ac[j], cr);
+            as[j] = add2(as[j], si);
+        }
+    }
+}
+
+template <int NP, int NPOLY, bool ATOMIC>
+__global__ void __launch_bounds__(256) encode_chunk_x2_kernel(const float2 *__restrict__ pts,
+                                                              const int4 *__restrict__ chunks,
+                                                              const int *__restrict__ n_chunks,
+                                                              const float *__restrict__ nu, int D,
+                                                              float nu_max_x, float nu_max_y,
+                                                              float2 *__restrict__ out)
+{
+    using namespace sm100;
+    __shared__ float2 sp[kMaxChunk];
+    __shared__ unsigned s_bound[2];
+    const int c = blockIdx.x;
+    if (c >= *n_chunks) return;
+    const int4 ch = chunks[c];
+    const int len = ch.z - ch.y;
+    const int kbase = blockIdx.y * (512 * NP) + threadIdx.x;
+    f32x2 nx[NP], ny[NP], ac[NP], as[NP];
+#pragma unroll
+    for (int j = 0; j < NP; ++j) {
+        int k0 = kbase + (2 * j) * 256, k1 = k0 + 256;
+        nx[j] = pack2(k0 < D ? nu[k0] : 0.f, k1 < D ? nu[k1] : 0.f);
+        ny[j] = pack2(k0 < D ? nu[D + k0] : 0.f, k1 < D ? nu[D + k1] : 0.f);
+        ac[j] = pack2(0.f, 0.f);
+        as[j] = pack2(0.f, 0.f);
+    }
+    if (threadIdx.x < 2) s_bound[threadIdx.x] = 0u;
+    __syncthreads();
+    float mx = 0.f, my = 0.f;
+    for (int i = threadIdx.x; i < len; i += blockDim.x) {
+        float2 q = pts[ch.y + i];
+        sp[i] = q;
+        mx = fmaxf(mx, fabsf(q.x));
+        my = fmaxf(my, fabsf(q.y));
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        my = fmaxf(my, __shfl_xor_sync(0xffffffffu, my, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicMax(&s_bound[0], __float_as_uint(mx));
+        atomicMax(&s_bound[1], __float_as_uint(my));
+    }
+    __syncthreads();
+    const bool fast = __uint_as_float(s_bound[0]) * nu_max_x < 32.0f &&
+                      __uint_as_float(s_bound[1]) * nu_max_y < 32.0f;
+    if (fast)
+        encode_points_x2<NP, NPOLY, false>(sp, len, nx, ny, ac, as);
+    else
+        encode_points_x2<NP, NPOLY, true>(sp, len, nx, ny, ac, as);
+#pragma unroll
+    for (int j = 0; j < NP; ++j) {
+        const float2 cr = unpack2(ac[j]), si = unpack2(as[j]);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            int k = kbase + (2 * j + h) * 256;
+            float re = h ? cr.y : cr.x, im = h ? si.y : si.x;
+            if (k < D) {
+                if (ATOMIC) {
+                    float2 *w = out + (size_t)ch.x * D + k;
+                    atomicAdd(&w->x, re);
+                    atomicAdd(&w->y, im);
+                } else {
+                    out[(size_t)c * D + k] = make_float2(re, im);
+                }
+            }
+        }
+    }
+}
+
 // 6. omega[s][k] += sum of the partial memories of segment s, in chunk order.
 __global__ void __launch_bounds__(256) reduce_partials_kernel(const float2 *__restrict__ partial,
                                                               const int *__restrict__ cbeg, int D,
@@ -355,6 +513,42 @@ __global__ void __launch_bounds__(256) reduce_partials_kernel(const float2 *__re
     }
     float2 w = omega[(size_t)s * D + k];
     omega[(size_t)s * D + k] = make_float2(w.x + sr, w.y + si);
+}
+
+template <int NP, int NPOLY>
+cudaError_t launch_x2(const vsaogm_map *m, const float2 *pts, const int4 *chunks,
+                      const int *n_chunks, float2 *out, int max_chunks, bool atomic,
+                      cudaStream_t st)
+{
+    const int D = m->cfg.D;
+    dim3 grid(max_chunks, (D + 512 * NP - 1) / (512 * NP));
+    if (atomic)
+        encode_chunk_x2_kernel<NP, NPOLY, true><<<grid, 256, 0, st>>>(
+            pts, chunks, n_chunks, m->nu, D, m->nu_max[0], m->nu_max[1], out);
+    else
+        encode_chunk_x2_kernel<NP, NPOLY, false><<<grid, 256, 0, st>>>(
+            pts, chunks, n_chunks, m->nu, D, m->nu_max[0], m->nu_max[1], out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_packed(const vsaogm_map *m, int np, const float2 *pts, const int4 *chunks,
+                          const int *n_chunks, float2 *out, int max_chunks, bool atomic,
+                          cudaStream_t st)
+{
+    const int npoly = std::min(m->encode_poly_pairs, np);
+    if (np == 4) {
+        switch (npoly) {
+            case 0: return launch_x2<4, 0>(m, pts, chunks, n_chunks, out, max_chunks, atomic, st);
+            case 1: return launch_x2<4, 1>(m, pts, chunks, n_chunks, out, max_chunks, atomic, st);
+            case 2: return launch_x2<4, 2>(m, pts, chunks, n_chunks, out, max_chunks, atomic, st);
+            default: return launch_x2<4, 3>(m, pts, chunks, n_chunks, out, max_chunks, atomic, st);
+        }
+    }
+    switch (npoly) {
+        case 0: return launch_x2<2, 0>(m, pts, chunks, n_chunks, out, max_chunks, atomic, st);
+        case 1: return launch_x2<2, 1>(m, pts, chunks, n_chunks, out, max_chunks, atomic, st);
+        default: return launch_x2<2, 2>(m, pts, chunks, n_chunks, out, max_chunks, atomic, st);
+    }
 }
 
 template <int KPT>
@@ -376,9 +570,12 @@ cudaError_t launch_encode(const vsaogm_map *m, const float2 *pts, const int4 *ch
 }  // namespace
 
 // Frequencies per thread and points per chunk for a batch of n points.
-static void encode_shape(int64_t n, int D, int *kpt, int *chunk)
+static void encode_shape(const vsaogm_map *m, int64_t n, int D, int *kpt, int *chunk)
 {
-    *kpt = D >= 4096 ? 4 : (D >= 2048 ? 2 : 1);
+    if (m->encode_packed)
+        *kpt = D >= 4096 ? 8 : 4;
+    else
+        *kpt = D >= 4096 ? 4 : (D >= 2048 ? 2 : 1);
     int64_t slices = (D + 256 * *kpt - 1) / (256 * *kpt);
     int64_t target = 152 * 8 * 4;  // about four waves of 8 CTAs per SM
     int64_t c = std::max<int64_t>(1, n * slices / target);
@@ -394,7 +591,7 @@ int encode_bundle(vsaogm_map *m, const float *xy_f, const uint8_t *lab, int64_t 
     const int S = m->S, S1 = S + 1, D = m->cfg.D;
     const bool atomic = (m->cfg.flags & VSAOGM_FLAG_ATOMIC) != 0;
     int kpt, chunk;
-    encode_shape(n, D, &kpt, &chunk);
+    encode_shape(m, n, D, &kpt, &chunk);
     const int nb = (n + kSortBlock - 1) / kSortBlock;
     const int max_chunks = (n + chunk - 1) / chunk + S;
     int rc;
@@ -431,7 +628,9 @@ int encode_bundle(vsaogm_map *m, const float *xy_f, const uint8_t *lab, int64_t 
     float2 *out = atomic ? m->omega : (float2 *)m->ws.partial.ptr;
     {
         StageScope sc(m, VSAOGM_STAGE_ENCODE, st);
-        if (kpt == 4)
+        if (m->encode_packed)
+            e = launch_packed(m, kpt / 2, sorted, chunks, n_chunks, out, max_chunks, atomic, st);
+        else if (kpt == 4)
             e = launch_encode<4>(m, sorted, chunks, n_chunks, out, max_chunks, atomic, st);
         else if (kpt == 2)
             e = launch_encode<2>(m, sorted, chunks, n_chunks, out, max_chunks, atomic, st);

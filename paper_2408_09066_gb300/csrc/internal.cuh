@@ -83,6 +83,8 @@ struct vsaogm_map {
     // device state owned by the map
     float *nu;                   // [2][D]: nu_x then nu_y, cycles per metre
     float nu_max[2];             // max_k |nu_x[k]|, max_k |nu_y[k]|
+    int encode_packed;           // 1: f32x2 encode kernel, 0: scalar kernel
+    int encode_poly_pairs;       // frequency pairs per thread on the FMA-pipe polynomial
     float2 *omega;               // [S][D]
     float *inv_norm;             // [S]: 1 / ||omega||, 0 for an all-zero memory
     unsigned *maxima;            // [2]: order-preserving encoding of max P per class

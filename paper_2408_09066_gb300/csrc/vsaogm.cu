@@ -309,6 +309,12 @@ int vsaogm_create(const vsaogm_config *cfg, vsaogm_map **out)
             m->nu_max[0] = std::max(m->nu_max[0], std::fabs(m->host_nu[k]));
             m->nu_max[1] = std::max(m->nu_max[1], std::fabs(m->host_nu[D + k]));
         }
+        // encode kernel family (tuning overrides through the environment)
+        m->encode_packed = 0;
+        m->encode_poly_pairs = 0;
+        if (const char *v = getenv("VSAOGM_ENCODE_PACKED")) m->encode_packed = atoi(v) != 0;
+        if (const char *v = getenv("VSAOGM_ENCODE_POLY"))
+            m->encode_poly_pairs = std::max(0, std::min(3, atoi(v)));
         std::vector<float> nu(m->host_nu, m->host_nu + 2 * (size_t)D);
         if ((rc = upload(&m->nu, nu))) break;
         // Tiling and cell tables (Sec. III-B3, Algorithm 1).

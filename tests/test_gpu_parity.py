@@ -1,7 +1,11 @@
 """Parity of the CUDA path (through the C ABI) with the FP64 oracle.
 
 Tolerances (normwise error = max|gpu - oracle| / max|oracle|):
-  * memories omega (FP32 accumulation of unit phasors): 1e-5;
+  * memories omega: 3e-5.  Each phasor carries at most 2.5e-5 rad of phase
+    error from the kernel's fast phase reduction (|nu . offset| < 32 turns;
+    far points take an exact reduction, about 4e-7 rad) plus about 4e-7 from
+    MUFU sin/cos; a memory of one point is a single phasor, so the bound is
+    reached there, while sums of many phasors average it down;
   * quasi-probabilities P and P_hat of the FP32 decode: 1e-4;
   * occupancy Pr(psi = 1) and OGM: 1e-3 absolute (the entropy sums up to
     |disk| terms -P_hat ln P_hat whose slope grows like |ln P_hat|, so the
@@ -21,7 +25,7 @@ from paper_2408_09066_gb300 import vsaogm as V
 
 pytestmark = pytest.mark.gpu
 
-TOL_OMEGA = 1e-5
+TOL_OMEGA = 3e-5
 TOL_HEAT = 1e-4
 TOL_PR = 1e-3
 
@@ -110,8 +114,25 @@ def test_single_point_phasors_anywhere(x, y):
     err = np.abs(got["omega"] - want["omega"]).max(0)
     k = int(np.argmax(err))
     nx, ny = want["nu"]
-    assert err[k] <= 2e-6, (f"k {k}: nu ({nx[k]}, {ny[k]}) got {got['omega'][:, k]} "
-                            f"want {want['omega'][:, k]}")
+    far = max(abs(x), abs(y)) > 10.0  # exact reduction; near points take the fast one
+    tol = 2e-6 if far else TOL_OMEGA
+    assert err[k] <= tol, (f"k {k}: nu ({nx[k]}, {ny[k]}) got {got['omega'][:, k]} "
+                           f"want {want['omega'][:, k]}")
+
+
+@pytest.mark.parametrize("poly", [0, 1, 2, 3])
+@pytest.mark.parametrize("D", [1000, 8192])
+def test_packed_encode_variants(monkeypatch, poly, D):
+    """The f32x2 encode kernel with 0..3 frequency pairs per thread on the FMA-pipe
+    polynomial matches the oracle like the scalar kernel, near and far points."""
+    monkeypatch.setenv("VSAOGM_ENCODE_PACKED", "1")
+    monkeypatch.setenv("VSAOGM_ENCODE_POLY", str(poly))
+    wl = synth.small_scan(seed=31, D=D)
+    far = np.array([[-100.0, 50.0], [40.0, -3.0]], np.float32)
+    xy = np.concatenate([wl.xy, far])
+    lab = np.concatenate([wl.labels, np.array([0, 1], np.uint8)])
+    cfg = config_for(wl)
+    _check_all(cfg, run_gpu(cfg, xy, lab), _oracle_all(cfg, xy, lab))
 
 
 def test_empty_input_and_single_class():
