@@ -114,6 +114,29 @@ int vsaogm_reset(vsaogm_map *map, void *stream);
 int vsaogm_encode_bundle(vsaogm_map *map, const float *xy_dev, const uint8_t *labels_dev,
                          int64_t n, void *stream);
 
+/* Encoding and bundling without any allocation (the paper has no counterpart;
+ * this is a service of the library).  Same inputs, outputs and result as
+ * vsaogm_encode_bundle, within its tolerance, but the call never calls
+ * cudaMalloc, cudaFree or any other allocating routine.  It is meant for
+ * callers that must not allocate device memory: a real-time control loop, for
+ * which cudaMalloc can synchronise the whole device and stall for
+ * milliseconds, or a host process that runs under a fixed device-memory budget
+ * owned by another allocator.  Map creation still allocates; do that at
+ * set-up time.
+ * Scratch lives in one static 4 MiB device array inside the library, which
+ * every GPU that loads the library keeps until the process exits.  The first
+ * call on each device looks up that array's device address
+ * (cudaGetSymbolAddress) with the device current, so make the first call
+ * before any stream capture.  All calls share the array: calls whose work
+ * overlaps on the GPU (different streams, or different maps at the same
+ * time) race and give wrong results; order them on one stream.  Bundling adds
+ * into the memories with atomics, so the result is not bitwise reproducible.
+ * Limits: n <= 262144 points per call (E_INVAL above, before any GPU work);
+ * the map's device must be current.  No stage timing is recorded.
+ * Errors: E_INVAL, E_CUDA.                                                  */
+int vsaogm_encode_bundle_noalloc(vsaogm_map *map, const float *xy_dev,
+                                 const uint8_t *labels_dev, int64_t n, void *stream);
+
 /* Decoding (Eqs. vector-normalization, loc-query, non-linearities):
  * heat_dev (float [2][H][W]) receives P_hat(psi | cell) =
  * (P / max_map P)^2 with P = Re sum_k conj(w_k) phi_k(cell) / ||w|| for the

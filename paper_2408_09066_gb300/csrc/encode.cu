@@ -19,9 +19,18 @@
 //                     VSAOGM_FLAG_ATOMIC step 5 adds into the memories with
 //                     atomics instead and step 6 is skipped.
 #include <algorithm>
+#include <mutex>
 
 #include "internal.cuh"
 #include "sm100.cuh"
+
+// Scratch of vsaogm_encode_bundle_noalloc: a fixed device array, so that the
+// call needs no allocation.  Every device that loads the library holds it
+// until the process exits.  In host code this name is only a stand-in for the
+// array; kernels receive the device address obtained with
+// cudaGetSymbolAddress (see noalloc_scratch below).
+static constexpr size_t kNoAllocScratchBytes = 4u << 20;  // 4 MiB
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 
 namespace vsaogm_impl {
 namespace {
@@ -650,4 +659,102 @@ int encode_bundle(vsaogm_map *m, const float *xy_f, const uint8_t *lab, int64_t 
     return VSAOGM_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Allocation-free encode + bundle (vsaogm_encode_bundle_noalloc).
+// ---------------------------------------------------------------------------
+constexpr int kNoAllocMaxPoints = 1 << 18;
+constexpr int kNoAllocMaxDevices = 64;
+
+// Device address of g_noalloc_scratch on the current device, looked up once
+// per device (with that device current) and cached.
+static int noalloc_scratch(int device, unsigned char **out)
+{
+    static std::mutex mu;
+    static unsigned char *addr[kNoAllocMaxDevices] = {};
+    if (device < 0 || device >= kNoAllocMaxDevices)
+        return set_error(VSAOGM_E_INVAL, "device %d out of range for the static scratch", device);
+    std::lock_guard<std::mutex> lock(mu);
+    if (!addr[device]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return cuda_error(e, "encode_noalloc: scratch address");
+        addr[device] = (unsigned char *)p;
+    }
+    *out = addr[device];
+    return VSAOGM_OK;
+}
+
+static size_t align256(size_t b) { return (b + 255) / 256 * 256; }
+
+static int encode_bundle_noalloc(vsaogm_map *m, const float *xy_f, const uint8_t *lab, int n,
+                                 cudaStream_t st)
+{
+    const int S = m->S, S1 = S + 1, D = m->cfg.D;
+    int kpt, chunk;
+    encode_shape(m, n, D, &kpt, &chunk);
+    const int nb = (n + kSortBlock - 1) / kSortBlock;
+    const int max_chunks = (n + chunk - 1) / chunk + S;
+    const size_t b_hist = align256(sizeof(int) * (size_t)nb * S1);
+    const size_t b_meta = align256(sizeof(int) * (size_t)(3 * S1 + 2));
+    const size_t b_chunks = align256(sizeof(int4) * (size_t)max_chunks);
+    const size_t b_sorted = align256(sizeof(float2) * (size_t)n);
+    if (b_hist + b_meta + b_chunks + b_sorted > kNoAllocScratchBytes)
+        return set_error(VSAOGM_E_INVAL,
+                         "encode_noalloc: %d points need %zu bytes of scratch, more than the "
+                         "static %zu",
+                         n, b_hist + b_meta + b_chunks + b_sorted, kNoAllocScratchBytes);
+    int device = -1;
+    cudaError_t e = cudaGetDevice(&device);
+    if (e != cudaSuccess) return cuda_error(e, "encode_noalloc");
+    if (device != m->device)
+        return set_error(VSAOGM_E_INVAL, "encode_noalloc: the map's device is not current");
+    unsigned char *base = nullptr;
+    int rc = noalloc_scratch(device, &base);
+    if (rc) return rc;
+    int *hist = (int *)base;
+    int *meta = (int *)(base + b_hist);
+    int4 *chunks = (int4 *)(base + b_hist + b_meta);
+    float2 *sorted = (float2 *)(base + b_hist + b_meta + b_chunks);
+    const float2 *xy = (const float2 *)xy_f;
+    AxisDev ax = axis_x(m), ay = axis_y(m);
+    const size_t smem_scatter = sizeof(int) * kSortWarps * S1;
+    if ((e = cudaFuncSetAttribute(seg_scatter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)smem_scatter)) != cudaSuccess)
+        return cuda_error(e, "encode_noalloc: shared memory");
+    // Every scratch word these kernels read is written earlier in the same call
+    // (histograms, offsets, chunk table, sorted points), so nothing has to be
+    // cleared; bundling adds straight into the map's memories with atomics.
+    seg_count_kernel<<<nb, 256, sizeof(int) * S1, st>>>(xy, lab, n, ax, ay, S, hist);
+    seg_scan_kernel<<<S1, kScanThreads, 0, st>>>(hist, nb, S1, meta);
+    seg_meta_kernel<<<1, kScanThreads, 0, st>>>(meta, S, chunk, chunks, m->rejected);
+    seg_scatter_kernel<<<nb, 256, smem_scatter, st>>>(xy, lab, n, ax, ay, S, hist, meta, sorted);
+    const int *n_chunks = meta + S1 + S1 + 1 + S + 1;
+    if (m->encode_packed)
+        e = launch_packed(m, kpt / 2, sorted, chunks, n_chunks, m->omega, max_chunks, true, st);
+    else if (kpt == 4)
+        e = launch_encode<4>(m, sorted, chunks, n_chunks, m->omega, max_chunks, true, st);
+    else if (kpt == 2)
+        e = launch_encode<2>(m, sorted, chunks, n_chunks, m->omega, max_chunks, true, st);
+    else
+        e = launch_encode<1>(m, sorted, chunks, n_chunks, m->omega, max_chunks, true, st);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_error(e, "encode_noalloc");
+    return VSAOGM_OK;
+}
+
 }  // namespace vsaogm_impl
+
+extern "C" int vsaogm_encode_bundle_noalloc(vsaogm_map *m, const float *xy, const uint8_t *lab,
+                                            int64_t n, void *stream)
+{
+    using namespace vsaogm_impl;
+    if (!m) return set_error(VSAOGM_E_INVAL, "map is NULL");
+    if (n < 0) return set_error(VSAOGM_E_INVAL, "n must be >= 0");
+    if (n == 0) return VSAOGM_OK;
+    if (n > kNoAllocMaxPoints)
+        return set_error(VSAOGM_E_INVAL, "encode_noalloc: n = %lld exceeds the maximum of %d points",
+                         (long long)n, kNoAllocMaxPoints);
+    if (!xy || !lab) return set_error(VSAOGM_E_INVAL, "xy and labels must not be NULL");
+    if ((uintptr_t)xy % 8 != 0) return set_error(VSAOGM_E_INVAL, "xy must be 8-byte aligned");
+    return encode_bundle_noalloc(m, xy, lab, (int)n, (cudaStream_t)stream);
+}

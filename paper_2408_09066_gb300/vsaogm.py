@@ -47,6 +47,7 @@ _SIGNATURES = {
     "vsaogm_destroy": (ctypes.c_int, [_V]),
     "vsaogm_reset": (ctypes.c_int, [_V, _V]),
     "vsaogm_encode_bundle": (ctypes.c_int, [_V, _V, _V, ctypes.c_int64, _V]),
+    "vsaogm_encode_bundle_noalloc": (ctypes.c_int, [_V, _V, _V, ctypes.c_int64, _V]),
     "vsaogm_decode": (ctypes.c_int, [_V, _V, _V]),
     "vsaogm_entropy": (ctypes.c_int, [_V, _V, _V, _V, _V, _V]),
     "vsaogm_query": (ctypes.c_int, [_V, _V, _V, _V, _V, _V]),
@@ -162,6 +163,15 @@ class Map:
         _check(lib().vsaogm_encode_bundle(self._h, _dev(xy, torch.float32, (n, 2), "xy"),
                                           _dev(labels, torch.uint8, (n,), "labels"), n,
                                           _stream(stream)))
+
+    def encode_bundle_noalloc(self, xy, labels, stream=None):
+        """Like encode_bundle, without allocating (static library scratch; at
+        most 262144 points per call; calls must not overlap on the GPU)."""
+        import torch
+        n = labels.shape[0]
+        _check(lib().vsaogm_encode_bundle_noalloc(self._h, _dev(xy, torch.float32, (n, 2), "xy"),
+                                                  _dev(labels, torch.uint8, (n,), "labels"), n,
+                                                  _stream(stream)))
 
     def decode(self, heat, stream=None):
         import torch
