@@ -21,6 +21,7 @@ import dataclasses
 import os
 import subprocess
 import threading
+from fractions import Fraction
 
 import numpy as np
 
@@ -92,19 +93,20 @@ def _load():
             lib.orc_memories.argtypes = [P(_Grid), ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
                                          ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
                                          ctypes.c_int32, ctypes.c_void_p, ctypes.c_int32,
-                                         ctypes.c_void_p]
+                                         ctypes.c_void_p, ctypes.c_void_p]
             lib.orc_norms.argtypes = [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32,
                                       ctypes.c_void_p]
             lib.orc_decode_cells.argtypes = [P(_Grid), ctypes.c_int32, ctypes.c_void_p,
                                              ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
-                                             ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]
+                                             ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
+                                             ctypes.c_void_p]
             lib.orc_decode_map.argtypes = [P(_Grid), ctypes.c_int32, ctypes.c_void_p,
                                            ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
-                                           ctypes.c_void_p]
+                                           ctypes.c_void_p, ctypes.c_void_p]
             lib.orc_direct_cells.argtypes = [P(_Grid), ctypes.c_int32, ctypes.c_void_p,
                                              ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                              ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64,
-                                             ctypes.c_void_p]
+                                             ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
             lib.orc_nonlinear.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
                                           ctypes.c_void_p]
             lib.orc_entropy.argtypes = [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32,
@@ -157,10 +159,62 @@ def tile_centre(g: Grid, beta: int):
     return cx.value, cy.value
 
 
+def _exact_tile(g: Grid, x: Fraction, y: Fraction) -> int:
+    """Algorithm 1's argmin of the L2 distance in exact rational arithmetic."""
+    tw = Fraction(g.W) * Fraction(g.res) / g.tiles_x
+    th = Fraction(g.H) * Fraction(g.res) / g.tiles_y
+    best, bd = 0, None
+    for by in range(g.tiles_y):
+        for bx in range(g.tiles_x):
+            cx = Fraction(g.x_min) + (bx + Fraction(1, 2)) * tw
+            cy = Fraction(g.y_min) + (by + Fraction(1, 2)) * th
+            d = (x - cx) ** 2 + (y - cy) ** 2
+            if bd is None or d < bd:
+                best, bd = by * g.tiles_x + bx, d
+    return best
+
+
+def _near_boundary(g: Grid, x: np.ndarray, y: np.ndarray) -> np.ndarray:
+    """Coordinates within 1e-9 (relative) of a line halfway between adjacent tile
+    centres, where rounding of FP64 distances could invert Algorithm 1's argmin."""
+    mask = np.zeros(len(x), bool)
+    for lo, cells, tiles, v in ((g.x_min, g.W, g.tiles_x, x), (g.y_min, g.H, g.tiles_y, y)):
+        t = cells * g.res / tiles
+        for a in range(1, tiles):
+            b = lo + a * t
+            mask |= np.abs(v - b) <= 1e-9 * max(1.0, abs(b), abs(t))
+    return mask
+
+
 def assign(g: Grid, xy: np.ndarray) -> np.ndarray:
+    """Algorithm 1: tile of each point.  FP64 distances decide, except for points
+    near a tile boundary, which are decided in exact rational arithmetic (FP64
+    rounding can make a point 1e-16 m off a boundary look like a tie)."""
     xy = np.ascontiguousarray(xy, np.float32).reshape(-1, 2)
     out = np.empty(len(xy), np.int32)
     _load().orc_assign(ctypes.byref(g.c()), _ptr(xy), len(xy), _ptr(out))
+    near = np.nonzero(_near_boundary(g, xy[:, 0].astype(np.float64), xy[:, 1].astype(np.float64)))[0]
+    for p in near:
+        out[p] = _exact_tile(g, Fraction(float(xy[p, 0])), Fraction(float(xy[p, 1])))
+    return out
+
+
+def assign_cells(g: Grid, cells: np.ndarray) -> np.ndarray:
+    """Tile of each cell (i, j): Algorithm 1's rule at the cell centre
+    (x_min + (i + 1/2) res, y_min + (j + 1/2) res), exact near boundaries."""
+    cells = np.ascontiguousarray(cells, np.int32).reshape(-1, 2)
+    out = np.empty(len(cells), np.int32)
+    cx = g.x_min + (cells[:, 0] + 0.5) * g.res
+    cy = g.y_min + (cells[:, 1] + 0.5) * g.res
+    lib = _load()
+    gc = g.c()
+    for q in range(len(cells)):
+        out[q] = lib.orc_tile_of(ctypes.byref(gc), float(cx[q]), float(cy[q]))
+    near = np.nonzero(_near_boundary(g, cx, cy))[0]
+    for q in near:
+        x = Fraction(g.x_min) + (int(cells[q, 0]) + Fraction(1, 2)) * Fraction(g.res)
+        y = Fraction(g.y_min) + (int(cells[q, 1]) + Fraction(1, 2)) * Fraction(g.res)
+        out[q] = _exact_tile(g, x, y)
     return out
 
 
@@ -177,8 +231,12 @@ def memories(g: Grid, nu_x, nu_y, xy, labels, frame: str = "tile", ks=None) -> n
         ks = np.ascontiguousarray(ks, np.int32)
         nk, kp = len(ks), _ptr(ks)
     out = np.empty((2 * g.T, nk, 2), np.float64)
+    if np.any(labels > 1):
+        raise ValueError("labels must be 0 or 1")
+    beta = assign(g, xy)
     rc = _load().orc_memories(ctypes.byref(g.c()), D, _ptr(nu_x), _ptr(nu_y), _ptr(xy),
-                              _ptr(labels), len(xy), _frame(frame), kp, nk, _ptr(out))
+                              _ptr(labels), len(xy), _frame(frame), kp, nk, _ptr(beta),
+                              _ptr(out))
     if rc != 0:
         raise ValueError("labels must be 0 or 1")
     return out[..., 0] + 1j * out[..., 1]
@@ -204,8 +262,14 @@ def decode_cells(g: Grid, nu_x, nu_y, omega, cells, frame: str = "tile") -> np.n
     _load().orc_decode_cells(ctypes.byref(g.c()), ri.shape[1],
                              _ptr(np.ascontiguousarray(nu_x, np.float32)),
                              _ptr(np.ascontiguousarray(nu_y, np.float32)), _ptr(ri),
-                             _frame(frame), _ptr(cells), len(cells), _ptr(out))
+                             _frame(frame), _ptr(cells), len(cells),
+                             _ptr(assign_cells(g, cells)), _ptr(out))
     return out
+
+
+def _all_cells(g: Grid) -> np.ndarray:
+    j, i = np.meshgrid(np.arange(g.H), np.arange(g.W), indexing="ij")
+    return np.ascontiguousarray(np.stack([i.ravel(), j.ravel()], 1), np.int32)
 
 
 def decode_map(g: Grid, nu_x, nu_y, omega, frame: str = "tile") -> np.ndarray:
@@ -215,7 +279,7 @@ def decode_map(g: Grid, nu_x, nu_y, omega, frame: str = "tile") -> np.ndarray:
     _load().orc_decode_map(ctypes.byref(g.c()), ri.shape[1],
                            _ptr(np.ascontiguousarray(nu_x, np.float32)),
                            _ptr(np.ascontiguousarray(nu_y, np.float32)), _ptr(ri),
-                           _frame(frame), _ptr(out))
+                           _frame(frame), _ptr(assign_cells(g, _all_cells(g))), _ptr(out))
     return out
 
 
@@ -228,7 +292,8 @@ def direct_cells(g: Grid, nu_x, nu_y, xy, labels, cells) -> np.ndarray:
     _load().orc_direct_cells(ctypes.byref(g.c()), len(nu_x),
                              _ptr(np.ascontiguousarray(nu_x, np.float32)),
                              _ptr(np.ascontiguousarray(nu_y, np.float32)), _ptr(xy),
-                             _ptr(labels), len(xy), _ptr(cells), len(cells), _ptr(out))
+                             _ptr(labels), len(xy), _ptr(cells), len(cells),
+                             _ptr(assign(g, xy)), _ptr(assign_cells(g, cells)), _ptr(out))
     return out
 
 
@@ -266,6 +331,27 @@ def classify_f32(ogm_f32: np.ndarray, rho: float) -> np.ndarray:
     out = np.empty(o.shape, np.uint8)
     _load().orc_classify_f32(_ptr(o), o.size, np.float32(rho), _ptr(out))
     return out
+
+
+def query_window(g: Grid, nu_x, nu_y, omega, x0: int, y0: int, w: int, h: int, r_occ: int,
+                 r_emp: int, frame: str = "tile") -> dict:
+    """A local map query (reading of the paper for windows): the window grown by
+    R = max(r_occ, r_emp) cells and clipped to the map is decoded (Eq. loc-query),
+    Eq. non-linearities normalises by the maximum over that region, Algorithm 2
+    runs on the region (zero outside it), then Eqs. softmax and psd.  Returns the
+    window's Pr(psi=1), OGM and the region's maxima."""
+    R = max(r_occ, r_emp)
+    rx0, ry0 = max(0, x0 - R), max(0, y0 - R)
+    rx1, ry1 = min(g.W, x0 + w + R), min(g.H, y0 + h + R)
+    jj, ii = np.meshgrid(np.arange(ry0, ry1), np.arange(rx0, rx1), indexing="ij")
+    cells = np.stack([ii.ravel(), jj.ravel()], 1)
+    P = decode_cells(g, nu_x, nu_y, omega, cells, frame).T.reshape(2, ry1 - ry0, rx1 - rx0)
+    Ph, mx = nonlinear(P)
+    H0 = entropy(Ph[0], r_emp)
+    H1 = entropy(Ph[1], r_occ)
+    pr1, pr0, ogm = softmax_psd(H0, H1)
+    sy, sx = slice(y0 - ry0, y0 - ry0 + h), slice(x0 - rx0, x0 - rx0 + w)
+    return dict(pr1=pr1[sy, sx], ogm=ogm[sy, sx], maxima=mx, P=P)
 
 
 def pipeline(g: Grid, nu_x, nu_y, xy, labels, r_occ: int, r_emp: int, rho: float = 0.0,

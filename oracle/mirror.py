@@ -39,7 +39,23 @@ def assign(g, xy):
     mu = centres(g)
     p = np.asarray(xy, np.float64).reshape(-1, 2)
     d2 = ((p[:, None, :] - mu[None, :, :]) ** 2).sum(-1)
-    return np.argmin(d2, axis=1)  # first minimum wins, as in Algorithm 1
+    beta = np.argmin(d2, axis=1)  # first minimum wins, as in Algorithm 1
+    # where the two smallest FP64 distances are (nearly) equal, rounding may have
+    # made the tie: decide those points with exact rational distances
+    srt = np.sort(d2, axis=1)
+    close = np.nonzero(srt[:, 1] - srt[:, 0] <= 1e-9 * np.maximum(srt[:, 1], 1e-300))[0] \
+        if d2.shape[1] > 1 else []
+    if len(close):
+        from fractions import Fraction as F
+        tw = F(g.W) * F(g.res) / g.tiles_x
+        th = F(g.H) * F(g.res) / g.tiles_y
+        cen = [(F(g.x_min) + (bx + F(1, 2)) * tw, F(g.y_min) + (by + F(1, 2)) * th)
+               for by in range(g.tiles_y) for bx in range(g.tiles_x)]
+        for q in close:
+            x, y = F(float(p[q, 0])), F(float(p[q, 1]))
+            d = [(x - cx) ** 2 + (y - cy) ** 2 for cx, cy in cen]
+            beta[q] = d.index(min(d))
+    return beta
 
 
 def memories(g, nu_x, nu_y, xy, labels, frame="tile"):

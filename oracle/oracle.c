@@ -125,14 +125,18 @@ void orc_assign(const orc_grid *g, const float *xy, int64_t n, int32_t *beta)
  * output then has layout [2T][nk][2].  Returns -1 on a label outside {0,1}. */
 int32_t orc_memories(const orc_grid *g, int32_t D, const float *nu_x, const float *nu_y,
                      const float *xy, const uint8_t *labels, int64_t n, int32_t frame,
-                     const int32_t *ks, int32_t nk, double *omega)
+                     const int32_t *ks, int32_t nk, const int32_t *beta_in, double *omega)
 {
     int32_t T = g->tiles_x * g->tiles_y;
     if (ks == NULL) nk = D;
     for (int64_t p = 0; p < n; ++p)
         if (labels[p] > 1) return -1;
     int32_t *beta = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
-    orc_assign(g, xy, n, beta);
+    /* beta_in: the caller's exact tile assignment (see oracle.assign); else FP64 argmin */
+    if (beta_in)
+        memcpy(beta, beta_in, sizeof(int32_t) * (size_t)n);
+    else
+        orc_assign(g, xy, n, beta);
     memset(omega, 0, sizeof(double) * (size_t)2 * T * nk * 2);
 #pragma omp parallel for schedule(static)
     for (int32_t q = 0; q < nk; ++q) {
@@ -176,7 +180,7 @@ void orc_norms(const double *omega, int32_t nmem, int32_t D, double *norms)
  * the frame the memories were built in.                                      */
 void orc_decode_cells(const orc_grid *g, int32_t D, const float *nu_x, const float *nu_y,
                       const double *omega, int32_t frame, const int32_t *cells, int64_t ncells,
-                      double *P)
+                      const int32_t *beta_cells, double *P)
 {
     int32_t T = g->tiles_x * g->tiles_y;
     double *norms = (double *)malloc(sizeof(double) * 2 * T);
@@ -185,7 +189,7 @@ void orc_decode_cells(const orc_grid *g, int32_t D, const float *nu_x, const flo
     for (int64_t c = 0; c < ncells; ++c) {
         double x = g->x_min + ((double)cells[2 * c] + 0.5) * g->res;
         double y = g->y_min + ((double)cells[2 * c + 1] + 0.5) * g->res;
-        int32_t beta = orc_tile_of(g, x, y);
+        int32_t beta = beta_cells ? beta_cells[c] : orc_tile_of(g, x, y);
         if (frame == 1) {
             double cx, cy;
             orc_tile_centre(g, beta, &cx, &cy);
@@ -207,9 +211,10 @@ void orc_decode_cells(const orc_grid *g, int32_t D, const float *nu_x, const flo
     free(norms);
 }
 
-/* The whole map: P has layout [2][H][W] (class, row j, column i). */
+/* The whole map: P has layout [2][H][W] (class, row j, column i).  beta_cells
+ * (nullable) gives the tile of each cell in the same row-major order.      */
 void orc_decode_map(const orc_grid *g, int32_t D, const float *nu_x, const float *nu_y,
-                    const double *omega, int32_t frame, double *P)
+                    const double *omega, int32_t frame, const int32_t *beta_cells, double *P)
 {
     int64_t nc = (int64_t)g->W * g->H;
     int32_t *cells = (int32_t *)malloc(sizeof(int32_t) * 2 * (size_t)nc);
@@ -218,7 +223,7 @@ void orc_decode_map(const orc_grid *g, int32_t D, const float *nu_x, const float
         cells[2 * c] = (int32_t)(c % g->W);
         cells[2 * c + 1] = (int32_t)(c / g->W);
     }
-    orc_decode_cells(g, D, nu_x, nu_y, omega, frame, cells, nc, tmp);
+    orc_decode_cells(g, D, nu_x, nu_y, omega, frame, cells, nc, beta_cells, tmp);
     for (int64_t c = 0; c < nc; ++c) {
         P[c] = tmp[2 * c];
         P[nc + c] = tmp[2 * c + 1];
@@ -234,12 +239,16 @@ void orc_decode_map(const orc_grid *g, int32_t D, const float *nu_x, const float
  * the frame.  Cost is O(n^2 D): tiny inputs only.                          */
 void orc_direct_cells(const orc_grid *g, int32_t D, const float *nu_x, const float *nu_y,
                       const float *xy, const uint8_t *labels, int64_t n,
-                      const int32_t *cells, int64_t ncells, double *P)
+                      const int32_t *cells, int64_t ncells, const int32_t *beta_in,
+                      const int32_t *beta_cells, double *P)
 {
     int32_t T = g->tiles_x * g->tiles_y;
     int32_t *beta = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
     double *norm2 = (double *)calloc((size_t)2 * T, sizeof(double));
-    orc_assign(g, xy, n, beta);
+    if (beta_in)
+        memcpy(beta, beta_in, sizeof(int32_t) * (size_t)n);
+    else
+        orc_assign(g, xy, n, beta);
     for (int64_t p = 0; p < n; ++p)
         for (int64_t q = 0; q < n; ++q) {
             if (beta[p] != beta[q] || labels[p] != labels[q]) continue;
@@ -253,7 +262,7 @@ void orc_direct_cells(const orc_grid *g, int32_t D, const float *nu_x, const flo
     for (int64_t c = 0; c < ncells; ++c) {
         double x = g->x_min + ((double)cells[2 * c] + 0.5) * g->res;
         double y = g->y_min + ((double)cells[2 * c + 1] + 0.5) * g->res;
-        int32_t b = orc_tile_of(g, x, y);
+        int32_t b = beta_cells ? beta_cells[c] : orc_tile_of(g, x, y);
         for (int32_t psi = 0; psi < 2; ++psi) {
             double num = 0.0;
             for (int64_t p = 0; p < n; ++p) {

@@ -73,7 +73,10 @@ def test_tile_assignment_exact_including_ties_and_outside():
     pts = rng.uniform([-6, -5], [6, 5], size=(300, 2)).astype(np.float32)
     # exact boundaries (x = -2, 0, 2 ; y = -1, 1) and corners: ties go to the lower tile
     bnd = np.array([[-2, 0.3], [0, 0.3], [2, 0.3], [0.1, -1], [0.1, 1], [0, 1], [2, -1],
-                    [-4, -3], [4, 3], [-100, 50], [100, -50]], np.float32)
+                    [-4, -3], [4, 3], [-100, 50], [100, -50],
+                    # a hair off a boundary: FP64 distances to the two centres round to a tie
+                    [5.4526174e-17, 0.3], [-3.0377352e-16, 0.7], [1e-38, -0.5], [-0.0, 0.2]],
+                   np.float32)
     pts = np.concatenate([pts, bnd])
     got = oracle.assign(g, pts)
     want = [_exact_argmin(g, float(x), float(y)) for x, y in pts]
@@ -297,6 +300,26 @@ def test_classification_threshold_inclusive_in_float32():
     ogm = np.array([-0.5, 0.0, 0.1, 0.09999999, np.float32(0.1)], np.float32)
     assert oracle.classify_f32(ogm, 0.1).tolist() == [0, 0, 1, 0, 1]
     assert oracle.classify_f32(ogm, 0.0).tolist() == [0, 1, 1, 1, 1]
+
+
+def test_window_query_over_the_whole_map_is_the_map_query():
+    """A window covering the map decodes the map: it reduces to the full pipeline."""
+    g = Grid(W=20, H=14, res=0.2, x_min=-2.0, y_min=-1.4, tiles_x=2, tiles_y=2)
+    rng = np.random.default_rng(8)
+    xy = rng.uniform(-2.0, 2.0, (80, 2)).astype(np.float32)
+    lab = rng.integers(0, 2, 80).astype(np.uint8)
+    nx, ny = oracle.draw_nu(4, 128, 0.2)
+    full = oracle.pipeline(g, nx, ny, xy, lab, 2, 3)
+    win = oracle.query_window(g, nx, ny, full["omega"], 0, 0, g.W, g.H, 2, 3)
+    assert np.allclose(win["pr1"], full["pr1"], atol=1e-14)
+    assert np.allclose(win["ogm"], full["ogm"], atol=1e-14)
+    # an interior window whose region holds the global maxima equals the map query there
+    j, i = np.unravel_index(np.argmax(full["P"][1]), full["P"][1].shape)
+    k, l = np.unravel_index(np.argmax(full["P"][0]), full["P"][0].shape)
+    x0, y0 = max(0, min(i, l) - 1), max(0, min(j, k) - 1)
+    x1, y1 = min(g.W, max(i, l) + 2), min(g.H, max(j, k) + 2)
+    part = oracle.query_window(g, nx, ny, full["omega"], x0, y0, x1 - x0, y1 - y0, 2, 3)
+    assert np.allclose(part["pr1"], full["pr1"][y0:y1, x0:x1], atol=1e-13)
 
 
 # ----------------------------------------------- the paper's printed numbers
