@@ -54,6 +54,20 @@ extern "C" {
 #define VSAOGM_DECODE_BF16X3 1 /* tensor cores, split hi/lo bf16, FP32 accum */
 #define VSAOGM_DECODE_FP16X3 2 /* tensor cores, split hi/lo fp16, FP32 accum */
 
+/* vsaogm_config.decode_mode: the toggles of the decoding ablation
+ * (Sec. IV-D1: P_hat = f_ACT(f_NL(f_N(P))) with toggles delta_N, delta_NL,
+ * delta_ACT).  0 is the paper's method: normalise by the class maximum, square,
+ * then the disk-mask entropy.  The low bits switch a step off; bits 4..7 pick
+ * the activation that replaces the entropy. */
+#define VSAOGM_MODE_NO_NORM 1u        /* skip f_N (division by max P)        */
+#define VSAOGM_MODE_NO_SQUARE 2u      /* skip f_NL (squaring)                */
+#define VSAOGM_ACT_ENTROPY (0u << 4)  /* Algorithm 2 (default)               */
+#define VSAOGM_ACT_RELU (1u << 4)     /* max(0, x) per cell                  */
+#define VSAOGM_ACT_TANH (2u << 4)     /* tanh(x) per cell                    */
+#define VSAOGM_ACT_SIGMOID (3u << 4)  /* 1 / (1 + e^-x) per cell             */
+#define VSAOGM_ACT_NONE (4u << 4)     /* identity (delta_ACT = 0)            */
+#define VSAOGM_ACT_MASK (15u << 4)
+
 /* vsaogm_config.flags */
 #define VSAOGM_FLAG_CHECKED 1u /* encode synchronises and reports rejected points */
 #define VSAOGM_FLAG_ATOMIC 2u  /* bundle with atomics (no partial-sum scratch,
@@ -76,6 +90,7 @@ typedef struct {
     uint64_t seed;        /* SplitMix64 seed of the axis frequencies              */
     int32_t decode_prec;  /* VSAOGM_DECODE_*                                      */
     uint32_t flags;       /* VSAOGM_FLAG_*                                        */
+    uint32_t decode_mode; /* VSAOGM_MODE_* | VSAOGM_ACT_*; 0 = the paper's method  */
 } vsaogm_config;
 
 typedef struct vsaogm_map vsaogm_map;
@@ -162,12 +177,37 @@ int vsaogm_entropy(vsaogm_map *map, const float *heat_dev, float *occ_dev, float
 int vsaogm_query(vsaogm_map *map, float *heat_dev, float *occ_dev, float *ogm_dev,
                  uint8_t *cls_dev, void *stream);
 
+/* Local map query for the window of cells [x0, x0 + w) x [y0, y0 + h):
+ * Eqs. vector-normalization, loc-query and non-linearities, Algorithm 2 and
+ * Eqs. softmax, psd, classification, restricted to a window.  The region
+ * decoded is the window grown by R = max(r_occ, r_emp) cells on each side and
+ * clipped to the map, so every window cell sees its whole disk; the maximum of
+ * Eq. non-linearities is taken over that region (a local query normalises by
+ * what it decodes; for the whole map this equals vsaogm_query).
+ * heat_dev: caller scratch of vsaogm_window_scratch() floats (receives P of
+ * the region); occ_dev (float [h][w], row stride w); ogm_dev, cls_dev nullable
+ * [h][w].  Errors: E_INVAL (window not inside the map, NULL), E_CUDA.       */
+int vsaogm_query_window(vsaogm_map *map, int32_t x0, int32_t y0, int32_t w, int32_t h,
+                        float *heat_dev, float *occ_dev, float *ogm_dev, uint8_t *cls_dev,
+                        void *stream);
+
+/* Floats of heat scratch vsaogm_query_window needs for that window. */
+int vsaogm_window_scratch(const vsaogm_map *map, int32_t x0, int32_t y0, int32_t w, int32_t h,
+                          int64_t *floats);
+
 /* End-to-end call on host buffers: copies xy_host/labels_host to the device,
  * bundles them, runs vsaogm_query and copies Pr(psi = 1) back into occ_host
  * (float [H][W]); returns after the stream has finished.  Device staging is
  * owned by the map and grows on demand.  Errors: as the calls it makes.     */
 int vsaogm_update_query_host(vsaogm_map *map, const float *xy_host, const uint8_t *labels_host,
                              int64_t n, float *occ_host, void *stream);
+
+/* Grows the map's scratch up front so that later calls allocate nothing:
+ * vsaogm_encode_bundle with up to max_points points per call, and every
+ * vsaogm_decode / vsaogm_query / vsaogm_query_window.  For servers that must
+ * not allocate (cudaMalloc synchronises the device) once they serve requests.
+ * Synchronous.  Errors: E_INVAL, E_NOMEM, E_CUDA.                            */
+int vsaogm_reserve(vsaogm_map *map, int64_t max_points);
 
 /* Number of points rejected by vsaogm_encode_bundle since the last reset
  * (synchronises `stream`).                                                  */

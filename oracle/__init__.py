@@ -333,6 +333,33 @@ def classify_f32(ogm_f32: np.ndarray, rho: float) -> np.ndarray:
     return out
 
 
+def decode_variant(P: np.ndarray, norm: bool, square: bool, act: str, r_occ: int, r_emp: int):
+    """The decoding ablation of Sec. IV-D1, P_hat = f_ACT(f_NL(f_N(P))), followed by
+    Eq. softmax and Eq. psd.  f_N divides each class map by its maximum (0 if the
+    maximum is not positive), f_NL squares, f_ACT is 'entropy' (Algorithm 2),
+    'relu', 'tanh', 'sigmoid' or 'none'.  Returns (Pr1, Pr0, OGM)."""
+    v = np.array(P, np.float64)
+    if norm:
+        for c in range(2):
+            m = v[c].max()
+            v[c] = v[c] / m if m > 0 else 0.0
+    if square:
+        v = v * v
+    if act == "entropy":
+        a0, a1 = entropy(v[0], r_emp), entropy(v[1], r_occ)
+    elif act == "relu":
+        a0, a1 = np.maximum(v[0], 0.0), np.maximum(v[1], 0.0)
+    elif act == "tanh":
+        a0, a1 = np.tanh(v[0]), np.tanh(v[1])
+    elif act == "sigmoid":
+        a0, a1 = 1.0 / (1.0 + np.exp(-v[0])), 1.0 / (1.0 + np.exp(-v[1]))
+    elif act == "none":
+        a0, a1 = v[0], v[1]
+    else:
+        raise ValueError(act)
+    return softmax_psd(a0, a1)
+
+
 def query_window(g: Grid, nu_x, nu_y, omega, x0: int, y0: int, w: int, h: int, r_occ: int,
                  r_emp: int, frame: str = "tile") -> dict:
     """A local map query (reading of the paper for windows): the window grown by

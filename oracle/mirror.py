@@ -104,7 +104,7 @@ def nonlinear(P):
 def entropy(Ph, r):
     H, W = Ph.shape
     with np.errstate(divide="ignore", invalid="ignore"):
-        h = np.where(Ph != 0, -Ph * np.log(np.where(Ph != 0, Ph, 1.0)), 0.0)
+        h = np.where(Ph > 0, -Ph * np.log(np.where(Ph > 0, Ph, 1.0)), 0.0)
     out = np.zeros_like(Ph)
     for dy in range(-r, r + 1):
         for dx in range(-r, r + 1):

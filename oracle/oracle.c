@@ -297,7 +297,9 @@ void orc_nonlinear(const double *P, int64_t ncell, double *Phat, double *maxima)
 
 /* Algorithm 2 with the localized Shannon entropy and the disk mask
  * (Eq. entropy-mask): H(x, y) = - sum over in-grid (x', y') with
- * (x'-x)^2 + (y'-y)^2 <= r^2 of P log P, natural log, 0 log 0 = 0.
+ * (x'-x)^2 + (y'-y)^2 <= r^2 of P log P, natural log, 0 log 0 = 0.  The
+ * summand is taken as 0 for P < 0, which only the decoding ablation without
+ * the squaring step can produce (P_hat is a square otherwise).
  * Distances are in cell units.  Phat and Hout are one class map each, layout
  * [H][W].                                                                    */
 void orc_entropy(const double *Phat, int32_t W, int32_t H, int32_t r, double *Hout)
@@ -314,7 +316,7 @@ void orc_entropy(const double *Phat, int32_t W, int32_t H, int32_t r, double *Ho
                     int64_t d2 = (int64_t)(xx - x) * (xx - x) + (int64_t)(yy - y) * (yy - y);
                     if (d2 > (int64_t)r * r) continue;
                     double v = Phat[(size_t)yy * W + xx];
-                    if (v != 0.0) s -= v * log(v);
+                    if (v > 0.0) s -= v * log(v); /* 0 ln 0 = 0; v < 0 carries no mass */
                 }
             Hout[(size_t)y * W + x] = s;
         }

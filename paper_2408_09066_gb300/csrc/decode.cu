@@ -57,15 +57,19 @@ __device__ __forceinline__ float2 unit_phasor(float nu, float d)
     return make_float2(c, s);
 }
 
+// One block of cells over one slice [k_begin, k_end) of the frequencies; the
+// partial maps of the slices are summed by reduce_slices_kernel.
 __global__ void __launch_bounds__(256) decode_fp32_kernel(
-    const DecodeBlock *__restrict__ blocks, const float2 *__restrict__ omega,
-    const float *__restrict__ inv_norm, const float *__restrict__ nu, int D, int W, int H,
-    const float *__restrict__ col_off, const float *__restrict__ row_off,
-    float *__restrict__ heat, unsigned *__restrict__ maxima)
+    const BlockBatch blocks, const float2 *__restrict__ omega, const float *__restrict__ inv_norm,
+    const float *__restrict__ nu, int D, OutGeom og, const float *__restrict__ col_off,
+    const float *__restrict__ row_off, int k_per_split, float *__restrict__ partial)
 {
     __shared__ float2 sA[kKC][kBI];
     __shared__ float2 sU[2][kKC][kBJ];
-    const DecodeBlock b = blocks[blockIdx.x];
+    const DecodeBlock b = blocks.b[blockIdx.x];
+    const int split = blockIdx.y;
+    const int k_first = split * k_per_split;
+    const int k_last = min(D, k_first + k_per_split);
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
     const float w0 = inv_norm[2 * b.tile], w1 = inv_norm[2 * b.tile + 1];
     const float2 *om0 = omega + (size_t)(2 * b.tile) * D;
@@ -78,20 +82,20 @@ __global__ void __launch_bounds__(256) decode_fp32_kernel(
 #pragma unroll
             for (int v = 0; v < 4; ++v) acc[c][u][v] = 0.f;
 
-    for (int k0 = 0; k0 < D; k0 += kKC) {
+    for (int k0 = k_first; k0 < k_last; k0 += kKC) {
         // tables for this stage: 2048 A entries and 2048 B entries (x2 classes)
         for (int e = threadIdx.x; e < kKC * kBI; e += blockDim.x) {
             int kk = e / kBI, ii = e % kBI;
             int k = k0 + kk, i = b.i0 + ii;
             float2 a = make_float2(0.f, 0.f);
-            if (k < D && i < b.i1) a = unit_phasor(nu[k], col_off[i]);
+            if (k < k_last && i < b.i1) a = unit_phasor(nu[k], col_off[i]);
             sA[kk][ii] = a;
         }
         for (int e = threadIdx.x; e < kKC * kBJ; e += blockDim.x) {
             int kk = e / kBJ, jj = e % kBJ;
             int k = k0 + kk, j = b.j0 + jj;
             float2 u0 = make_float2(0.f, 0.f), u1 = u0;
-            if (k < D && j < b.j1) {
+            if (k < k_last && j < b.j1) {
                 float2 bb = unit_phasor(nu[D + k], row_off[j]);
                 float2 m0 = om0[k], m1 = om1[k];
                 // conj(w_hat) * B
@@ -121,8 +125,8 @@ __global__ void __launch_bounds__(256) decode_fp32_kernel(
         }
         __syncthreads();
     }
-    // epilogue: store and fold the per-class maximum
-    float mx[2] = {-INFINITY, -INFINITY};
+    // epilogue: this slice's partial maps
+    float *out = partial + (size_t)split * 2 * og.OH * og.OW;
 #pragma unroll
     for (int v = 0; v < 4; ++v) {
         int j = b.j0 + ty + 16 * v;
@@ -131,14 +135,31 @@ __global__ void __launch_bounds__(256) decode_fp32_kernel(
             int i = b.i0 + tx + 16 * q;
             if (i < b.i1 && j < b.j1) {
 #pragma unroll
-                for (int c = 0; c < 2; ++c) {
-                    heat[((size_t)c * H + j) * W + i] = acc[c][v][q];
-                    mx[c] = fmaxf(mx[c], acc[c][v][q]);
-                }
+                for (int c = 0; c < 2; ++c)
+                    out[((size_t)c * og.OH + (j - og.oy)) * og.OW + (i - og.ox)] = acc[c][v][q];
             }
         }
     }
-#pragma unroll
+}
+
+// heat = (sum of the slices' partial maps, in slice order) * inv_scale, and
+// the per-class maxima of Eq. non-linearities (order-preserving atomicMax).
+__global__ void __launch_bounds__(256) reduce_slices_kernel(const float *__restrict__ partial,
+                                                            int n_splits, size_t cells,
+                                                            float inv_scale,
+                                                            float *__restrict__ heat,
+                                                            unsigned *__restrict__ maxima)
+{
+    float mx[2] = {-INFINITY, -INFINITY};
+    for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < 2 * cells;
+         q += (size_t)gridDim.x * blockDim.x) {
+        float s = 0.f;
+        for (int sp = 0; sp < n_splits; ++sp) s += partial[(size_t)sp * 2 * cells + q];
+        s *= inv_scale;
+        heat[q] = s;
+        int c = q < cells ? 0 : 1;
+        mx[c] = fmaxf(mx[c], s);
+    }
     for (int c = 0; c < 2; ++c) {
         float m = mx[c];
         for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
@@ -146,16 +167,19 @@ __global__ void __launch_bounds__(256) decode_fp32_kernel(
     }
 }
 
-// P -> P_hat = (P / m)^2, or 0 where the class maximum m is not positive.
+// P -> P_hat = (P / m)^2 (Eq. non-linearities), 0 where the class maximum m is
+// not positive; the decode_mode toggles switch the division or the square off.
 __global__ void nonlinear_kernel(float *__restrict__ heat, size_t cells,
-                                 const unsigned *__restrict__ maxima)
+                                 const unsigned *__restrict__ maxima, unsigned mode)
 {
     const float m0 = ordered_to_float(maxima[0]), m1 = ordered_to_float(maxima[1]);
     const float i0 = m0 > 0.f ? 1.0f / m0 : 0.f, i1 = m1 > 0.f ? 1.0f / m1 : 0.f;
+    const bool norm = !(mode & VSAOGM_MODE_NO_NORM), square = !(mode & VSAOGM_MODE_NO_SQUARE);
     for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < 2 * cells;
          q += (size_t)gridDim.x * blockDim.x) {
-        float v = heat[q] * (q < cells ? i0 : i1);
-        heat[q] = v * v;
+        float v = heat[q];
+        if (norm) v *= q < cells ? i0 : i1;
+        heat[q] = square ? v * v : v;
     }
 }
 
@@ -180,22 +204,83 @@ int memory_norms(vsaogm_map *m, cudaStream_t st)
     return VSAOGM_OK;
 }
 
-int decode_raw(vsaogm_map *m, float *heat, cudaStream_t st)
+void region_blocks(const vsaogm_map *m, Region r, int bi, int bj, std::vector<DecodeBlock> &out)
+{
+    out.clear();
+    const int tx = m->cfg.tiles_x, ty = m->cfg.tiles_y;
+    for (int by = 0; by < ty; ++by) {
+        const int y0 = std::max(r.y0, m->tile_first[1][by]), y1 = std::min(r.y1, m->tile_last[1][by]);
+        if (y0 >= y1) continue;
+        for (int bx = 0; bx < tx; ++bx) {
+            const int x0 = std::max(r.x0, m->tile_first[0][bx]);
+            const int x1 = std::min(r.x1, m->tile_last[0][bx]);
+            if (x0 >= x1) continue;
+            for (int j0 = y0; j0 < y1; j0 += bj)
+                for (int i0 = x0; i0 < x1; i0 += bi)
+                    out.push_back(DecodeBlock{by * tx + bx, i0, j0, std::min(i0 + bi, x1),
+                                              std::min(j0 + bj, y1)});
+        }
+    }
+}
+
+int decode_region(vsaogm_map *m, Region r, float *heat, cudaStream_t st)
 {
     int rc = memory_norms(m, st);
     if (rc) return rc;
-    if (m->cfg.decode_prec != VSAOGM_DECODE_FP32) return decode_tensor_cores(m, heat, st);
+    if (m->cfg.decode_prec != VSAOGM_DECODE_FP32) return decode_tensor_cores(m, r, heat, st);
+    std::vector<DecodeBlock> blocks;
+    region_blocks(m, r, kBI, kBJ, blocks);
+    const int D = m->cfg.D, nb = (int)blocks.size();
+    const size_t cells = (size_t)r.w() * r.h();
+    // slices of the frequencies: about three resident CTAs per SM in total
+    int splits = std::max(1, std::min((D + kKC - 1) / kKC, 3 * 152 / std::max(nb, 1)));
+    const int kps = ((D + splits - 1) / splits + kKC - 1) / kKC * kKC;
+    splits = (D + kps - 1) / kps;
+    rc = ensure(m->ws.dec_partial, sizeof(float) * (size_t)splits * 2 * cells);
+    if (rc) return rc;
     StageScope sc(m, VSAOGM_STAGE_DECODE, st);
+    const OutGeom og{r.x0, r.y0, r.w(), r.h()};
+    int launches = 0;
+    for (int b0 = 0; b0 < nb; b0 += kMaxLaunchBlocks) {
+        BlockBatch batch;
+        batch.n = std::min(kMaxLaunchBlocks, nb - b0);
+        for (int q = 0; q < batch.n; ++q) batch.b[q] = blocks[b0 + q];
+        decode_fp32_kernel<<<dim3(batch.n, splits), 256, 0, st>>>(
+            batch, m->omega, m->inv_norm, m->nu, D, og, m->col_off, m->row_off, kps,
+            (float *)m->ws.dec_partial.ptr);
+        ++launches;
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_error(e, "decode: fp32");
+    if ((rc = sum_slices(m, (const float *)m->ws.dec_partial.ptr, splits, cells, 1.0f, heat, st)))
+        return rc;
+    sc.end(launches + 1);
+    return VSAOGM_OK;
+}
+
+// Grows the decode scratch so that no map or window query allocates.  A query
+// of a region with nb blocks uses at most (slots / nb) frequency slices, and the
+// blocks cover the region, so slices x cells <= slots x block cells: 152 x 128^2
+// for the tensor-core decode, 456 x 64^2 for the SIMT one; one slice of the
+// whole map bounds the rest.
+int reserve_decode(vsaogm_map *m)
+{
+    const size_t cells = (size_t)m->cfg.grid_w * m->cfg.grid_h;
+    size_t need = std::max<size_t>({(size_t)152 * 128 * 128, (size_t)3 * 152 * kBI * kBJ, cells});
+    return ensure(m->ws.dec_partial, sizeof(float) * 2 * need);
+}
+
+int sum_slices(vsaogm_map *m, const float *partial, int splits, size_t cells, float inv_scale,
+               float *heat, cudaStream_t st)
+{
     // ordered encoding 0 is below every float: the running maximum starts empty
     cudaError_t e = cudaMemsetAsync(m->maxima, 0, 2 * sizeof(unsigned), st);
     if (e != cudaSuccess) return cuda_error(e, "decode");
-    decode_fp32_kernel<<<m->n_dblocks, 256, 0, st>>>(m->dblocks, m->omega, m->inv_norm, m->nu,
-                                                    m->cfg.D, m->cfg.grid_w, m->cfg.grid_h,
-                                                    m->col_off, m->row_off, heat, m->maxima);
+    int blocks = (int)std::min<size_t>((2 * cells + 255) / 256, 152 * 8);
+    reduce_slices_kernel<<<blocks, 256, 0, st>>>(partial, splits, cells, inv_scale, heat,
+                                                 m->maxima);
     e = cudaGetLastError();
-    if (e != cudaSuccess) return cuda_error(e, "decode: fp32");
-    sc.end(1);
-    return VSAOGM_OK;
+    return e == cudaSuccess ? VSAOGM_OK : cuda_error(e, "decode: slice sum");
 }
 
 int apply_nonlinearity(vsaogm_map *m, float *heat, cudaStream_t st)
@@ -203,7 +288,7 @@ int apply_nonlinearity(vsaogm_map *m, float *heat, cudaStream_t st)
     StageScope sc(m, VSAOGM_STAGE_NONLINEAR, st);
     size_t cells = (size_t)m->cfg.grid_w * m->cfg.grid_h;
     int blocks = (int)std::min<size_t>((2 * cells + 255) / 256, 152 * 16);
-    nonlinear_kernel<<<blocks, 256, 0, st>>>(heat, cells, m->maxima);
+    nonlinear_kernel<<<blocks, 256, 0, st>>>(heat, cells, m->maxima, m->cfg.decode_mode);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_error(e, "decode: non-linearity");
     sc.end(1);

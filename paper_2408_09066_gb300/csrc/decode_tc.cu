@@ -85,10 +85,10 @@ __device__ __forceinline__ void split2(float x, float y, uint32_t &hi, uint32_t 
 
 template <bool BF16>
 __global__ void __launch_bounds__(256, 1) decode_tc_kernel(
-    const DecodeBlock *__restrict__ blocks, const float2 *__restrict__ omega,
-    const float *__restrict__ inv_norm, const float *__restrict__ nu, int D, int W, int H,
-    const float *__restrict__ col_off, const float *__restrict__ row_off, int k_per_split, int N,
-    float u_scale, float *__restrict__ partial, int *__restrict__ status)
+    const BlockBatch blocks, const float2 *__restrict__ omega, const float *__restrict__ inv_norm,
+    const float *__restrict__ nu, int D, OutGeom og, const float *__restrict__ col_off,
+    const float *__restrict__ row_off, int k_per_split, int N, float u_scale,
+    float *__restrict__ partial, int *__restrict__ status)
 {
     extern __shared__ uint8_t smem_raw[];
     __shared__ uint64_t empty_bar[2], done_bar;
@@ -98,7 +98,7 @@ __global__ void __launch_bounds__(256, 1) decode_tc_kernel(
     const int stage_bytes = kAStage + 2 * N * kRowBytes;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const DecodeBlock b = blocks[blockIdx.x];
+    const DecodeBlock b = blocks.b[blockIdx.x];
     const int split = blockIdx.y;
     const int k_begin = split * k_per_split;
     const int k_end = min(D, k_begin + k_per_split);
@@ -210,12 +210,12 @@ __global__ void __launch_bounds__(256, 1) decode_tc_kernel(
     if (!abort_s && n_stages > 0) {
         const int c = warp >> 2, lane_base = 32 * (warp & 3);
         const int m = lane_base + lane;
-        float *out = partial + (((size_t)split * 2 + c) * H) * W;
+        float *out = partial + (((size_t)split * 2 + c) * og.OH) * og.OW;
         for (int cc = 0; cc < N / 16; ++cc) {
             float v[16];
             tmem_ld_32x32b_x16(tmem + ((uint32_t)lane_base << 16) + 128u * c + cc * 16, v);
             if (m < nj) {
-                float *row = out + (size_t)(b.j0 + m) * W + b.i0;
+                float *row = out + (size_t)(b.j0 + m - og.oy) * og.OW + (b.i0 - og.ox);
 #pragma unroll
                 for (int x = 0; x < 16; ++x)
                     if (cc * 16 + x < ni) row[cc * 16 + x] = v[x];
@@ -224,9 +224,10 @@ __global__ void __launch_bounds__(256, 1) decode_tc_kernel(
     } else if (!abort_s && n_stages == 0) {
         // no frequencies in this slice: its contribution is zero
         const int c = warp >> 2, m = 32 * (warp & 3) + lane;
-        float *out = partial + (((size_t)split * 2 + c) * H) * W;
+        float *out = partial + (((size_t)split * 2 + c) * og.OH) * og.OW;
         if (m < nj)
-            for (int x = 0; x < ni; ++x) out[(size_t)(b.j0 + m) * W + b.i0 + x] = 0.f;
+            for (int x = 0; x < ni; ++x)
+                out[(size_t)(b.j0 + m - og.oy) * og.OW + (b.i0 - og.ox) + x] = 0.f;
     }
     if (abort_s && tid == 0) atomicExch(status, VSAOGM_E_TIMEOUT);
     tc_fence_before_sync();
@@ -234,80 +235,62 @@ __global__ void __launch_bounds__(256, 1) decode_tc_kernel(
     if (warp == 0) tmem_dealloc(tmem, kTmemCols);
 }
 
-// heat = sum over slices (fixed order) / u_scale, and the per-class maxima.
-__global__ void __launch_bounds__(256) decode_tc_reduce_kernel(const float *__restrict__ partial,
-                                                               int n_splits, size_t cells,
-                                                               float inv_scale,
-                                                               float *__restrict__ heat,
-                                                               unsigned *__restrict__ maxima)
-{
-    float mx[2] = {-INFINITY, -INFINITY};
-    for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < 2 * cells;
-         q += (size_t)gridDim.x * blockDim.x) {
-        float s = 0.f;
-        for (int sp = 0; sp < n_splits; ++sp) s += partial[(size_t)sp * 2 * cells + q];
-        s *= inv_scale;
-        heat[q] = s;
-        int c = q < cells ? 0 : 1;
-        mx[c] = fmaxf(mx[c], s);
-    }
-    for (int c = 0; c < 2; ++c) {
-        float m = mx[c];
-        for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-        if ((threadIdx.x & 31) == 0 && m > -INFINITY) atomicMax(&maxima[c], float_to_ordered(m));
-    }
-}
-
 }  // namespace
 
-int decode_tensor_cores(vsaogm_map *m, float *heat, cudaStream_t st)
+int decode_tensor_cores(vsaogm_map *m, Region r, float *heat, cudaStream_t st)
 {
-    const int D = m->cfg.D, W = m->cfg.grid_w, H = m->cfg.grid_h;
+    const int D = m->cfg.D;
     const bool bf16 = m->cfg.decode_prec == VSAOGM_DECODE_BF16X3;
-    const int nb = m->n_tcblocks;
+    std::vector<DecodeBlock> blocks;
+    region_blocks(m, r, 128, kM, blocks);
+    const int nb = (int)blocks.size();
     // slices of the frequencies so that blocks x slices fills the 152 SMs once
-    int splits = std::max(1, std::min((D + kKS - 1) / kKS, 152 / nb));
+    int splits = std::max(1, std::min((D + kKS - 1) / kKS, 152 / std::max(nb, 1)));
     int kps = ((D + splits - 1) / splits + kKS - 1) / kKS * kKS;
     splits = (D + kps - 1) / kps;
-    const size_t cells = (size_t)W * H;
+    const size_t cells = (size_t)r.w() * r.h();
     int rc = ensure(m->ws.dec_partial, sizeof(float) * (size_t)splits * 2 * cells);
     if (rc) return rc;
-    const int N = m->tc_n;
-    const size_t smem = 1024 + 2 * (size_t)(kAStage + 2 * N * kRowBytes);
     float u_scale = 1.f;
     if (!bf16) {
-        u_scale = 1.f;
         while (u_scale * u_scale * 4.f <= (float)D) u_scale *= 2.f;
     }
-    cudaError_t e;
-    StageScope sc(m, VSAOGM_STAGE_DECODE, st);
-    if ((e = cudaMemsetAsync(m->maxima, 0, 2 * sizeof(unsigned), st)) != cudaSuccess)
-        return cuda_error(e, "decode");
-    dim3 grid(nb, splits);
-    float *part = (float *)m->ws.dec_partial.ptr;
-    if (bf16) {
-        e = cudaFuncSetAttribute(decode_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)smem);
-        if (e == cudaSuccess)
-            decode_tc_kernel<true><<<grid, 256, smem, st>>>(m->tcblocks, m->omega, m->inv_norm,
-                                                            m->nu, D, W, H, m->col_off, m->row_off,
-                                                            kps, N, u_scale, part, m->status);
-    } else {
-        e = cudaFuncSetAttribute(decode_tc_kernel<false>,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e == cudaSuccess)
-            decode_tc_kernel<false><<<grid, 256, smem, st>>>(m->tcblocks, m->omega, m->inv_norm,
-                                                             m->nu, D, W, H, m->col_off,
-                                                             m->row_off, kps, N, u_scale, part,
-                                                             m->status);
-    }
-    if (e == cudaSuccess) e = cudaGetLastError();
+    const size_t smem_max = 1024 + 2 * (size_t)(kAStage + 2 * 128 * kRowBytes);
+    cudaError_t e = bf16 ? cudaFuncSetAttribute(decode_tc_kernel<true>,
+                                                cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                (int)smem_max)
+                         : cudaFuncSetAttribute(decode_tc_kernel<false>,
+                                                cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                (int)smem_max);
     if (e != cudaSuccess) return cuda_error(e, "decode: tensor cores");
-    int rblocks = (int)std::min<size_t>((2 * cells + 255) / 256, 152 * 8);
-    decode_tc_reduce_kernel<<<rblocks, 256, 0, st>>>(part, splits, cells, 1.0f / u_scale, heat,
-                                                     m->maxima);
-    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_error(e, "decode: slice sum");
-    sc.end(2);
+    StageScope sc(m, VSAOGM_STAGE_DECODE, st);
+    float *part = (float *)m->ws.dec_partial.ptr;
+    const OutGeom og{r.x0, r.y0, r.w(), r.h()};
+    int launches = 0;
+    for (int b0 = 0; b0 < nb; b0 += kMaxLaunchBlocks) {
+        BlockBatch batch;
+        batch.n = std::min(kMaxLaunchBlocks, nb - b0);
+        int widest = 16;
+        for (int q = 0; q < batch.n; ++q) {
+            batch.b[q] = blocks[b0 + q];
+            widest = std::max(widest, batch.b[q].i1 - batch.b[q].i0);
+        }
+        const int N = (widest + 15) / 16 * 16;  // MMA N: the widest block, multiple of 16
+        const size_t smem = 1024 + 2 * (size_t)(kAStage + 2 * N * kRowBytes);
+        dim3 grid(batch.n, splits);
+        if (bf16)
+            decode_tc_kernel<true><<<grid, 256, smem, st>>>(batch, m->omega, m->inv_norm, m->nu, D,
+                                                            og, m->col_off, m->row_off, kps, N,
+                                                            u_scale, part, m->status);
+        else
+            decode_tc_kernel<false><<<grid, 256, smem, st>>>(batch, m->omega, m->inv_norm, m->nu,
+                                                             D, og, m->col_off, m->row_off, kps, N,
+                                                             u_scale, part, m->status);
+        ++launches;
+    }
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_error(e, "decode: tensor cores");
+    if ((rc = sum_slices(m, part, splits, cells, 1.0f / u_scale, heat, st))) return rc;
+    sc.end(launches + 1);
     return VSAOGM_OK;
 }
 

@@ -401,8 +401,11 @@ __device__ __forceinline__ void encode_points_x2(const float2 *sp, int len,
                 f32x2 g = add2(add2(f1, f2), add2(e1, e2));
                 f = sub2(g, sub2(add2(g, kM), kM));
             } else {
-                f32x2 r = sub2(add2(add2(p1, p2), kM), kM);
-                f = add2(sub2(p1, r), p2);
+                // t = nu_x dx + nu_y dy with one rounding of the sum (FMA);
+                // t - rint(t) is exact.  Error at most ulp(64)/2 + ulp(32)/2
+                // = 2.9e-6 turns for |t| < 64.
+                f32x2 t = fma2(nx[j], qx, p2);
+                f = sub2(t, sub2(add2(t, kM), kM));
             }
             f32x2 cr, si;
             if (j < NPOLY) {
@@ -435,12 +438,16 @@ __device__ __forceinline__ void encode_points_x2(const float2 *sp, int len,
     }
 }
 
+// NPOLY < 0 selects the mixed form: warps below poly_warps use one polynomial
+// pair, the others none, so the polynomial share is poly_warps / (8 NP) of the
+// exponentials (warps of an SM share its MUFU and FMA pipes).
 template <int NP, int NPOLY, bool ATOMIC>
 __global__ void __launch_bounds__(256) encode_chunk_x2_kernel(const float2 *__restrict__ pts,
                                                               const int4 *__restrict__ chunks,
                                                               const int *__restrict__ n_chunks,
                                                               const float *__restrict__ nu, int D,
                                                               float nu_max_x, float nu_max_y,
+                                                              int poly_warps,
                                                               float2 *__restrict__ out)
 {
     using namespace sm100;
@@ -480,10 +487,23 @@ __global__ void __launch_bounds__(256) encode_chunk_x2_kernel(const float2 *__re
     __syncthreads();
     const bool fast = __uint_as_float(s_bound[0]) * nu_max_x < 32.0f &&
                       __uint_as_float(s_bound[1]) * nu_max_y < 32.0f;
-    if (fast)
-        encode_points_x2<NP, NPOLY, false>(sp, len, nx, ny, ac, as);
-    else
-        encode_points_x2<NP, NPOLY, true>(sp, len, nx, ny, ac, as);
+    if (NPOLY >= 0) {
+        constexpr int P = NPOLY < 0 ? 0 : NPOLY;
+        if (fast)
+            encode_points_x2<NP, P, false>(sp, len, nx, ny, ac, as);
+        else
+            encode_points_x2<NP, P, true>(sp, len, nx, ny, ac, as);
+    } else if ((int)(threadIdx.x >> 5) < poly_warps) {
+        if (fast)
+            encode_points_x2<NP, 1, false>(sp, len, nx, ny, ac, as);
+        else
+            encode_points_x2<NP, 1, true>(sp, len, nx, ny, ac, as);
+    } else {
+        if (fast)
+            encode_points_x2<NP, 0, false>(sp, len, nx, ny, ac, as);
+        else
+            encode_points_x2<NP, 0, true>(sp, len, nx, ny, ac, as);
+    }
 #pragma unroll
     for (int j = 0; j < NP; ++j) {
         const float2 cr = unpack2(ac[j]), si = unpack2(as[j]);
@@ -524,19 +544,25 @@ __global__ void __launch_bounds__(256) reduce_partials_kernel(const float2 *__re
     omega[(size_t)s * D + k] = make_float2(w.x + sr, w.y + si);
 }
 
+// Warps per CTA (of 8) that evaluate one frequency pair by polynomial when the
+// map does not say otherwise: the share of exponentials moved from the MUFU
+// pipe to the FMA pipe that balanced the two pipes on GB300.
+constexpr int kAutoPolyWarps4 = 6;  // 4 pairs per thread: 6/32 of the exponentials
+constexpr int kAutoPolyWarps2 = 3;  // 2 pairs per thread: 3/16
+
 template <int NP, int NPOLY>
 cudaError_t launch_x2(const vsaogm_map *m, const float2 *pts, const int4 *chunks,
                       const int *n_chunks, float2 *out, int max_chunks, bool atomic,
-                      cudaStream_t st)
+                      int pw, cudaStream_t st)
 {
     const int D = m->cfg.D;
     dim3 grid(max_chunks, (D + 512 * NP - 1) / (512 * NP));
     if (atomic)
         encode_chunk_x2_kernel<NP, NPOLY, true><<<grid, 256, 0, st>>>(
-            pts, chunks, n_chunks, m->nu, D, m->nu_max[0], m->nu_max[1], out);
+            pts, chunks, n_chunks, m->nu, D, m->nu_max[0], m->nu_max[1], pw, out);
     else
         encode_chunk_x2_kernel<NP, NPOLY, false><<<grid, 256, 0, st>>>(
-            pts, chunks, n_chunks, m->nu, D, m->nu_max[0], m->nu_max[1], out);
+            pts, chunks, n_chunks, m->nu, D, m->nu_max[0], m->nu_max[1], pw, out);
     return cudaGetLastError();
 }
 
@@ -545,19 +571,29 @@ cudaError_t launch_packed(const vsaogm_map *m, int np, const float2 *pts, const 
                           cudaStream_t st)
 {
     const int npoly = std::min(m->encode_poly_pairs, np);
+    const int pw = m->encode_poly_warps >= 0 ? m->encode_poly_warps
+                                             : (np == 4 ? kAutoPolyWarps4 : kAutoPolyWarps2);
+    if (npoly == 0 && pw > 0) {  // mixed: some warps with one polynomial pair
+        if (np == 4)
+            return launch_x2<4, -1>(m, pts, chunks, n_chunks, out, max_chunks, atomic, pw, st);
+        return launch_x2<2, -1>(m, pts, chunks, n_chunks, out, max_chunks, atomic, pw, st);
+    }
+#define VSA_X2(NPV, NPOLYV) \
+    launch_x2<NPV, NPOLYV>(m, pts, chunks, n_chunks, out, max_chunks, atomic, 0, st)
     if (np == 4) {
         switch (npoly) {
-            case 0: return launch_x2<4, 0>(m, pts, chunks, n_chunks, out, max_chunks, atomic, st);
-            case 1: return launch_x2<4, 1>(m, pts, chunks, n_chunks, out, max_chunks, atomic, st);
-            case 2: return launch_x2<4, 2>(m, pts, chunks, n_chunks, out, max_chunks, atomic, st);
-            default: return launch_x2<4, 3>(m, pts, chunks, n_chunks, out, max_chunks, atomic, st);
+            case 0: return VSA_X2(4, 0);
+            case 1: return VSA_X2(4, 1);
+            case 2: return VSA_X2(4, 2);
+            default: return VSA_X2(4, 3);
         }
     }
     switch (npoly) {
-        case 0: return launch_x2<2, 0>(m, pts, chunks, n_chunks, out, max_chunks, atomic, st);
-        case 1: return launch_x2<2, 1>(m, pts, chunks, n_chunks, out, max_chunks, atomic, st);
-        default: return launch_x2<2, 2>(m, pts, chunks, n_chunks, out, max_chunks, atomic, st);
+        case 0: return VSA_X2(2, 0);
+        case 1: return VSA_X2(2, 1);
+        default: return VSA_X2(2, 2);
     }
+#undef VSA_X2
 }
 
 template <int KPT>
@@ -591,6 +627,59 @@ static void encode_shape(const vsaogm_map *m, int64_t n, int D, int *kpt, int *c
     int p = 32;
     while (p * 2 <= c && p * 2 <= kMaxChunk) p *= 2;
     *chunk = p;
+}
+
+// Grows the encode scratch so that any batch of up to n points needs no
+// allocation (the sizes encode_bundle asks for are monotone in n).
+int reserve_encode(vsaogm_map *m, int64_t n64)
+{
+    const int n = (int)std::min<int64_t>(n64, kMaxBatch);
+    if (n <= 0) return VSAOGM_OK;
+    const int S1 = m->S + 1, D = m->cfg.D;
+    int kpt, chunk;
+    encode_shape(m, n, D, &kpt, &chunk);
+    const int nb = (n + kSortBlock - 1) / kSortBlock;
+    // The chunk size grows with the batch, so the chunk count ceil(n'/chunk(n'))
+    // peaks just before each doubling of the chunk: evaluate it there and at n.
+    int max_chunks = 0;
+    auto chunks_at = [&](int np) {
+        int k2, c2;
+        encode_shape(m, np, D, &k2, &c2);
+        return (np + c2 - 1) / c2;
+    };
+    max_chunks = chunks_at(n);
+    int lo = 1;
+    while (lo < n) {  // binary-search-free walk: step to the next size where the chunk changes
+        int c_lo, k_lo;
+        encode_shape(m, lo, D, &k_lo, &c_lo);
+        int hi = lo;
+        while (hi < n) {
+            int c_hi, k_hi;
+            encode_shape(m, std::min(n, hi * 2), D, &k_hi, &c_hi);
+            if (c_hi != c_lo) break;
+            hi = std::min(n, hi * 2);
+        }
+        // the largest n' in [hi, 2 hi) with the same chunk as lo
+        int a = hi, b = std::min(n, 2 * hi);
+        while (a < b) {
+            int mid = a + (b - a + 1) / 2, c_mid, k_mid;
+            encode_shape(m, mid, D, &k_mid, &c_mid);
+            if (c_mid == c_lo) a = mid; else b = mid - 1;
+        }
+        max_chunks = std::max(max_chunks, chunks_at(a));
+        if (a >= n) break;
+        lo = a + 1;
+    }
+    max_chunks += m->S;
+    int rc;
+    if ((rc = ensure(m->ws.blk_hist, sizeof(int) * (size_t)nb * S1))) return rc;
+    if ((rc = ensure(m->ws.seg_meta, sizeof(int) * (size_t)(3 * S1 + 2)))) return rc;
+    if ((rc = ensure(m->ws.chunks, sizeof(int4) * (size_t)max_chunks))) return rc;
+    if ((rc = ensure(m->ws.sorted, sizeof(float2) * (size_t)n))) return rc;
+    if (!(m->cfg.flags & VSAOGM_FLAG_ATOMIC) &&
+        (rc = ensure(m->ws.partial, sizeof(float2) * (size_t)max_chunks * D)))
+        return rc;
+    return VSAOGM_OK;
 }
 
 int encode_bundle(vsaogm_map *m, const float *xy_f, const uint8_t *lab, int64_t n64,

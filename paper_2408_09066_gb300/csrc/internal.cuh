@@ -41,6 +41,25 @@ struct DecodeBlock {
     int i1, j1;     // one past the last column / row (clipped to the tile)
 };
 
+// Blocks of one decode launch, passed by value as a kernel parameter.
+constexpr int kMaxLaunchBlocks = 128;
+struct BlockBatch {
+    int n;
+    DecodeBlock b[kMaxLaunchBlocks];
+};
+
+// A rectangle of cells [x0, x1) x [y0, y1) of the map.
+struct Region {
+    int x0, y0, x1, y1;
+    __host__ __device__ int w() const { return x1 - x0; }
+    __host__ __device__ int h() const { return y1 - y0; }
+};
+
+// Where decode writes cell (i, j): at (i - ox, j - oy) of an OW x OH grid.
+struct OutGeom {
+    int ox, oy, OW, OH;
+};
+
 // Grow-on-demand device buffer owned by a map.
 struct DevBuf {
     void *ptr = nullptr;
@@ -85,6 +104,7 @@ struct vsaogm_map {
     float nu_max[2];             // max_k |nu_x[k]|, max_k |nu_y[k]|
     int encode_packed;           // 1: f32x2 encode kernel, 0: scalar kernel
     int encode_poly_pairs;       // frequency pairs per thread on the FMA-pipe polynomial
+    int encode_poly_warps;       // > 0: only this many warps per CTA use one polynomial pair
     float2 *omega;               // [S][D]
     float *inv_norm;             // [S]: 1 / ||omega||, 0 for an all-zero memory
     unsigned *maxima;            // [2]: order-preserving encoding of max P per class
@@ -93,11 +113,7 @@ struct vsaogm_map {
     double *centre_x, *centre_y; // [tiles]
     int *col_tile, *row_tile;    // [W], [H]
     float *col_off, *row_off;    // [W], [H]
-    vsaogm_impl::DecodeBlock *dblocks;     // 64 x 64 blocks (FP32 SIMT decode)
-    int n_dblocks;
-    vsaogm_impl::DecodeBlock *tcblocks;    // <= 128 x 128 blocks (tensor-core decode)
-    int n_tcblocks;
-    int tc_n;                              // MMA N: widest block rounded up to 16
+    std::vector<int> tile_first[2], tile_last[2];  // per axis (x, y): cells of each tile
     int *status;                           // first error code recorded by a kernel
     int r_hw[2][2 * vsaogm_impl::kMaxRadius + 1];  // disk half-widths per class and dy
     vsaogm_impl::Scratch ws;
@@ -133,22 +149,43 @@ inline AxisDev axis_y(const vsaogm_map *m) { return {m->cfg.tiles_y, m->bnd_y_lo
 
 // encode.cu
 int encode_bundle(vsaogm_map *m, const float *xy, const uint8_t *lab, int64_t n, cudaStream_t st);
+int reserve_encode(vsaogm_map *m, int64_t n);
+// decode.cu
+int reserve_decode(vsaogm_map *m);
 
 // decode.cu
-int decode_raw(vsaogm_map *m, float *heat, cudaStream_t st);         // P and maxima
+inline Region full_region(const vsaogm_map *m);
+// Blocks of at most bi x bj cells covering region r, never straddling a tile.
+void region_blocks(const vsaogm_map *m, Region r, int bi, int bj, std::vector<DecodeBlock> &out);
+// P over region r into heat [2][r.h()][r.w()], and the maxima over r
+int decode_region(vsaogm_map *m, Region r, float *heat, cudaStream_t st);
+inline int decode_raw(vsaogm_map *m, float *heat, cudaStream_t st);
 int apply_nonlinearity(vsaogm_map *m, float *heat, cudaStream_t st); // P -> P_hat in place
 int memory_norms(vsaogm_map *m, cudaStream_t st);
-// decode_tc.cu: split-precision tensor-core decode (P and maxima)
-int decode_tensor_cores(vsaogm_map *m, float *heat, cudaStream_t st);
+// heat = inv_scale * sum over `splits` partial maps [splits][2][cells], plus maxima
+int sum_slices(vsaogm_map *m, const float *partial, int splits, size_t cells, float inv_scale,
+               float *heat, cudaStream_t st);
+// decode_tc.cu: split-precision tensor-core decode of region r (P and maxima)
+int decode_tensor_cores(vsaogm_map *m, Region r, float *heat, cudaStream_t st);
 
 // entropy.cu
-// raw_input: heat holds P (the non-linearity is applied on load with the
-// map's maxima); otherwise heat holds P_hat.
-int entropy(vsaogm_map *m, const float *heat, bool raw_input, float *occ, float *ogm,
-            uint8_t *cls, cudaStream_t st);
+// heat holds the class maps of region r ([2][r.h()][r.w()]); the outputs cover
+// window win (inside r), row stride win.w().  raw_input: heat holds P and the
+// non-linearity is applied on load with the map's maxima; else it holds P_hat.
+int entropy(vsaogm_map *m, const float *heat, Region r, Region win, bool raw_input, float *occ,
+            float *ogm, uint8_t *cls, cudaStream_t st);
 
 // misc kernels (decode.cu)
 int add_memories(float2 *dst, const float2 *src, int64_t count, cudaStream_t st);
+
+inline Region full_region(const vsaogm_map *m)
+{
+    return Region{0, 0, m->cfg.grid_w, m->cfg.grid_h};
+}
+inline int decode_raw(vsaogm_map *m, float *heat, cudaStream_t st)
+{
+    return decode_region(m, full_region(m), heat, st);
+}
 
 // Order-preserving map from float to unsigned (for atomicMax of floats).
 __host__ __device__ inline unsigned float_to_ordered(float f)

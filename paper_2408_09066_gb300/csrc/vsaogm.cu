@@ -135,7 +135,7 @@ void free_map(vsaogm_map *m)
     if (!m) return;
     void *ptrs[] = {m->nu, m->omega, m->inv_norm, m->maxima, m->rejected, m->bnd_x_lo,
                     m->bnd_y_lo, m->centre_x, m->centre_y, m->col_tile, m->row_tile,
-                    m->col_off, m->row_off, m->dblocks, m->tcblocks, m->status};
+                    m->col_off, m->row_off, m->status};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     DevBuf *bufs[] = {&m->ws.blk_hist, &m->ws.seg_meta, &m->ws.chunks, &m->ws.sorted,
@@ -175,6 +175,9 @@ int validate(const vsaogm_config *c)
         return set_error(VSAOGM_E_INVAL, "unknown decode_prec %d", c->decode_prec);
     if (c->flags & ~(VSAOGM_FLAG_CHECKED | VSAOGM_FLAG_ATOMIC))
         return set_error(VSAOGM_E_INVAL, "unknown flags 0x%x", c->flags);
+    if ((c->decode_mode & ~(VSAOGM_MODE_NO_NORM | VSAOGM_MODE_NO_SQUARE | VSAOGM_ACT_MASK)) ||
+        (c->decode_mode & VSAOGM_ACT_MASK) > VSAOGM_ACT_NONE)
+        return set_error(VSAOGM_E_INVAL, "unknown decode_mode 0x%x", c->decode_mode);
     return VSAOGM_OK;
 }
 
@@ -254,7 +257,6 @@ void disk_half_widths(int r, int *hw)
         if (e_ != cudaSuccess) return cuda_error(e_, what);    \
     } while (0)
 
-static const int kDecodeTileI = 64, kDecodeTileJ = 64;
 
 extern "C" {
 
@@ -310,11 +312,14 @@ int vsaogm_create(const vsaogm_config *cfg, vsaogm_map **out)
             m->nu_max[1] = std::max(m->nu_max[1], std::fabs(m->host_nu[D + k]));
         }
         // encode kernel family (tuning overrides through the environment)
-        m->encode_packed = 0;
+        m->encode_packed = 1;
         m->encode_poly_pairs = 0;
+        m->encode_poly_warps = -1;  // automatic share of polynomial phasors
         if (const char *v = getenv("VSAOGM_ENCODE_PACKED")) m->encode_packed = atoi(v) != 0;
         if (const char *v = getenv("VSAOGM_ENCODE_POLY"))
             m->encode_poly_pairs = std::max(0, std::min(3, atoi(v)));
+        if (const char *v = getenv("VSAOGM_ENCODE_POLY_WARPS"))
+            m->encode_poly_warps = std::max(-1, std::min(8, atoi(v)));
         std::vector<float> nu(m->host_nu, m->host_nu + 2 * (size_t)D);
         if ((rc = upload(&m->nu, nu))) break;
         // Tiling and cell tables (Sec. III-B3, Algorithm 1).
@@ -327,40 +332,11 @@ int vsaogm_create(const vsaogm_config *cfg, vsaogm_map **out)
             (rc = upload(&m->col_tile, ax.cell_tile)) || (rc = upload(&m->row_tile, ay.cell_tile)) ||
             (rc = upload(&m->col_off, ax.cell_off)) || (rc = upload(&m->row_off, ay.cell_off)))
             break;
-        std::vector<DecodeBlock> blocks;
-        for (int by = 0; by < cfg->tiles_y; ++by)
-            for (int bx = 0; bx < cfg->tiles_x; ++bx)
-                for (int j0 = ay.first[by]; j0 < ay.last[by]; j0 += kDecodeTileJ)
-                    for (int i0 = ax.first[bx]; i0 < ax.last[bx]; i0 += kDecodeTileI) {
-                        DecodeBlock b;
-                        b.tile = by * cfg->tiles_x + bx;
-                        b.i0 = i0;
-                        b.j0 = j0;
-                        b.i1 = std::min(i0 + kDecodeTileI, ax.last[bx]);
-                        b.j1 = std::min(j0 + kDecodeTileJ, ay.last[by]);
-                        blocks.push_back(b);
-                    }
-        m->n_dblocks = (int)blocks.size();
-        if ((rc = upload(&m->dblocks, blocks))) break;
-        // tensor-core decode blocks: up to 128 rows x 128 columns of one tile
-        std::vector<DecodeBlock> tcb;
-        int widest = 16;
-        for (int by = 0; by < cfg->tiles_y; ++by)
-            for (int bx = 0; bx < cfg->tiles_x; ++bx)
-                for (int j0 = ay.first[by]; j0 < ay.last[by]; j0 += 128)
-                    for (int i0 = ax.first[bx]; i0 < ax.last[bx]; i0 += 128) {
-                        DecodeBlock b;
-                        b.tile = by * cfg->tiles_x + bx;
-                        b.i0 = i0;
-                        b.j0 = j0;
-                        b.i1 = std::min(i0 + 128, ax.last[bx]);
-                        b.j1 = std::min(j0 + 128, ay.last[by]);
-                        widest = std::max(widest, b.i1 - b.i0);
-                        tcb.push_back(b);
-                    }
-        m->n_tcblocks = (int)tcb.size();
-        m->tc_n = (widest + 15) / 16 * 16;
-        if ((rc = upload(&m->tcblocks, tcb))) break;
+        // cells of each tile per axis; decode blocks are cut from these per call
+        m->tile_first[0] = ax.first;
+        m->tile_last[0] = ax.last;
+        m->tile_first[1] = ay.first;
+        m->tile_last[1] = ay.last;
         if ((rc = upload(&m->status, std::vector<int>(1, 0)))) break;
         disk_half_widths(cfg->r_emp, m->r_hw[0]);
         disk_half_widths(cfg->r_occ, m->r_hw[1]);
@@ -444,7 +420,8 @@ int vsaogm_entropy(vsaogm_map *m, const float *heat, float *occ, float *ogm, uin
                    void *stream)
 {
     if (!m || !heat || !occ) return set_error(VSAOGM_E_INVAL, "map, heat and occ must not be NULL");
-    return entropy(m, heat, false, occ, ogm, cls, (cudaStream_t)stream);
+    return entropy(m, heat, full_region(m), full_region(m), false, occ, ogm, cls,
+                   (cudaStream_t)stream);
 }
 
 int vsaogm_query(vsaogm_map *m, float *heat, float *occ, float *ogm, uint8_t *cls, void *stream)
@@ -452,7 +429,35 @@ int vsaogm_query(vsaogm_map *m, float *heat, float *occ, float *ogm, uint8_t *cl
     if (!m || !heat || !occ) return set_error(VSAOGM_E_INVAL, "map, heat and occ must not be NULL");
     cudaStream_t st = (cudaStream_t)stream;
     VSA_TRY(decode_raw(m, heat, st));
-    return entropy(m, heat, true, occ, ogm, cls, st);
+    return entropy(m, heat, full_region(m), full_region(m), true, occ, ogm, cls, st);
+}
+
+int vsaogm_window_scratch(const vsaogm_map *m, int32_t x0, int32_t y0, int32_t w, int32_t h,
+                          int64_t *floats)
+{
+    if (!m || !floats) return set_error(VSAOGM_E_INVAL, "map and floats must not be NULL");
+    if (w < 1 || h < 1 || x0 < 0 || y0 < 0 || x0 + w > m->cfg.grid_w || y0 + h > m->cfg.grid_h)
+        return set_error(VSAOGM_E_INVAL, "window must lie inside the map");
+    const int R = std::max(m->cfg.r_occ, m->cfg.r_emp);
+    const int64_t rw = std::min(m->cfg.grid_w, x0 + w + R) - std::max(0, x0 - R);
+    const int64_t rh = std::min(m->cfg.grid_h, y0 + h + R) - std::max(0, y0 - R);
+    *floats = 2 * rw * rh;
+    return VSAOGM_OK;
+}
+
+int vsaogm_query_window(vsaogm_map *m, int32_t x0, int32_t y0, int32_t w, int32_t h, float *heat,
+                        float *occ, float *ogm, uint8_t *cls, void *stream)
+{
+    int64_t need;
+    VSA_TRY(vsaogm_window_scratch(m, x0, y0, w, h, &need));
+    if (!heat || !occ) return set_error(VSAOGM_E_INVAL, "heat and occ must not be NULL");
+    const int R = std::max(m->cfg.r_occ, m->cfg.r_emp);
+    const Region win{x0, y0, x0 + w, y0 + h};
+    const Region r{std::max(0, x0 - R), std::max(0, y0 - R), std::min(m->cfg.grid_w, x0 + w + R),
+                   std::min(m->cfg.grid_h, y0 + h + R)};
+    cudaStream_t st = (cudaStream_t)stream;
+    VSA_TRY(decode_region(m, r, heat, st));
+    return entropy(m, heat, r, win, true, occ, ogm, cls, st);
 }
 
 int vsaogm_update_query_host(vsaogm_map *m, const float *xy_host, const uint8_t *lab_host,
@@ -480,6 +485,16 @@ int vsaogm_update_query_host(vsaogm_map *m, const float *xy_host, const uint8_t 
     VSA_CUDA(cudaMemcpyAsync(occ_host, m->ws.stage_occ.ptr, sizeof(float) * cells,
                              cudaMemcpyDeviceToHost, st), "occupancy download");
     VSA_CUDA(cudaStreamSynchronize(st), "update_query_host");
+    return VSAOGM_OK;
+}
+
+int vsaogm_reserve(vsaogm_map *m, int64_t max_points)
+{
+    if (!m) return set_error(VSAOGM_E_INVAL, "map is NULL");
+    if (max_points < 0) return set_error(VSAOGM_E_INVAL, "max_points must be >= 0");
+    VSA_TRY(reserve_encode(m, max_points));
+    VSA_TRY(reserve_decode(m));
+    VSA_CUDA(cudaDeviceSynchronize(), "reserve");
     return VSAOGM_OK;
 }
 

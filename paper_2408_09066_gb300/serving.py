@@ -1,0 +1,210 @@
+"""Continuous-batching serving of many robots' maps on one GPU.
+
+Each robot owns a resident map (its tile memories stay on the device between
+requests).  Two request kinds arrive over time:
+  * update(robot, points, labels): encode and bundle a scan into the map
+    (Eq. fb-with-ls-2d, Eq. bundling, Algorithm 1);
+  * query(robot, window): decode and entropy for a window of cells
+    (Eqs. loc-query, non-linearities, Algorithm 2, softmax, psd).
+
+The server keeps a fixed set of execution slots.  A slot is a CUDA stream with
+preallocated device buffers for the largest update and window it accepts, so
+serving never allocates; the number of slots is what the device-memory budget
+admits after the resident maps.  A request is started as soon as a slot is free
+and no earlier request of the same robot is still running (requests of one
+robot keep their arrival order; a map is used by one stream at a time).
+Requests of different robots run concurrently on different streams, so work
+that arrives while the GPU is busy joins it as slots free up.  Latency is
+measured from arrival to the completion event of the request's last GPU
+operation (for queries, the copy of the occupancy window to pinned host
+memory).
+"""
+from __future__ import annotations
+
+import collections
+import dataclasses
+import time
+
+import numpy as np
+
+from . import vsaogm as V
+
+
+@dataclasses.dataclass
+class Request:
+    kind: str                 # "update" or "query"
+    robot: int
+    arrival: float            # seconds from the start of the run
+    xy: np.ndarray | None = None       # update: float32 [n][2]
+    labels: np.ndarray | None = None   # update: uint8 [n]
+    window: tuple | None = None        # query: (x0, y0, w, h)
+    # filled in by the server
+    start: float = float("nan")
+    done: float = float("nan")
+    result: np.ndarray | None = None   # query: Pr(psi = 1) of the window, float32 [h][w]
+
+    @property
+    def latency(self) -> float:
+        return self.done - self.arrival
+
+
+class _Slot:
+    def __init__(self, torch, max_points: int, max_window_floats: int, max_window_cells: int):
+        dev = torch.device("cuda")
+        self.stream = torch.cuda.Stream()
+        self.xy = torch.empty((max_points, 2), dtype=torch.float32, device=dev)
+        self.lab = torch.empty(max_points, dtype=torch.uint8, device=dev)
+        self.heat = torch.empty(max_window_floats, dtype=torch.float32, device=dev)
+        self.occ = torch.empty(max_window_cells, dtype=torch.float32, device=dev)
+        self.xy_h = torch.empty((max_points, 2), dtype=torch.float32).pin_memory()
+        self.lab_h = torch.empty(max_points, dtype=torch.uint8).pin_memory()
+        self.occ_h = torch.empty(max_window_cells, dtype=torch.float32).pin_memory()
+        self.done = torch.cuda.Event(enable_timing=True)
+        self.req: Request | None = None
+
+    @staticmethod
+    def bytes_needed(max_points: int, max_window_floats: int, max_window_cells: int) -> int:
+        return max_points * 9 + 4 * (max_window_floats + max_window_cells)
+
+
+class Server:
+    """Resident maps + execution slots; see the module docstring."""
+
+    def __init__(self, configs: list, max_points: int, max_window: int, n_slots: int = 8,
+                 mem_budget: int | None = None):
+        import torch
+        self.torch = torch
+        self.maps = [V.Map(c) for c in configs]
+        R = max(max(c.r_occ, c.r_emp) for c in configs)
+        edge = max_window + 2 * R
+        self.max_points, self.max_window = max_points, max_window
+        win_floats, win_cells = 2 * edge * edge, max_window * max_window
+        # grow every map's scratch to the largest request so serving never allocates
+        for m in self.maps:
+            m.reserve(max_points)
+        torch.cuda.synchronize()
+        free, _ = torch.cuda.mem_get_info()
+        budget = free if mem_budget is None else min(mem_budget, free)
+        per_slot = _Slot.bytes_needed(max_points, win_floats, win_cells)
+        self.n_slots = max(1, min(n_slots, budget // per_slot))
+        self.slots = [_Slot(torch, max_points, win_floats, win_cells) for _ in range(self.n_slots)]
+        self.t0_event = torch.cuda.Event(enable_timing=True)
+
+    def close(self):
+        for m in self.maps:
+            m.close()
+        self.maps = []
+
+    # ------------------------------------------------------------------
+    def _launch(self, slot: _Slot, r: Request, now: float):
+        torch = self.torch
+        m = self.maps[r.robot]
+        r.start = now
+        slot.req = r
+        with torch.cuda.stream(slot.stream):
+            if r.kind == "update":
+                n = len(r.labels)
+                if n > self.max_points:
+                    raise ValueError("update larger than the server's slot buffers")
+                slot.xy_h[:n].numpy()[:] = r.xy
+                slot.lab_h[:n].numpy()[:] = r.labels
+                slot.xy[:n].copy_(slot.xy_h[:n], non_blocking=True)
+                slot.lab[:n].copy_(slot.lab_h[:n], non_blocking=True)
+                m.encode_bundle(slot.xy[:n], slot.lab[:n], stream=slot.stream)
+            else:
+                x0, y0, w, h = r.window
+                occ = slot.occ[:w * h].view(h, w)
+                m.query_window(x0, y0, w, h, slot.heat, occ, stream=slot.stream)
+                slot.occ_h[:w * h].copy_(slot.occ[:w * h], non_blocking=True)
+            slot.done.record(slot.stream)
+
+    def _retire(self, slot: _Slot):
+        r = slot.req
+        r.done = self.t0_event.elapsed_time(slot.done) / 1e3
+        if r.kind == "query":
+            x0, y0, w, h = r.window
+            r.result = slot.occ_h[:w * h].numpy().reshape(h, w).copy()
+        slot.req = None
+        return r
+
+    def run(self, requests: list[Request], realtime: bool = True) -> list[Request]:
+        """Serves `requests` (sorted by arrival).  With realtime=False every
+        request counts as arrived at time 0 (a closed batch)."""
+        torch = self.torch
+        torch.cuda.synchronize()
+        self.t0_event.record()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        pending = collections.deque(requests)
+        waiting: list[Request] = []
+        busy = set()
+        finished = []
+        while pending or waiting or any(s.req for s in self.slots):
+            now = time.perf_counter() - t0
+            while pending and (not realtime or pending[0].arrival <= now):
+                waiting.append(pending.popleft())
+            for s in self.slots:
+                if s.req is not None and s.done.query():
+                    busy.discard(s.req.robot)
+                    finished.append(self._retire(s))
+            for s in self.slots:
+                if s.req is not None:
+                    continue
+                pick = next((r for r in waiting if r.robot not in busy), None)
+                if pick is None:
+                    break
+                waiting.remove(pick)
+                busy.add(pick.robot)
+                self._launch(s, pick, now)
+            if not waiting and pending and realtime:
+                gap = pending[0].arrival - (time.perf_counter() - t0)
+                if gap > 2e-4 and not any(s.req for s in self.slots):
+                    time.sleep(gap - 1e-4)
+        return finished
+
+
+def fleet_configs(fleet, D: int = 8192, decode_prec: int = V.DECODE_BF16X3, seed0: int = 5000):
+    """One map configuration per robot of a synth.robot_fleet: the robot's map
+    centred on its world, tiles of 128 cells, l = 0.1 m."""
+    out = []
+    for i, r in enumerate(fleet):
+        half = r.cells * r.res / 2
+        out.append(V.default_config(D=D, grid_w=r.cells, grid_h=r.cells, resolution=r.res,
+                                    x_min=-half, y_min=-half, tiles_x=r.tiles, tiles_y=r.tiles,
+                                    length_scale=0.1, seed=seed0 + i, decode_prec=decode_prec))
+    return out
+
+
+def poisson_requests(fleet, rate: float, duration: float, query_frac: float = 0.5,
+                     seed: int = 0, win_lo: int = 128, win_hi: int = 512) -> list[Request]:
+    """Poisson arrivals at `rate` requests/s for `duration` s over the fleet:
+    scan updates (the robot's next scan) and window queries (128^2 to 512^2)."""
+    from . import synth
+    rng = np.random.default_rng(seed)
+    t, reqs = 0.0, []
+    next_scan = [0] * len(fleet)
+    while True:
+        t += rng.exponential(1.0 / rate)
+        if t > duration:
+            break
+        rb = int(rng.integers(len(fleet)))
+        if rng.uniform() < query_frac:
+            win = synth.window_sizes(rng, fleet[rb].cells, win_lo, win_hi)
+            reqs.append(Request("query", rb, t, window=win))
+        else:
+            xy, lab = fleet[rb].scans[next_scan[rb] % len(fleet[rb].scans)]
+            next_scan[rb] += 1
+            reqs.append(Request("update", rb, t, xy=xy, labels=lab))
+    return reqs
+
+
+def summarize(reqs: list[Request], duration: float) -> dict:
+    out = {}
+    for kind in ("update", "query"):
+        lat = np.array([r.latency for r in reqs if r.kind == kind]) * 1e3
+        if len(lat):
+            out[kind] = {"count": int(len(lat)), "p50_ms": float(np.percentile(lat, 50)),
+                         "p99_ms": float(np.percentile(lat, 99)), "max_ms": float(lat.max())}
+    end = max((r.done for r in reqs), default=0.0)
+    out["requests_per_s"] = len(reqs) / max(end, duration, 1e-9)
+    return out

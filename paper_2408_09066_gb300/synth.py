@@ -179,6 +179,85 @@ def paper_trajectory(seed: int = 1002, D: int = 8192, n_scans: int = 100) -> Wor
                     0.1, seed, w)
 
 
+def _walk_workload(name, seed, half, n_rect, n_disc, rect_size, disc_r, n_scans, beams,
+                   max_range, n_empty, cells, res, tiles, D, length_scale, step=0.5,
+                   sigma=0.03, cells_y=None):
+    rng = np.random.default_rng(seed)
+    w = make_world(rng, half, n_rect, n_disc, rect_size, disc_r, free_r=1.0)
+    poses = trajectory(w, (0.0, 0.0), n_scans, step, rng)
+    parts = [scan(w, p, beams, max_range, sigma, n_empty, rng) for p in poses]
+    xy = np.concatenate([p[0] for p in parts])
+    lab = np.concatenate([p[1] for p in parts])
+    ch = cells_y or cells
+    return Workload(name, xy, lab, cells, ch, res, -cells * res / 2, -ch * res / 2, tiles[0],
+                    tiles[1], D, length_scale, seed, w)
+
+
+def toysim_like(seed: int = 2001, D: int = 16000) -> Workload:
+    """Shaped like the ToySim row of the paper's dataset table: a 100 m x 100 m
+    world, 90 scans of 50 beams, about as many occupied as empty points; with
+    the ToySim parameters d = 32000 (D = 16000), l = 1, delta = 2; 0.25 m cells."""
+    return _walk_workload("toysim_like_400x400_2x2tiles", seed, 50.0, 30, 15, (2.0, 10.0),
+                          (1.0, 4.0), 90, 50, 40.0, 1, 400, 0.25, (2, 2), D, 1.0, step=1.0)
+
+
+def intel_like(seed: int = 2002, D: int = 16000) -> Workload:
+    """Shaped like the Intel Map row: a 38 m x 38 m building-sized world, 910 scans
+    of 421 beams, a little more occupied than empty; d = 32000, l = 0.2,
+    delta = 8, 0.1 m cells."""
+    return _walk_workload("intel_like_380x380_8x8tiles", seed, 19.0, 40, 10, (0.5, 4.0),
+                          (0.3, 1.0), 910, 421, 20.0, 1, 380, 0.1, (8, 8), D, 0.2, step=0.25)
+
+
+def evilog_like(seed: int = 2003, D: int = 16000) -> Workload:
+    """Shaped like the EviLOG row: one 48,000-point frame (2400 beams x 20 points)
+    over 56.32 m x 81.92 m at 0.16 m (352 x 512 cells), d = 32000, l = 0.2,
+    delta = 1."""
+    rng = np.random.default_rng(seed)
+    w = make_world(rng, 41.0, 40, 20, (1.0, 5.0), (0.5, 2.0), free_r=1.0)
+    xy, lab = scan(w, (0.0, 0.0), 2400, 40.0, 0.03, 19, rng)
+    return Workload("evilog_like_352x512_1tile", xy, lab, 352, 512, 0.16, -352 * 0.16 / 2,
+                    -512 * 0.16 / 2, 1, 1, D, 0.2, seed, w)
+
+
+@dataclasses.dataclass
+class Robot:
+    """One robot of a serving fleet: a square map of `cells` x `cells` cells of
+    0.1 m centred on its world, tiles of 128 cells, and a pool of scans."""
+    world: World
+    cells: int
+    res: float
+    tiles: int
+    scans: list            # [(xy float32 [n][2], labels uint8 [n])]
+
+
+def robot_fleet(n_robots: int, seed: int = 1005, min_cells: int = 256, max_cells: int = 1024,
+                scans_per_robot: int = 4, beams: int = 1080, n_empty: int = 20) -> list:
+    """Robots with maps of 256^2 to 1024^2 cells (log-uniform, multiples of 128),
+    each with a random-walk pool of scans of `beams` beams and `n_empty` empty
+    samples per beam (1080 x 21 = 22,680 points per scan)."""
+    rng = np.random.default_rng(seed)
+    fleet = []
+    for _ in range(n_robots):
+        cells = int(np.exp(rng.uniform(np.log(min_cells), np.log(max_cells))) // 128 * 128)
+        cells = max(min_cells, min(max_cells, cells))
+        half = cells * 0.1 / 2
+        w = make_world(rng, half, max(2, cells // 40), max(1, cells // 80), (1.0, 4.0),
+                       (0.4, 1.5), free_r=1.0)
+        poses = trajectory(w, (0.0, 0.0), scans_per_robot, 0.5, rng)
+        rmax = min(30.0, half)
+        scans = [scan(w, p, beams, rmax, 0.03, n_empty, rng) for p in poses]
+        fleet.append(Robot(w, cells, 0.1, cells // 128, scans))
+    return fleet
+
+
+def window_sizes(rng: np.random.Generator, cells: int, lo: int = 128, hi: int = 512):
+    """A random query window (x0, y0, w, h) of lo..hi cells per side inside the map."""
+    w = int(min(cells, rng.integers(lo, hi + 1)))
+    h = int(min(cells, rng.integers(lo, hi + 1)))
+    return (int(rng.integers(0, cells - w + 1)), int(rng.integers(0, cells - h + 1)), w, h)
+
+
 def ground_truth(world: World, W: int, H: int, res: float, x_min: float, y_min: float) -> np.ndarray:
     """Occupancy of each cell centre (1 inside an obstacle or outside the walls)."""
     j, i = np.meshgrid(np.arange(H), np.arange(W), indexing="ij")

@@ -19,6 +19,8 @@ STAGES = ("sort", "encode", "reduce", "norms", "decode", "nonlinear", "entropy")
 OK, E_INVAL, E_NOMEM, E_CUDA, E_TIMEOUT, E_DATA = 0, -1, -2, -3, -4, -5
 DECODE_FP32, DECODE_BF16X3, DECODE_FP16X3 = 0, 1, 2
 FLAG_CHECKED, FLAG_ATOMIC = 1, 2
+MODE_NO_NORM, MODE_NO_SQUARE = 1, 2
+ACT_ENTROPY, ACT_RELU, ACT_TANH, ACT_SIGMOID, ACT_NONE = 0, 16, 32, 48, 64
 
 
 class VsaogmError(RuntimeError):
@@ -35,7 +37,7 @@ class Config(ctypes.Structure):
                 ("tiles_y", ctypes.c_int32), ("length_scale", ctypes.c_float),
                 ("r_occ", ctypes.c_int32), ("r_emp", ctypes.c_int32), ("rho", ctypes.c_float),
                 ("seed", ctypes.c_uint64), ("decode_prec", ctypes.c_int32),
-                ("flags", ctypes.c_uint32)]
+                ("flags", ctypes.c_uint32), ("decode_mode", ctypes.c_uint32)]
 
 
 _lib = None
@@ -52,7 +54,12 @@ _SIGNATURES = {
     "vsaogm_entropy": (ctypes.c_int, [_V, _V, _V, _V, _V, _V]),
     "vsaogm_query": (ctypes.c_int, [_V, _V, _V, _V, _V, _V]),
     "vsaogm_update_query_host": (ctypes.c_int, [_V, _V, _V, ctypes.c_int64, _V, _V]),
+    "vsaogm_query_window": (ctypes.c_int, [_V, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                           ctypes.c_int32, _V, _V, _V, _V, _V]),
+    "vsaogm_window_scratch": (ctypes.c_int, [_V, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                             ctypes.c_int32, _V]),
     "vsaogm_rejected": (ctypes.c_int, [_V, _V, _V]),
+    "vsaogm_reserve": (ctypes.c_int, [_V, ctypes.c_int64]),
     "vsaogm_get_memory": (ctypes.c_int, [_V, _V, _V]),
     "vsaogm_set_memory": (ctypes.c_int, [_V, _V, _V]),
     "vsaogm_fuse": (ctypes.c_int, [_V, _V, _V]),
@@ -194,6 +201,26 @@ class Map:
             _dev(ogm, torch.float32, hw, "ogm") if ogm is not None else None,
             _dev(cls, torch.uint8, hw, "cls") if cls is not None else None, _stream(stream)))
 
+    def window_scratch(self, x0: int, y0: int, w: int, h: int) -> int:
+        """Floats of heat scratch query_window needs for that window."""
+        v = ctypes.c_int64()
+        _check(lib().vsaogm_window_scratch(self._h, x0, y0, w, h, ctypes.byref(v)))
+        return v.value
+
+    def query_window(self, x0: int, y0: int, w: int, h: int, heat, occ, ogm=None, cls=None,
+                     stream=None):
+        """Occupancy of the window [x0, x0+w) x [y0, y0+h) into occ [h][w]; heat is
+        scratch of at least window_scratch(...) floats."""
+        import torch
+        need = self.window_scratch(x0, y0, w, h)
+        if not (isinstance(heat, torch.Tensor) and heat.is_cuda and heat.dtype == torch.float32
+                and heat.is_contiguous() and heat.numel() >= need):
+            raise ValueError(f"heat must be a contiguous CUDA float32 tensor of >= {need} elements")
+        _check(lib().vsaogm_query_window(
+            self._h, x0, y0, w, h, _V(heat.data_ptr()), _dev(occ, torch.float32, (h, w), "occ"),
+            _dev(ogm, torch.float32, (h, w), "ogm") if ogm is not None else None,
+            _dev(cls, torch.uint8, (h, w), "cls") if cls is not None else None, _stream(stream)))
+
     def update_query_host(self, xy: np.ndarray, labels: np.ndarray, occ: np.ndarray, stream=None):
         """Host arrays in and out: xy float32 [n][2], labels uint8 [n], occ float32 [H][W]."""
         for a, dt in ((xy, np.float32), (labels, np.uint8), (occ, np.float32)):
@@ -205,6 +232,11 @@ class Map:
                                               len(labels), _V(occ.ctypes.data), _stream(stream)))
 
     # -- state --------------------------------------------------------------
+    def reserve(self, max_points: int):
+        """Grow scratch now so that later calls with up to max_points points
+        (and any query) allocate nothing."""
+        _check(lib().vsaogm_reserve(self._h, int(max_points)))
+
     def rejected(self, stream=None) -> int:
         v = ctypes.c_int64()
         _check(lib().vsaogm_rejected(self._h, ctypes.byref(v), _stream(stream)))

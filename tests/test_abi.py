@@ -39,7 +39,7 @@ def test_library_exports_every_declared_symbol(L):
 
 
 def test_config_layout_and_defaults(L):
-    assert ctypes.sizeof(V.Config) == 64
+    assert ctypes.sizeof(V.Config) == 72
     c = V.default_config()
     assert (c.D, c.grid_w, c.grid_h, c.tiles_x, c.tiles_y, c.r_occ, c.r_emp) == (8192, 400, 400, 4, 4, 3, 3)
     assert abs(c.resolution - 0.1) < 1e-7 and abs(c.length_scale - 0.1) < 1e-7

@@ -120,13 +120,17 @@ def test_single_point_phasors_anywhere(x, y):
                            f"want {want['omega'][:, k]}")
 
 
-@pytest.mark.parametrize("poly", [0, 1, 2, 3])
+@pytest.mark.parametrize("packed,poly,poly_warps",
+                         [(0, 0, 0), (1, 0, 0), (1, 1, 0), (1, 2, 0), (1, 3, 0), (1, 0, 3),
+                          (1, 0, 8), (1, 0, -1)])
 @pytest.mark.parametrize("D", [1000, 8192])
-def test_packed_encode_variants(monkeypatch, poly, D):
-    """The f32x2 encode kernel with 0..3 frequency pairs per thread on the FMA-pipe
-    polynomial matches the oracle like the scalar kernel, near and far points."""
-    monkeypatch.setenv("VSAOGM_ENCODE_PACKED", "1")
+def test_encode_kernel_variants(monkeypatch, packed, poly, poly_warps, D):
+    """The scalar encode kernel and the f32x2 one with 0..3 frequency pairs per
+    thread on the FMA-pipe polynomial (or one pair in some warps only; -1 is
+    the automatic share) match the oracle, near and far points."""
+    monkeypatch.setenv("VSAOGM_ENCODE_PACKED", str(packed))
     monkeypatch.setenv("VSAOGM_ENCODE_POLY", str(poly))
+    monkeypatch.setenv("VSAOGM_ENCODE_POLY_WARPS", str(poly_warps))
     wl = synth.small_scan(seed=31, D=D)
     far = np.array([[-100.0, 50.0], [40.0, -3.0]], np.float32)
     xy = np.concatenate([wl.xy, far])

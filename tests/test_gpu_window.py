@@ -1,0 +1,82 @@
+"""Local map queries (vsaogm_query_window) against the oracle's window query,
+for the FP32 and the tensor-core decodes: corner, edge, interior and whole-map
+windows, several radii."""
+import numpy as np
+import pytest
+
+import oracle
+from helpers import config_for, oracle_grid
+from paper_2408_09066_gb300 import synth
+from paper_2408_09066_gb300 import vsaogm as V
+
+pytestmark = pytest.mark.gpu
+
+TOL_PR = 1e-3
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    from paper_2408_09066_gb300 import build
+    build.build()
+
+
+WINDOWS = [(0, 0, 20, 17), (40, 3, 24, 30), (10, 12, 33, 40), (0, 0, 64, 64), (63, 63, 1, 1)]
+
+
+@pytest.mark.parametrize("prec", [V.DECODE_FP32, V.DECODE_BF16X3])
+@pytest.mark.parametrize("radii", [(3, 3), (1, 5)])
+def test_window_queries_match_oracle(prec, radii):
+    import torch
+    wl = synth.small_scan(seed=77)
+    cfg = config_for(wl, tiles_x=2, tiles_y=2, r_occ=radii[0], r_emp=radii[1], decode_prec=prec)
+    dev = torch.device("cuda")
+    g = oracle_grid(cfg)
+    nx, ny = oracle.draw_nu(cfg.seed, cfg.D, float(np.float32(cfg.length_scale)))
+    om = oracle.memories(g, nx, ny, wl.xy, wl.labels, "tile")
+    with V.Map(cfg) as m:
+        m.encode_bundle(torch.from_numpy(wl.xy).to(dev), torch.from_numpy(wl.labels).to(dev))
+        for (x0, y0, w, h) in WINDOWS:
+            heat = torch.empty(m.window_scratch(x0, y0, w, h), dtype=torch.float32, device=dev)
+            occ = torch.empty((h, w), dtype=torch.float32, device=dev)
+            ogm = torch.empty((h, w), dtype=torch.float32, device=dev)
+            cls = torch.empty((h, w), dtype=torch.uint8, device=dev)
+            m.query_window(x0, y0, w, h, heat, occ, ogm, cls)
+            torch.cuda.synchronize()
+            m.status()
+            want = oracle.query_window(g, nx, ny, om, x0, y0, w, h, cfg.r_occ, cfg.r_emp)
+            P = heat[:want["P"].size].cpu().numpy().reshape(want["P"].shape)
+            perr = np.abs(P - want["P"]).max() / np.abs(want["P"]).max()
+            assert perr <= 1e-4, (x0, y0, w, h, perr, P.reshape(2, -1).max(1), want["maxima"])
+            assert np.abs(occ.cpu().numpy() - want["pr1"]).max() <= TOL_PR, (x0, y0, w, h)
+            assert np.abs(ogm.cpu().numpy() - want["ogm"]).max() <= 2 * TOL_PR
+            assert np.array_equal(cls.cpu().numpy(),
+                                  oracle.classify_f32(ogm.cpu().numpy(), cfg.rho))
+
+
+def test_whole_map_window_equals_map_query():
+    import torch
+    wl = synth.small_scan(seed=78)
+    cfg = config_for(wl, tiles_x=2, tiles_y=2)
+    dev = torch.device("cuda")
+    with V.Map(cfg) as m:
+        m.encode_bundle(torch.from_numpy(wl.xy).to(dev), torch.from_numpy(wl.labels).to(dev))
+        heat = torch.empty((2, wl.H, wl.W), dtype=torch.float32, device=dev)
+        occ = torch.empty((wl.H, wl.W), dtype=torch.float32, device=dev)
+        m.query(heat, occ)
+        heat2 = torch.empty(m.window_scratch(0, 0, wl.W, wl.H), dtype=torch.float32, device=dev)
+        occ2 = torch.empty((wl.H, wl.W), dtype=torch.float32, device=dev)
+        m.query_window(0, 0, wl.W, wl.H, heat2, occ2)
+        torch.cuda.synchronize()
+        assert torch.equal(occ, occ2)
+
+
+def test_window_outside_the_map_is_rejected():
+    wl = synth.small_scan(seed=79)
+    with V.Map(config_for(wl)) as m:
+        for bad in [(-1, 0, 4, 4), (0, 0, 65, 4), (60, 60, 5, 1), (0, 0, 0, 3)]:
+            with pytest.raises(V.VsaogmError) as ei:
+                m.window_scratch(*bad)
+            assert ei.value.code == V.E_INVAL

@@ -302,6 +302,28 @@ def test_classification_threshold_inclusive_in_float32():
     assert oracle.classify_f32(ogm, 0.0).tolist() == [0, 1, 1, 1, 1]
 
 
+def test_decoding_ablation_variants():
+    """Sec. IV-D1 toggles: all on with the entropy is the paper's pipeline; with no
+    activation the two-class softmax is sigma(P_hat_1 - P_hat_0); ReLU of a
+    non-negative square is the identity; the entropy ignores negative values."""
+    from scipy.special import expit
+    rng = np.random.default_rng(12)
+    P = rng.normal(size=(2, 9, 11))
+    Ph, mx = oracle.nonlinear(P)
+    full = oracle.softmax_psd(oracle.entropy(Ph[0], 2), oracle.entropy(Ph[1], 3))
+    var = oracle.decode_variant(P, True, True, "entropy", 3, 2)
+    for u, v in zip(full, var):
+        assert np.allclose(u, v, atol=1e-15)
+    pr1, _, ogm = oracle.decode_variant(P, True, True, "none", 3, 2)
+    assert np.allclose(pr1, expit(Ph[1] - Ph[0]), atol=1e-15)
+    relu = oracle.decode_variant(P, True, True, "relu", 3, 2)
+    assert np.allclose(relu[0], pr1, atol=1e-15)
+    pr1t, _, _ = oracle.decode_variant(P, False, False, "tanh", 3, 2)
+    assert np.allclose(pr1t, expit(np.tanh(P[1]) - np.tanh(P[0])), atol=1e-15)
+    neg = -np.abs(P[0])
+    assert np.all(oracle.entropy(neg, 2) == 0.0)
+
+
 def test_window_query_over_the_whole_map_is_the_map_query():
     """A window covering the map decodes the map: it reduces to the full pipeline."""
     g = Grid(W=20, H=14, res=0.2, x_min=-2.0, y_min=-1.4, tiles_x=2, tiles_y=2)
