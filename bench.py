@@ -54,9 +54,12 @@ def parse_args():
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--decode", choices=["fp32", "bf16x3", "fp16x3"], default="bf16x3",
                    help="decode arithmetic of the headline path (fp32 plain is also timed)")
-    p.add_argument("--workload", choices=["paper", "toysim", "intel", "evilog"], default="paper",
-                   help="paper: the 400x400 / 4x4 / D=8192 / 2.27M-point map; the others are "
-                        "shaped like the paper's dataset table (context rows)")
+    p.add_argument("--workload", choices=["paper", "toysim", "intel", "evilog", "batch64"],
+                   default="paper",
+                   help="paper: the 400x400 / 4x4 / D=8192 / 2.27M-point map; toysim, intel, "
+                        "evilog: shaped like the paper's dataset table (context rows); batch64: "
+                        "64 maps of uneven size stepped together (one launch per stage, CUDA "
+                        "graph, autotuned)")
     p.add_argument("--no-cpu-baseline", action="store_true",
                    help="skip the oracle timing (for quick runs)")
     return p.parse_args()
@@ -506,8 +509,284 @@ def run_ours(args):
     return 0
 
 
+# --------------------------------------------------------------------------- 64-map batch
+BATCH_DATA = ("synthetic: 64 seeded lidar maps, 64^2-1024^2 cells at 0.1 m (log-uniform), 1..8 "
+              "tiles per axis, D in {2048, 4096, 8192}, 10k-500k points each (log-uniform; "
+              "360 beams, 10 empty samples per beam, sigma 0.02 m, random walk)")
+
+
+def batch_config(wls, tune=None) -> dict:
+    n = sum(len(w.labels) for w in wls)
+    cells = sum(w.W * w.H for w in wls)
+    return {"workload": f"64-map batch: {len(wls)} maps, {n} points, {cells} cells, "
+                        f"sum n*D = {sum(len(w.labels) * w.D for w in wls):.4g}, "
+                        f"sum cells*D = {sum(w.W * w.H * w.D for w in wls):.4g}",
+            "maps": len(wls), "points_per_step": n, "cells_per_step": cells,
+            "grid_range": [min(w.W for w in wls), max(w.W for w in wls)],
+            "D_values": sorted({w.D for w in wls}),
+            "tiles_total": sum(w.tiles_x * w.tiles_y for w in wls), "decode": "bf16x3",
+            "launch": "one CUDA graph per step: per-map sorts on 8 streams, then one launch "
+                      "per stage for all maps", "autotuned": tune,
+            "l2": "flushed between timed steps (256 MB device write outside the step events)",
+            "parallelism": "one independent 64-map batch per GPU"}
+
+
+def batch_oracle_plan(wls, budget_s: float, rng):
+    """Three maps of the batch and, for each, oracle sample sizes of about
+    budget_s / 3 seconds (bounded probes, as for the single map)."""
+    picks = [int(i) for i in rng.choice(len(wls), 3, replace=False)]
+    return [(i, *calibrate_oracle(wls[i], budget_s / 3, rng)) for i in sorted(picks)]
+
+
+def batch_oracle_time(wls, plan, rng):
+    """The oracle's cost per point-frequency (encode + bundle) and per
+    cell-frequency (decode), measured on the planned bounded samples, and its
+    entropy pass per cell; extrapolated to the whole batch (costs are linear in
+    n*D and in cells*D).  Returns (seconds, text)."""
+    import numpy as np
+    per_pd, per_cd, ent_per_cell = [], [], []
+    for i, n_pts, n_cells in plan:
+        w = wls[i]
+        _, parts = oracle_step_time(w, n_pts, n_cells, rng)
+        per_pd.append(parts["encode_s"] / (n_pts * w.D))
+        per_cd.append(parts["decode_s"] / (n_cells * w.D))
+        ent_per_cell.append(parts["entropy_s"] / (w.W * w.H))
+    c_pd, c_cd, c_e = (float(np.mean(x)) for x in (per_pd, per_cd, ent_per_cell))
+    total = sum(c_pd * len(w.labels) * w.D + (c_cd * w.D + c_e) * w.W * w.H for w in wls)
+    text = (f"FP64 oracle on bounded samples of maps {[p[0] for p in plan]} "
+            f"({[p[1] for p in plan]} random points x all frequencies, {[p[2] for p in plan]} "
+            f"random cells, full-grid entropy); per point-frequency {c_pd:.3g} s, per "
+            f"cell-frequency {c_cd:.3g} s, entropy {c_e:.3g} s per cell; extrapolated to the "
+            f"{len(wls)} maps")
+    return total, text
+
+
+def run_batch(args):
+    import numpy as np
+    import torch
+
+    from paper_2408_09066_gb300 import build, synth
+    from paper_2408_09066_gb300 import vsaogm as V
+    d = Dist("nccl" if int(os.environ.get("WORLD_SIZE", "1")) > 1 else None)
+    torch.cuda.set_device(d.local)
+    if d.local == 0:
+        build.build()
+    d.barrier()
+    dev = torch.device("cuda", d.local)
+    wls = synth.batch_maps(seed=1004 + d.rank)
+    n_total = sum(len(w.labels) for w in wls)
+    cells_total = sum(w.W * w.H for w in wls)
+
+    def cfg(w, prec):
+        return V.default_config(D=w.D, grid_w=w.W, grid_h=w.H, resolution=w.res,
+                                x_min=w.x_min, y_min=w.y_min, tiles_x=w.tiles_x,
+                                tiles_y=w.tiles_y, length_scale=w.length_scale, seed=w.seed,
+                                decode_prec=prec)
+
+    xy = [torch.from_numpy(w.xy).to(dev) for w in wls]
+    lab = [torch.from_numpy(w.labels).to(dev) for w in wls]
+    heat = [torch.empty((2, w.H, w.W), dtype=torch.float32, device=dev) for w in wls]
+    occ = [torch.empty((w.H, w.W), dtype=torch.float32, device=dev) for w in wls]
+    ogm = [torch.empty((w.H, w.W), dtype=torch.float32, device=dev) for w in wls]
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+    s = torch.cuda.Stream(dev)
+    bus = None
+    try:
+        bus = torch.cuda.get_device_properties(dev).pci_bus_id
+    except Exception:
+        pass
+
+    def timed(step, steps, warmup, clocks=None):
+        for _ in range(warmup):
+            step()
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(steps)]
+        d.barrier()
+        torch.cuda.synchronize()
+        if clocks:
+            clocks.start()
+        for i in range(steps):
+            with torch.cuda.stream(s):
+                flush.fill_(float(i))
+            ev[i][0].record(s)
+            step()
+            ev[i][1].record(s)
+        torch.cuda.synchronize()
+        d.barrier()
+        clk = clocks.stop() if clocks else None
+        return [a.elapsed_time(b) for a, b in ev], clk
+
+    # 1. the same maps stepped one at a time: FP32 plain decode, and BF16x3
+    loops = {}
+    for name, prec in (("fp32_plain_per_map", V.DECODE_FP32),
+                       ("bf16x3_per_map", V.DECODE_BF16X3)):
+        maps = [V.Map(cfg(w, prec)) for w in wls]
+
+        def loop_step(maps=maps):
+            for i, m in enumerate(maps):
+                m.reset(s)
+                m.encode_bundle(xy[i], lab[i], s)
+                m.query(heat[i], occ[i], ogm[i], stream=s)
+
+        ms, _ = timed(loop_step, max(3, args.steps // 4), args.warmup)
+        tot = d.max(sum(ms) / 1e3)
+        loops[name] = {"value": d.sum(float(n_total * len(ms))) / tot, "unit": "points/s",
+                       "ms_per_step": tot / len(ms) * 1e3, "p50_ms": percentile(ms, 50),
+                       "p99_ms": percentile(ms, 99), "launch": "one map after another"}
+        for m in maps:
+            m.close()
+
+    # 2. the batch: autotune, per-stage timing (uncaptured steps), then graph replays
+    maps = [V.Map(cfg(w, V.DECODE_BF16X3)) for w in wls]
+    batch = V.Batch(maps)
+    tune = batch.autotune(xy, lab, heat, occ, stream=s)
+    batch.set_timing(True)
+    for _ in range(args.warmup):
+        batch.step(xy, lab, heat, occ, ogm, stream=s)
+    batch.stage_times(reset=True)
+    n_stage = max(3, args.steps // 4)
+    for i in range(n_stage):
+        with torch.cuda.stream(s):
+            flush.fill_(float(i))
+        batch.step(xy, lab, heat, occ, ogm, stream=s)
+    stages = batch.stage_times(reset=True)
+    batch.set_timing(False)
+    batch.capture(xy, lab, heat, occ, ogm, stream=s)
+    batch.stage_times(reset=True)
+    step_ms, clk = timed(lambda: batch.replay(s), args.steps, args.warmup, ClockSampler(bus))
+    launches = sum(v[1] for v in batch.stage_times(reset=True).values()) / (
+        args.steps + args.warmup)
+    batch.status()
+    total_s = d.max(sum(step_ms) / 1e3)
+    value = d.sum(float(n_total * args.steps)) / total_s
+
+    # 3. end to end: pinned host points in, occupancy maps out, around each replay
+    xy_h = [torch.from_numpy(w.xy).pin_memory() for w in wls]
+    lab_h = [torch.from_numpy(w.labels).pin_memory() for w in wls]
+    occ_h = [torch.empty((w.H, w.W), dtype=torch.float32).pin_memory() for w in wls]
+
+    def e2e_step():
+        with torch.cuda.stream(s):
+            for i in range(len(wls)):
+                xy[i].copy_(xy_h[i], non_blocking=True)
+                lab[i].copy_(lab_h[i], non_blocking=True)
+            batch.replay(s)
+            for i in range(len(wls)):
+                occ_h[i].copy_(occ[i], non_blocking=True)
+        s.synchronize()
+
+    for _ in range(max(1, args.warmup)):
+        e2e_step()
+    e2e_s = []
+    for i in range(args.steps):
+        flush.fill_(float(i))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        e2e_step()
+        e2e_s.append(time.perf_counter() - t0)
+    e2e_total = d.max(sum(e2e_s))
+
+    # rooflines from the per-stage times of the uncaptured steps
+    peaks = measured_peaks()
+    exps = float(sum(len(w.labels) * w.D for w in wls))
+    enc_s = stages["encode"][0] / 1e3 / n_stage
+    sm_hz = SMS * SM_MAX_MHZ * 1e6
+    a = (2 * FP32_FMA_PER_SM_CLK / MUFU_PER_SM_CLK - MUFU_PATH_FMA) / (
+        2 * FP32_FMA_PER_SM_CLK / MUFU_PER_SM_CLK - MUFU_PATH_FMA + POLY_PATH_FMA)
+    peak_joint = sm_hz / (2.0 * (1.0 - a) / MUFU_PER_SM_CLK) / 1e9
+    achieved = exps / enc_s / 1e9
+    roofline = {"bound": "alu", "kernel": "encode_batch_kernel", "achieved": achieved,
+                "peak": peak_joint, "unit": "Gexp/s", "frac": achieved / peak_joint,
+                "traffic": None, "peak_mufu_only": sm_hz * MUFU_PER_SM_CLK / 2.0 / 1e9,
+                "peak_basis": "as the single-map encode: MUFU + FMA pipes, 152 SMs x 2070 MHz"}
+    dec_s = stages["decode"][0] / 1e3 / n_stage
+    flops = 3 * 8.0 * sum(w.W * w.H * w.D for w in wls)
+    ent_s = stages["entropy"][0] / 1e3 / n_stage
+    ent_bytes = 16.0 * cells_total
+    other = {
+        "decode_bf16x3_batch": {
+            "bound": "tensor", "achieved": flops / dec_s / 1e12, "peak": peaks["bf16_tflops"],
+            "unit": "TFLOP/s", "frac": flops / dec_s / 1e12 / peaks["bf16_tflops"],
+            "kernels": "decode_tc_batch_kernel + slice sums",
+            "work": "3 split products x 8 flops per cell, class pair and frequency"},
+        "entropy_batch": {
+            "bound": "hbm", "achieved": ent_bytes / ent_s / 1e9, "peak": peaks["hbm_gbs"],
+            "unit": "GB/s", "frac": ent_bytes / ent_s / 1e9 / peaks["hbm_gbs"],
+            "work": "16 B per cell: two class maps read, occupancy and signed difference written"},
+    }
+    line = {
+        "metric": METRIC, "value": value, "unit": "points/s", "n_gpus": d.world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_s / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": BATCH_DATA, "config": batch_config(wls, tune),
+        "cells_per_s": d.sum(float(cells_total * args.steps)) / total_s,
+        "p50_ms": percentile(step_ms, 50), "p99_ms": percentile(step_ms, 99),
+        "stage_ms_per_step": {k: v[0] / n_stage for k, v in stages.items()},
+        "per_map_loops": loops,
+        "e2e": {"value": d.sum(float(n_total * args.steps)) / e2e_total, "unit": "points/s",
+                "h2d_bytes_per_step": int(sum(w.xy.nbytes + w.labels.nbytes for w in wls)),
+                "d2h_bytes_per_step": int(4 * cells_total),
+                "p50_ms": percentile(e2e_s, 50) * 1e3, "p99_ms": percentile(e2e_s, 99) * 1e3},
+        "roofline": roofline, "rooflines_other": other, "gpu_launches": int(launches),
+        "clocks": clk,
+    }
+    batch.close()
+    for m in maps:
+        m.close()
+    if d.rank == 0 and d.world == 1 and not args.no_cpu_baseline:
+        import oracle
+        rng = np.random.default_rng(7)
+        t, text = batch_oracle_time(wls, batch_oracle_plan(wls, 12.0, rng), rng)
+        line["cpu_baseline"] = {"value": n_total / t, "unit": "points/s",
+                                "cores": oracle.num_threads(), "kind": "oracle",
+                                "sample": text, "step_s_extrapolated": t}
+    if d.rank == 0:
+        print(json.dumps(line), flush=True)
+    d.close()
+    return 0
+
+
+def run_reference_batch(args):
+    """The FP64 CPU oracle on the 64-map batch, bounded samples per step."""
+    import numpy as np
+
+    import oracle
+    from paper_2408_09066_gb300 import synth
+    if int(os.environ.get("RANK", "0")) != 0:
+        return 0
+    oracle.build()
+    wls = synth.batch_maps(seed=1004)
+    rng = np.random.default_rng(11)
+    n_total = sum(len(w.labels) for w in wls)
+    plan = batch_oracle_plan(wls, 1.5, rng)
+    for _ in range(args.warmup):
+        batch_oracle_time(wls, plan, rng)
+    steps, text = [], ""
+    for _ in range(args.steps):
+        t, text = batch_oracle_time(wls, plan, rng)
+        steps.append(t)
+    mean_s = sum(steps) / len(steps)
+    value = n_total / mean_s
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "points/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": mean_s * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": BATCH_DATA,
+        "config": batch_config(wls, None),
+        "p50_ms": percentile(steps, 50) * 1e3, "p99_ms": percentile(steps, 99) * 1e3,
+        "e2e": {"value": value, "unit": "points/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+        "cpu_baseline": {"value": value, "unit": "points/s", "cores": oracle.num_threads(),
+                         "kind": "oracle", "sample": text},
+        "gpu_launches": 0}), flush=True)
+    return 0
+
+
 def main():
     args = parse_args()
+    if args.workload == "batch64":
+        return run_reference_batch(args) if args.impl == "reference" else run_batch(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

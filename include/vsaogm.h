@@ -257,6 +257,91 @@ int vsaogm_set_timing(vsaogm_map *map, int enable);
  * every stream the timed calls used.  Errors: E_INVAL, E_CUDA.               */
 int vsaogm_stage_times(vsaogm_map *map, double *ms, int64_t *launches, int reset);
 
+/* Batches: many maps in one step.  The paper runs one map per call; a batch
+ * runs the same stages (Algorithm 1 and Sec. III-B4 encode + bundle, then
+ * Eqs. vector-normalization and loc-query, the non-linearities, Algorithm 2
+ * and Eqs. softmax, psd, classification) for up to VSAOGM_MAX_BATCH maps with
+ * one kernel launch per stage across all maps, so that small maps share the
+ * GPU instead of each leaving most SMs idle.  Results equal those of
+ * vsaogm_encode_bundle followed by vsaogm_query on each map up to the
+ * summation order inside each memory (one fixed order per map shape and point
+ * set: a batch is deterministic run to run) and the decode slicing.
+ *  - A batch refers to its maps; they must outlive it and keep their
+ *    configuration.  Every map needs decode_prec BF16X3 or FP16X3 (the same
+ *    for all), the deterministic bundling (no VSAOGM_FLAG_ATOMIC) and one
+ *    device.  The batch owns its own scratch, so per-map calls on its maps
+ *    never move memory a captured step uses.
+ *  - Per-map arrays (xy_dev, labels_dev, n, heat_dev, occ_dev, ogm_dev) have
+ *    `count` entries, in the order of `maps`.  n[i] = 0 skips map i's encode
+ *    (its query still runs).  heat_dev[i]: float [2][H_i][W_i] receiving P;
+ *    occ_dev[i], ogm_dev[i] (ogm_dev or its entries nullable): float
+ *    [H_i][W_i] as vsaogm_query.  `reset` non-zero clears each map's memories
+ *    first (a fresh map per step); zero accumulates into them.
+ *  - Steps of one batch are not thread-safe and must be ordered (one stream).
+ *  - Errors: E_INVAL, E_NOMEM, E_CUDA.  Device-side timeouts are reported by
+ *    vsaogm_status on the maps.                                             */
+#define VSAOGM_MAX_BATCH 64
+typedef struct vsaogm_batch vsaogm_batch;
+
+/* Creates a batch over maps[0..count-1] (1 <= count <= VSAOGM_MAX_BATCH,
+ * distinct maps).  Allocates a few small device buffers and 8 streams used
+ * for the per-map sorts.                                                   */
+int vsaogm_batch_create(vsaogm_map *const *maps, int32_t count, vsaogm_batch **out);
+
+/* Frees the batch (synchronises the device); the maps stay.  NULL is a no-op. */
+int vsaogm_batch_destroy(vsaogm_batch *batch);
+
+/* One step on `stream`: optional reset, encode + bundle of every map's
+ * points, then the query of every map.  Scratch grows on the first step and
+ * whenever a step needs more (cudaMalloc synchronises the device); a step
+ * that grows it also drops a captured step, whose graph held the old
+ * buffers (vsaogm_batch_replay then fails with E_INVAL until the next
+ * capture).                                                                */
+int vsaogm_batch_step(vsaogm_batch *batch, const float *const *xy_dev,
+                      const uint8_t *const *labels_dev, const int64_t *n,
+                      float *const *heat_dev, float *const *occ_dev, float *const *ogm_dev,
+                      int32_t reset, void *stream);
+
+/* Runs one step as vsaogm_batch_step (growing the scratch), then captures
+ * the same step into a CUDA graph for vsaogm_batch_replay.  The graph keeps
+ * every pointer and count given here: a replay reads the same input buffers
+ * (the caller refills them in place with exactly n[i] points each; the point
+ * counts and chunk sizes are part of the graph) and writes the same outputs.
+ * `stream` must not be the default stream.  Stage
+ * timing must be off on every map.  Replaces a previous capture.            */
+int vsaogm_batch_capture(vsaogm_batch *batch, const float *const *xy_dev,
+                         const uint8_t *const *labels_dev, const int64_t *n,
+                         float *const *heat_dev, float *const *occ_dev,
+                         float *const *ogm_dev, int32_t reset, void *stream);
+
+/* Launches the captured step on `stream`.  E_INVAL if nothing is captured. */
+int vsaogm_batch_replay(vsaogm_batch *batch, void *stream);
+
+/* Times candidate shapes of the batched step on these inputs (each a few
+ * steps with reset, so the maps' memories are overwritten) and keeps the
+ * fastest: the share of phasors the encode evaluates by polynomial instead
+ * of the special-function unit, the encode work per persistent CTA (which
+ * sets the chunk size) and the decode work items per SM.  Synchronous.
+ * Drops a captured step (capture again after tuning).  Outputs (nullable):
+ * the chosen values.                                                        */
+int vsaogm_batch_autotune(vsaogm_batch *batch, const float *const *xy_dev,
+                          const uint8_t *const *labels_dev, const int64_t *n,
+                          float *const *heat_dev, float *const *occ_dev, void *stream,
+                          int32_t *poly_warps, int32_t *items_per_cta, int32_t *decode_waves);
+
+/* Stage timing of a batch (tracing): when on, vsaogm_batch_step records CUDA
+ * events between its stages on the step's stream.  Stages as VSAOGM_STAGE_*:
+ * SORT (with the reset), ENCODE, REDUCE, NORMS, DECODE (with the slice sums
+ * and maxima) and ENTROPY (with the fused non-linearity; NONLINEAR stays 0).
+ * Replays are not timed per stage; their kernels are counted.               */
+int vsaogm_batch_set_timing(vsaogm_batch *batch, int32_t enable);
+
+/* Accumulated milliseconds and kernel launches per stage (both nullable,
+ * VSAOGM_N_STAGES entries) since the last reset; resets them when `reset` is
+ * non-zero.  Synchronises with the timed steps.  Errors: E_INVAL, E_CUDA.   */
+int vsaogm_batch_stage_times(vsaogm_batch *batch, double *ms, int64_t *launches,
+                             int32_t reset);
+
 /* Description of the last error on the calling thread ("" if none). */
 const char *vsaogm_last_error(void);
 

@@ -19,7 +19,7 @@ CSRC = os.path.join(HERE, "csrc")
 OBJ = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libvsaogm.so")
 INCLUDE = os.path.join(ROOT, "include")
-SOURCES = ["vsaogm.cu", "encode.cu", "decode.cu", "decode_tc.cu", "entropy.cu"]
+SOURCES = ["vsaogm.cu", "encode.cu", "decode.cu", "decode_tc.cu", "entropy.cu", "batch.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -183,6 +183,64 @@ __global__ void nonlinear_kernel(float *__restrict__ heat, size_t cells,
     }
 }
 
+// ---- batched forms (many maps per launch) ----
+__global__ void __launch_bounds__(256) norms_batch_kernel(const __grid_constant__ BatchNormTable tab)
+{
+    const int gs = blockIdx.x;
+    int lo = 0, hi = tab.n_maps - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (tab.m[mid].mem_begin <= gs) lo = mid; else hi = mid - 1;
+    }
+    const BatchNormMap &M = tab.m[lo];
+    const int s = gs - M.mem_begin;
+    float acc = 0.f;
+    for (int k = threadIdx.x; k < M.D; k += blockDim.x) {
+        float2 w = M.omega[(size_t)s * M.D + k];
+        acc = fmaf(w.x, w.x, fmaf(w.y, w.y, acc));
+    }
+    __shared__ float red[8];
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float t = 0.f;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+        M.inv_norm[s] = t > 0.f ? rsqrtf(t) : 0.f;
+    }
+}
+
+__global__ void zero_maxima_batch_kernel(const __grid_constant__ BatchOutTable tab)
+{
+    const int i = threadIdx.x;
+    if (i < tab.n_maps) {
+        tab.m[i].maxima[0] = 0u;
+        tab.m[i].maxima[1] = 0u;
+    }
+}
+
+// blockIdx.y is the map: its slices summed in order, scaled, and the maxima.
+__global__ void __launch_bounds__(256) reduce_slices_batch_kernel(const __grid_constant__ BatchOutTable tab)
+{
+    const BatchMapOut &M = tab.m[blockIdx.y];
+    const size_t cells = (size_t)M.W * M.H;
+    float mx[2] = {-INFINITY, -INFINITY};
+    for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < 2 * cells;
+         q += (size_t)gridDim.x * blockDim.x) {
+        float s = 0.f;
+        for (int sp = 0; sp < M.splits; ++sp) s += M.partial[(size_t)sp * 2 * cells + q];
+        s *= M.inv_scale;
+        M.heat[q] = s;
+        int c = q < cells ? 0 : 1;
+        mx[c] = fmaxf(mx[c], s);
+    }
+    for (int c = 0; c < 2; ++c) {
+        float m = mx[c];
+        for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+        if ((threadIdx.x & 31) == 0 && m > -INFINITY) atomicMax(&M.maxima[c], float_to_ordered(m));
+    }
+}
+
 __global__ void add_kernel(float2 *__restrict__ dst, const float2 *__restrict__ src, size_t n)
 {
     for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < n;
@@ -293,6 +351,22 @@ int apply_nonlinearity(vsaogm_map *m, float *heat, cudaStream_t st)
     if (e != cudaSuccess) return cuda_error(e, "decode: non-linearity");
     sc.end(1);
     return VSAOGM_OK;
+}
+
+int launch_norms_batch(const BatchNormTable &tab, int total_memories, cudaStream_t st)
+{
+    norms_batch_kernel<<<total_memories, 256, 0, st>>>(tab);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? VSAOGM_OK : cuda_error(e, "batch norms");
+}
+
+int launch_sums_batch(const BatchOutTable &tab, size_t max_cells, cudaStream_t st)
+{
+    zero_maxima_batch_kernel<<<1, kMaxBatchMaps, 0, st>>>(tab);
+    const int bx = (int)std::max<size_t>(1, std::min<size_t>((2 * max_cells + 255) / 256, 64));
+    reduce_slices_batch_kernel<<<dim3(bx, tab.n_maps), 256, 0, st>>>(tab);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? VSAOGM_OK : cuda_error(e, "batch slice sums");
 }
 
 int add_memories(float2 *dst, const float2 *src, int64_t count, cudaStream_t st)

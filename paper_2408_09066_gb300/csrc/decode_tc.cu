@@ -83,12 +83,13 @@ __device__ __forceinline__ void split2(float x, float y, uint32_t &hi, uint32_t 
     }
 }
 
+// One (block of cells, frequency slice) item, executed by the whole CTA.
 template <bool BF16>
-__global__ void __launch_bounds__(256, 1) decode_tc_kernel(
-    const BlockBatch blocks, const float2 *__restrict__ omega, const float *__restrict__ inv_norm,
-    const float *__restrict__ nu, int D, OutGeom og, const float *__restrict__ col_off,
-    const float *__restrict__ row_off, int k_per_split, int N, float u_scale,
-    float *__restrict__ partial, int *__restrict__ status)
+__device__ __forceinline__ void decode_tc_body(
+    const DecodeBlock b, const int split, const float2 *__restrict__ omega,
+    const float *__restrict__ inv_norm, const float *__restrict__ nu, int D, OutGeom og,
+    const float *__restrict__ col_off, const float *__restrict__ row_off, int k_per_split, int N,
+    float u_scale, float *__restrict__ partial, int *__restrict__ status)
 {
     extern __shared__ uint8_t smem_raw[];
     __shared__ uint64_t empty_bar[2], done_bar;
@@ -98,8 +99,6 @@ __global__ void __launch_bounds__(256, 1) decode_tc_kernel(
     const int stage_bytes = kAStage + 2 * N * kRowBytes;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const DecodeBlock b = blocks.b[blockIdx.x];
-    const int split = blockIdx.y;
     const int k_begin = split * k_per_split;
     const int k_end = min(D, k_begin + k_per_split);
     const int n_stages = (k_end - k_begin + kKS - 1) / kKS;
@@ -235,7 +234,58 @@ __global__ void __launch_bounds__(256, 1) decode_tc_kernel(
     if (warp == 0) tmem_dealloc(tmem, kTmemCols);
 }
 
+template <bool BF16>
+__global__ void __launch_bounds__(256, 1) decode_tc_kernel(
+    const BlockBatch blocks, const float2 *__restrict__ omega, const float *__restrict__ inv_norm,
+    const float *__restrict__ nu, int D, OutGeom og, const float *__restrict__ col_off,
+    const float *__restrict__ row_off, int k_per_split, int N, float u_scale,
+    float *__restrict__ partial, int *__restrict__ status)
+{
+    decode_tc_body<BF16>(blocks.b[blockIdx.x], blockIdx.y, omega, inv_norm, nu, D, og, col_off,
+                         row_off, k_per_split, N, u_scale, partial, status);
+}
+
+// Many maps in one launch: CTA q decodes item q of a device list of
+// (map, block, slice); each map's pointers come from the table.
+template <bool BF16>
+__global__ void __launch_bounds__(256, 1) decode_tc_batch_kernel(
+    const __grid_constant__ BatchDecodeTable tab, const BatchDecodeItem *__restrict__ items)
+{
+    const BatchDecodeItem it = items[blockIdx.x];
+    const BatchDecodeMap &M = tab.m[it.map];
+    const int N = ((it.b.i1 - it.b.i0) + 15) / 16 * 16;
+    decode_tc_body<BF16>(it.b, it.split, M.omega, M.inv_norm, M.nu, M.D,
+                         OutGeom{0, 0, M.W, M.H}, M.col_off, M.row_off, M.k_per_split, N,
+                         M.u_scale, M.partial, M.status);
+}
+
 }  // namespace
+
+int launch_decode_tc_batch(const BatchDecodeTable &tab, const BatchDecodeItem *items,
+                           int n_items, bool bf16, cudaStream_t st)
+{
+    const size_t smem = 1024 + 2 * (size_t)(kAStage + 2 * 128 * kRowBytes);
+    cudaError_t e;
+    if (bf16) {
+        e = cudaFuncSetAttribute(decode_tc_batch_kernel<true>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e == cudaSuccess) decode_tc_batch_kernel<true><<<n_items, 256, smem, st>>>(tab, items);
+    } else {
+        e = cudaFuncSetAttribute(decode_tc_batch_kernel<false>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e == cudaSuccess) decode_tc_batch_kernel<false><<<n_items, 256, smem, st>>>(tab, items);
+    }
+    if (e == cudaSuccess) e = cudaGetLastError();
+    return e == cudaSuccess ? VSAOGM_OK : cuda_error(e, "batch decode");
+}
+
+float tc_u_scale(const vsaogm_map *m)
+{
+    float u = 1.f;
+    if (m->cfg.decode_prec == VSAOGM_DECODE_FP16X3)
+        while (u * u * 4.f <= (float)m->cfg.D) u *= 2.f;
+    return u;
+}
 
 int decode_tensor_cores(vsaogm_map *m, Region r, float *heat, cudaStream_t st)
 {

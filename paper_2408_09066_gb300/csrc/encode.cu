@@ -441,23 +441,21 @@ __device__ __forceinline__ void encode_points_x2(const float2 *sp, int len,
 // NPOLY < 0 selects the mixed form: warps below poly_warps use one polynomial
 // pair, the others none, so the polynomial share is poly_warps / (8 NP) of the
 // exponentials (warps of an SM share its MUFU and FMA pipes).
+// One (chunk, frequency slice) work item, executed by the whole CTA (256
+// threads; contains __syncthreads).  sp and s_bound are the CTA's shared
+// staging buffers; out receives the chunk's partial memory (or, with ATOMIC,
+// is the map's memories).
 template <int NP, int NPOLY, bool ATOMIC>
-__global__ void __launch_bounds__(256) encode_chunk_x2_kernel(const float2 *__restrict__ pts,
-                                                              const int4 *__restrict__ chunks,
-                                                              const int *__restrict__ n_chunks,
-                                                              const float *__restrict__ nu, int D,
-                                                              float nu_max_x, float nu_max_y,
-                                                              int poly_warps,
-                                                              float2 *__restrict__ out)
+__device__ __forceinline__ void encode_chunk_x2_body(const float2 *__restrict__ pts, int4 ch,
+                                                     int c, int slice,
+                                                     const float *__restrict__ nu, int D,
+                                                     float nu_max_x, float nu_max_y,
+                                                     int poly_warps, float2 *__restrict__ out,
+                                                     float2 *sp, unsigned *s_bound)
 {
     using namespace sm100;
-    __shared__ float2 sp[kMaxChunk];
-    __shared__ unsigned s_bound[2];
-    const int c = blockIdx.x;
-    if (c >= *n_chunks) return;
-    const int4 ch = chunks[c];
     const int len = ch.z - ch.y;
-    const int kbase = blockIdx.y * (512 * NP) + threadIdx.x;
+    const int kbase = slice * (512 * NP) + threadIdx.x;
     f32x2 nx[NP], ny[NP], ac[NP], as[NP];
 #pragma unroll
     for (int j = 0; j < NP; ++j) {
@@ -522,6 +520,82 @@ __global__ void __launch_bounds__(256) encode_chunk_x2_kernel(const float2 *__re
             }
         }
     }
+}
+
+template <int NP, int NPOLY, bool ATOMIC>
+__global__ void __launch_bounds__(256) encode_chunk_x2_kernel(const float2 *__restrict__ pts,
+                                                              const int4 *__restrict__ chunks,
+                                                              const int *__restrict__ n_chunks,
+                                                              const float *__restrict__ nu, int D,
+                                                              float nu_max_x, float nu_max_y,
+                                                              int poly_warps,
+                                                              float2 *__restrict__ out)
+{
+    __shared__ float2 sp[kMaxChunk];
+    __shared__ unsigned s_bound[2];
+    const int c = blockIdx.x;
+    if (c >= *n_chunks) return;
+    encode_chunk_x2_body<NP, NPOLY, ATOMIC>(pts, chunks[c], c, blockIdx.y, nu, D, nu_max_x,
+                                            nu_max_y, poly_warps, out, sp, s_bound);
+}
+
+// 5''. Many maps in one persistent launch.  Work items are (map, chunk,
+//      frequency slice), numbered map-major, chunk-major, slice-minor (the
+//      slices of a chunk reuse its points from L2); each CTA takes the next
+//      item from a global counter until none is left, so maps of any size and
+//      dimension share the GPU evenly.
+__global__ void __launch_bounds__(256) encode_batch_kernel(const __grid_constant__ BatchEncodeTable tab,
+                                                           unsigned long long *counter)
+{
+    __shared__ float2 sp[kMaxChunk];
+    __shared__ unsigned s_bound[2];
+    __shared__ long long s_item;
+    for (;;) {
+        if (threadIdx.x == 0) s_item = (long long)atomicAdd(counter, 1ull);
+        __syncthreads();
+        const long long it = s_item;
+        if (it >= tab.total) break;
+        int lo = 0, hi = tab.n_maps - 1;
+        while (lo < hi) {
+            int mid = (lo + hi + 1) >> 1;
+            if (tab.m[mid].item_begin <= it) lo = mid; else hi = mid - 1;
+        }
+        const BatchEncodeMap &M = tab.m[lo];
+        const long long local = it - M.item_begin;
+        const int c = (int)(local / M.slices), slice = (int)(local % M.slices);
+        if (c < *M.n_chunks)
+            encode_chunk_x2_body<4, -1, false>(M.pts, M.chunks[c], c, slice, M.nu, M.D,
+                                               M.nu_max_x, M.nu_max_y, tab.poly_warps, M.out, sp,
+                                               s_bound);
+        __syncthreads();  // the staging buffers are reused by the next item
+    }
+}
+
+// 6'. The fixed-order partial sums of many maps in one launch: blockIdx.x is a
+//     global segment (maps' segments numbered one after the other; up to
+//     64 x 2048 of them, beyond the 65535 limit of a grid's y extent).
+__global__ void __launch_bounds__(256) reduce_batch_kernel(const __grid_constant__ BatchReduceTable tab)
+{
+    const int gs = blockIdx.x;
+    int lo = 0, hi = tab.n_maps - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (tab.m[mid].seg_begin <= gs) lo = mid; else hi = mid - 1;
+    }
+    const BatchReduceMap &M = tab.m[lo];
+    const int s = gs - M.seg_begin;
+    const int k = blockIdx.y * blockDim.x + threadIdx.x;
+    if (k >= M.D) return;
+    const int c0 = M.cbeg[s], c1 = M.cbeg[s + 1];
+    if (c0 == c1) return;
+    float sr = 0.f, si = 0.f;
+    for (int c = c0; c < c1; ++c) {
+        float2 v = M.partial[(size_t)c * M.D + k];
+        sr += v.x;
+        si += v.y;
+    }
+    float2 w = M.omega[(size_t)s * M.D + k];
+    M.omega[(size_t)s * M.D + k] = make_float2(w.x + sr, w.y + si);
 }
 
 // 6. omega[s][k] += sum of the partial memories of segment s, in chunk order.
@@ -680,6 +754,104 @@ int reserve_encode(vsaogm_map *m, int64_t n64)
         (rc = ensure(m->ws.partial, sizeof(float2) * (size_t)max_chunks * D)))
         return rc;
     return VSAOGM_OK;
+}
+
+// Stage 1 of encode + bundle for one map: tile assignment and the stable
+// counting sort into segment order with chunks of at most `chunk` points, in
+// the map's scratch (grown if needed).  Returns the chunk-table bound.
+static int sort_stage(vsaogm_map *m, Scratch &ws, const float *xy_f, const uint8_t *lab, int n,
+                      int chunk, bool need_partial, cudaStream_t st, int *max_chunks_out)
+{
+    const int S = m->S, S1 = S + 1, D = m->cfg.D;
+    const int nb = (n + kSortBlock - 1) / kSortBlock;
+    const int max_chunks = (n + chunk - 1) / chunk + S;
+    *max_chunks_out = max_chunks;
+    int rc;
+    if ((rc = ensure(ws.blk_hist, sizeof(int) * (size_t)nb * S1))) return rc;
+    if ((rc = ensure(ws.seg_meta, sizeof(int) * (size_t)(3 * S1 + 2)))) return rc;
+    if ((rc = ensure(ws.chunks, sizeof(int4) * (size_t)max_chunks))) return rc;
+    if ((rc = ensure(ws.sorted, sizeof(float2) * (size_t)n))) return rc;
+    if (need_partial && (rc = ensure(ws.partial, sizeof(float2) * (size_t)max_chunks * D)))
+        return rc;
+    int *hist = (int *)ws.blk_hist.ptr, *meta = (int *)ws.seg_meta.ptr;
+    int4 *chunks = (int4 *)ws.chunks.ptr;
+    float2 *sorted = (float2 *)ws.sorted.ptr;
+    const float2 *xy = (const float2 *)xy_f;
+    AxisDev ax = axis_x(m), ay = axis_y(m);
+    cudaError_t e;
+    const size_t smem_count = sizeof(int) * S1;
+    const size_t smem_scatter = sizeof(int) * kSortWarps * S1;
+    // opt-in to more than 48 KB of dynamic shared memory (a per-device setting)
+    if ((e = cudaFuncSetAttribute(seg_scatter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)smem_scatter)) != cudaSuccess)
+        return cuda_error(e, "encode: shared memory");
+    StageScope sc(m, VSAOGM_STAGE_SORT, st);
+    seg_count_kernel<<<nb, 256, smem_count, st>>>(xy, lab, n, ax, ay, S, hist);
+    seg_scan_kernel<<<S1, kScanThreads, 0, st>>>(hist, nb, S1, meta);
+    seg_meta_kernel<<<1, kScanThreads, 0, st>>>(meta, S, chunk, chunks, m->rejected);
+    seg_scatter_kernel<<<nb, 256, smem_scatter, st>>>(xy, lab, n, ax, ay, S, hist, meta, sorted);
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_error(e, "encode: sort");
+    sc.end(4);
+    return VSAOGM_OK;
+}
+
+int batch_sort(vsaogm_map *m, Scratch &ws, const float *xy, const uint8_t *lab, int n, int chunk,
+               cudaStream_t st, int *max_chunks)
+{
+    return sort_stage(m, ws, xy, lab, n, chunk, true, st, max_chunks);
+}
+
+void batch_encode_entry(const vsaogm_map *m, const Scratch &ws, BatchEncodeMap *e)
+{
+    const int S1 = m->S + 1;
+    const int *meta = (const int *)ws.seg_meta.ptr;
+    e->pts = (const float2 *)ws.sorted.ptr;
+    e->chunks = (const int4 *)ws.chunks.ptr;
+    e->n_chunks = meta + 3 * S1 + 1;
+    e->nu = m->nu;
+    e->out = (float2 *)ws.partial.ptr;
+    e->D = m->cfg.D;
+    e->slices = (m->cfg.D + 2047) / 2048;  // the batched kernel holds 8 frequencies a thread
+    e->nu_max_x = m->nu_max[0];
+    e->nu_max_y = m->nu_max[1];
+}
+
+void batch_reduce_entry(const vsaogm_map *m, const Scratch &ws, BatchReduceMap *e)
+{
+    const int S1 = m->S + 1;
+    const int *meta = (const int *)ws.seg_meta.ptr;
+    e->partial = (const float2 *)ws.partial.ptr;
+    e->cbeg = meta + 2 * S1 + 1;
+    e->omega = m->omega;
+    e->D = m->cfg.D;
+}
+
+int encode_batch_ctas()
+{
+    int per_sm = 0, dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, encode_batch_kernel, 256, 0) !=
+        cudaSuccess)
+        per_sm = 1;
+    return std::max(1, per_sm) * std::max(1, sms);
+}
+
+int launch_encode_batch(const BatchEncodeTable &tab, unsigned long long *counter, int ctas,
+                        cudaStream_t st)
+{
+    cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(unsigned long long), st);
+    if (e != cudaSuccess) return cuda_error(e, "batch encode");
+    encode_batch_kernel<<<ctas, 256, 0, st>>>(tab, counter);
+    e = cudaGetLastError();
+    return e == cudaSuccess ? VSAOGM_OK : cuda_error(e, "batch encode");
+}
+
+int launch_reduce_batch(const BatchReduceTable &tab, int d_max, cudaStream_t st)
+{
+    reduce_batch_kernel<<<dim3(tab.total_segs, (d_max + 255) / 256), 256, 0, st>>>(tab);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? VSAOGM_OK : cuda_error(e, "batch reduce");
 }
 
 int encode_bundle(vsaogm_map *m, const float *xy_f, const uint8_t *lab, int64_t n64,

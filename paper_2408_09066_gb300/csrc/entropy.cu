@@ -29,19 +29,20 @@ struct DiskParams {
 // heat: the class maps of a W x H grid of cells (the whole map, or a decoded
 // region of it); the block covers window cells (wx0 + x, wy0 + y) of that
 // grid, and writes output (x, y) of the ww x wh window, row stride ww.
-__global__ void __launch_bounds__(256) entropy_kernel(const float *__restrict__ heat, int W, int H,
-                                                      int wx0, int wy0, int ww, int wh, int raw,
-                                                      const unsigned *__restrict__ maxima,
-                                                      DiskParams dp, unsigned mode, float rho,
-                                                      float *__restrict__ occ,
-                                                      float *__restrict__ ogm,
-                                                      uint8_t *__restrict__ cls)
+// The work of one CTA (the 32 x 32 output cells from window cell (bx0, by0)).
+// r: disk radius per class; hw: the disks' half-widths per class and dy, in
+// shared memory ([2][2 kMaxRadius + 1], -1 outside the disk).
+__device__ __forceinline__ void entropy_body(const float *__restrict__ heat, int W, int H, int wx0,
+                                             int wy0, int ww, int wh, int raw,
+                                             const unsigned *__restrict__ maxima, const int *r_c,
+                                             const int *hw, unsigned mode, float rho,
+                                             float *__restrict__ occ, float *__restrict__ ogm,
+                                             uint8_t *__restrict__ cls, int bx0, int by0)
 {
     __shared__ float sh[2][kSW][kSP];
     const unsigned act = mode & VSAOGM_ACT_MASK;
     const bool stencil = act == VSAOGM_ACT_ENTROPY;
-    const int R = stencil ? max(dp.r[0], dp.r[1]) : 0;
-    const int bx0 = blockIdx.x * kTB, by0 = blockIdx.y * kTB;  // window coordinates
+    const int R = stencil ? max(r_c[0], r_c[1]) : 0;
     const int x0 = wx0 + bx0, y0 = wy0 + by0;                  // grid coordinates
     const int edge = kTB + 2 * R;
     float inv[2] = {1.f, 1.f};
@@ -86,10 +87,10 @@ __global__ void __launch_bounds__(256) entropy_kernel(const float *__restrict__ 
                                                     : v;
                 continue;
             }
-            const int r = dp.r[c];
+            const int r = r_c[c];
             float s = 0.f;
             for (int dy = -r; dy <= r; ++dy) {
-                const int w = dp.hw[c][dy + kMaxRadius];
+                const int w = hw[c * (2 * kMaxRadius + 1) + dy + kMaxRadius];
                 const float *row = &sh[c][R + ly + dy][R + tx];
                 for (int dx = -w; dx <= w; ++dx) s += row[dx];
             }
@@ -106,7 +107,56 @@ __global__ void __launch_bounds__(256) entropy_kernel(const float *__restrict__ 
     }
 }
 
+constexpr int kHW = 2 * kMaxRadius + 1;
+
+// heat: the class maps of a W x H grid of cells (the whole map, or a decoded
+// region of it); the grid of CTAs covers window cells (wx0 + x, wy0 + y) of
+// that grid and writes output (x, y) of the ww x wh window, row stride ww.
+__global__ void __launch_bounds__(256) entropy_kernel(const float *__restrict__ heat, int W, int H,
+                                                      int wx0, int wy0, int ww, int wh, int raw,
+                                                      const unsigned *__restrict__ maxima,
+                                                      DiskParams dp, unsigned mode, float rho,
+                                                      float *__restrict__ occ,
+                                                      float *__restrict__ ogm,
+                                                      uint8_t *__restrict__ cls)
+{
+    __shared__ int hw[2 * kHW];
+    if (threadIdx.x < 2 * kHW) hw[threadIdx.x] = dp.hw[threadIdx.x / kHW][threadIdx.x % kHW];
+    __syncthreads();
+    entropy_body(heat, W, H, wx0, wy0, ww, wh, raw, maxima, dp.r, hw, mode, rho, occ, ogm, cls,
+                 blockIdx.x * kTB, blockIdx.y * kTB);
+}
+
+// Every map of a batch in one launch: blockIdx.z is the map; the grid covers
+// the largest map and CTAs beyond a map's extent return at once.
+__global__ void __launch_bounds__(256) entropy_batch_kernel(const __grid_constant__ BatchOutTable tab)
+{
+    const BatchMapOut &M = tab.m[blockIdx.z];
+    const int bx0 = blockIdx.x * kTB, by0 = blockIdx.y * kTB;
+    if (bx0 >= M.W || by0 >= M.H) return;
+    __shared__ int hw[2 * kHW];
+    if (threadIdx.x < 2 * kHW) {
+        // half-width of the disk of class c at row offset dy (Eq. entropy-mask)
+        const int c = threadIdx.x / kHW, dy = threadIdx.x % kHW - kMaxRadius, r = M.r[c];
+        int w = -1;
+        if (dy >= -r && dy <= r)
+            while ((w + 1) * (w + 1) + dy * dy <= r * r) ++w;
+        hw[threadIdx.x] = w;
+    }
+    __syncthreads();
+    entropy_body(M.heat, M.W, M.H, 0, 0, M.W, M.H, 1, M.maxima, M.r, hw, M.mode, M.rho, M.occ,
+                 M.ogm, nullptr, bx0, by0);
+}
+
 }  // namespace
+
+int launch_entropy_batch(const BatchOutTable &tab, int w_max, int h_max, cudaStream_t st)
+{
+    dim3 grid((w_max + kTB - 1) / kTB, (h_max + kTB - 1) / kTB, tab.n_maps);
+    entropy_batch_kernel<<<grid, 256, 0, st>>>(tab);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? VSAOGM_OK : cuda_error(e, "batch entropy");
+}
 
 int entropy(vsaogm_map *m, const float *heat, Region r, Region win, bool raw_input, float *occ,
             float *ogm, uint8_t *cls, cudaStream_t st)

@@ -60,6 +60,75 @@ struct OutGeom {
     int ox, oy, OW, OH;
 };
 
+// Tables of the batched (many-map) kernels, passed as __grid_constant__ params.
+constexpr int kMaxBatchMaps = 64;
+struct BatchEncodeMap {
+    const float2 *pts;      // sorted tile-centred points
+    const int4 *chunks;     // chunk table
+    const int *n_chunks;    // device count of chunks
+    const float *nu;        // [2][D]
+    float2 *out;            // partial memories [chunks][D]
+    long long item_begin;   // first work item of this map
+    int D, slices;
+    float nu_max_x, nu_max_y;
+};
+struct BatchEncodeTable {
+    int n_maps, poly_warps;
+    long long total;        // work items over all maps
+    BatchEncodeMap m[kMaxBatchMaps];
+};
+struct BatchReduceMap {
+    const float2 *partial;
+    const int *cbeg;        // chunk range of each segment [S + 1]
+    float2 *omega;
+    int D, seg_begin;       // first global segment of this map
+};
+struct BatchReduceTable {
+    int n_maps, total_segs;
+    BatchReduceMap m[kMaxBatchMaps];
+};
+
+struct BatchDecodeMap {
+    const float2 *omega;
+    const float *inv_norm, *nu, *col_off, *row_off;
+    float *partial;         // [slices][2][H][W]
+    int *status;
+    int D, k_per_split, W, H;
+    float u_scale;
+};
+struct BatchDecodeTable {
+    int n_maps;
+    BatchDecodeMap m[kMaxBatchMaps];
+};
+struct BatchDecodeItem {
+    int map, split;
+    DecodeBlock b;
+};
+struct BatchNormMap {
+    const float2 *omega;
+    float *inv_norm;
+    int D, mem_begin;       // first global memory of this map
+};
+struct BatchNormTable {
+    int n_maps;
+    BatchNormMap m[kMaxBatchMaps];
+};
+// Per-map slice sums / entropy of a batch.
+struct BatchMapOut {
+    const float *partial;   // decode slices
+    float *heat;            // [2][H][W] P
+    unsigned *maxima;
+    float *occ, *ogm;       // [H][W]
+    int splits, W, H;
+    float inv_scale, rho;
+    int r[2];               // disk radius of class 0 (empty) and 1 (occupied)
+    unsigned mode;
+};
+struct BatchOutTable {
+    int n_maps;
+    BatchMapOut m[kMaxBatchMaps];
+};
+
 // Grow-on-demand device buffer owned by a map.
 struct DevBuf {
     void *ptr = nullptr;
@@ -127,6 +196,7 @@ namespace vsaogm_impl {
 int set_error(int code, const char *fmt, ...);
 int cuda_error(cudaError_t e, const char *what);
 int ensure(DevBuf &b, size_t bytes);
+void free_scratch(Scratch &ws);
 
 // Brackets one stage: records a start event on `st` when timing is on and,
 // on end(), the stop event and `kernels` launches for the stage.
@@ -177,6 +247,23 @@ int entropy(vsaogm_map *m, const float *heat, Region r, Region win, bool raw_inp
 
 // misc kernels (decode.cu)
 int add_memories(float2 *dst, const float2 *src, int64_t count, cudaStream_t st);
+
+// batched (many-map) stages, used by batch.cu; `ws` is scratch the batch owns
+// (not the map's), so per-map calls never move memory a captured step uses
+int batch_sort(vsaogm_map *m, Scratch &ws, const float *xy, const uint8_t *lab, int n, int chunk,
+               cudaStream_t st, int *max_chunks);
+void batch_encode_entry(const vsaogm_map *m, const Scratch &ws, BatchEncodeMap *e);
+void batch_reduce_entry(const vsaogm_map *m, const Scratch &ws, BatchReduceMap *e);
+int encode_batch_ctas();
+int launch_encode_batch(const BatchEncodeTable &tab, unsigned long long *counter, int ctas,
+                        cudaStream_t st);
+int launch_reduce_batch(const BatchReduceTable &tab, int d_max, cudaStream_t st);
+int launch_norms_batch(const BatchNormTable &tab, int total_memories, cudaStream_t st);
+int launch_sums_batch(const BatchOutTable &tab, size_t max_cells, cudaStream_t st);
+int launch_decode_tc_batch(const BatchDecodeTable &tab, const BatchDecodeItem *items,
+                           int n_items, bool bf16, cudaStream_t st);
+int launch_entropy_batch(const BatchOutTable &tab, int w_max, int h_max, cudaStream_t st);
+float tc_u_scale(const vsaogm_map *m);
 
 inline Region full_region(const vsaogm_map *m)
 {

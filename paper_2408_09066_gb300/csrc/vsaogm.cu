@@ -99,6 +99,18 @@ StageScope::~StageScope()
     if (a_) m_->timer.free_events.push_back(a_);
 }
 
+void free_scratch(Scratch &ws)
+{
+    DevBuf *bufs[] = {&ws.blk_hist, &ws.seg_meta,  &ws.chunks,    &ws.sorted,
+                      &ws.partial,  &ws.stage_xy,  &ws.stage_lab, &ws.stage_heat,
+                      &ws.stage_occ, &ws.dec_partial};
+    for (DevBuf *b : bufs) {
+        if (b->ptr) cudaFree(b->ptr);
+        b->ptr = nullptr;
+        b->bytes = 0;
+    }
+}
+
 }  // namespace vsaogm_impl
 
 namespace {
@@ -123,12 +135,6 @@ float round_down_f32(double v)
     return f;
 }
 
-void free_buf(DevBuf &b)
-{
-    if (b.ptr) cudaFree(b.ptr);
-    b.ptr = nullptr;
-    b.bytes = 0;
-}
 
 void free_map(vsaogm_map *m)
 {
@@ -138,10 +144,7 @@ void free_map(vsaogm_map *m)
                     m->col_off, m->row_off, m->status};
     for (void *p : ptrs)
         if (p) cudaFree(p);
-    DevBuf *bufs[] = {&m->ws.blk_hist, &m->ws.seg_meta, &m->ws.chunks, &m->ws.sorted,
-                      &m->ws.partial, &m->ws.stage_xy, &m->ws.stage_lab, &m->ws.stage_heat,
-                      &m->ws.stage_occ, &m->ws.dec_partial};
-    for (DevBuf *b : bufs) free_buf(*b);
+    free_scratch(m->ws);
     for (cudaEvent_t e : m->timer.free_events) cudaEventDestroy(e);
     for (auto &p : m->timer.pending) {
         cudaEventDestroy(p.a);

@@ -251,6 +251,42 @@ def robot_fleet(n_robots: int, seed: int = 1005, min_cells: int = 256, max_cells
     return fleet
 
 
+def batch_maps(n_maps: int = 64, seed: int = 1004, min_cells: int = 64, max_cells: int = 1024,
+               min_points: int = 10_000, max_points: int = 500_000, max_tiles: int = 8,
+               dims=(2048, 4096, 8192)) -> list:
+    """Independent maps of uneven size for batched stepping: cells per side
+    log-uniform in [min_cells, max_cells] at 0.1 m, tiles per axis uniform in
+    1..max_tiles (independently, at least 8 cells a tile), D drawn from
+    ``dims``, and a log-uniform number of labelled points in [min_points,
+    max_points] from the small-scan generator (360 beams, 10 empty samples per
+    beam, sigma 0.02 m) along a 0.5 m-step random walk, max range
+    min(30 m, half the world)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for k in range(n_maps):
+        cells = int(round(np.exp(rng.uniform(np.log(min_cells), np.log(max_cells)))))
+        cells = max(min_cells, min(max_cells, cells))
+        tx = int(rng.integers(1, max_tiles + 1))
+        ty = int(rng.integers(1, max_tiles + 1))
+        tx, ty = max(1, min(tx, cells // 8)), max(1, min(ty, cells // 8))
+        D = int(dims[int(rng.integers(len(dims)))])
+        n = int(round(np.exp(rng.uniform(np.log(min_points), np.log(max_points)))))
+        half = cells * 0.1 / 2
+        sc = min(1.0, half / 3.2)   # obstacles and steps shrink with worlds below 6.4 m
+        w = make_world(rng, half, max(5, cells // 40), max(3, cells // 80),
+                       (0.3 * sc, 3.0 * sc), (0.2 * sc, 1.2 * sc), free_r=0.6 * sc)
+        per_scan = 360 * 11
+        poses = trajectory(w, (0.0, 0.0), (n + per_scan - 1) // per_scan, 0.5 * sc, rng,
+                           margin=0.3 * sc)
+        parts = [scan(w, p, 360, min(30.0, half), 0.02, 10, rng) for p in poses]
+        xy = np.concatenate([q[0] for q in parts])[:n]
+        lab = np.concatenate([q[1] for q in parts])[:n]
+        out.append(Workload(f"batch{k}_{cells}x{cells}_{tx}x{ty}_D{D}", np.ascontiguousarray(xy),
+                            np.ascontiguousarray(lab), cells, cells, 0.1, -half, -half, tx, ty, D,
+                            0.1, seed * 1000 + k, w))
+    return out
+
+
 def window_sizes(rng: np.random.Generator, cells: int, lo: int = 128, hi: int = 512):
     """A random query window (x0, y0, w, h) of lo..hi cells per side inside the map."""
     w = int(min(cells, rng.integers(lo, hi + 1)))

@@ -21,6 +21,7 @@ DECODE_FP32, DECODE_BF16X3, DECODE_FP16X3 = 0, 1, 2
 FLAG_CHECKED, FLAG_ATOMIC = 1, 2
 MODE_NO_NORM, MODE_NO_SQUARE = 1, 2
 ACT_ENTROPY, ACT_RELU, ACT_TANH, ACT_SIGMOID, ACT_NONE = 0, 16, 32, 48, 64
+MAX_BATCH = 64
 
 
 class VsaogmError(RuntimeError):
@@ -69,6 +70,14 @@ _SIGNATURES = {
     "vsaogm_set_timing": (ctypes.c_int, [_V, ctypes.c_int]),
     "vsaogm_stage_times": (ctypes.c_int, [_V, _V, _V, ctypes.c_int]),
     "vsaogm_last_error": (ctypes.c_char_p, []),
+    "vsaogm_batch_create": (ctypes.c_int, [_V, ctypes.c_int32, _V]),
+    "vsaogm_batch_destroy": (ctypes.c_int, [_V]),
+    "vsaogm_batch_step": (ctypes.c_int, [_V, _V, _V, _V, _V, _V, _V, ctypes.c_int32, _V]),
+    "vsaogm_batch_capture": (ctypes.c_int, [_V, _V, _V, _V, _V, _V, _V, ctypes.c_int32, _V]),
+    "vsaogm_batch_replay": (ctypes.c_int, [_V, _V]),
+    "vsaogm_batch_autotune": (ctypes.c_int, [_V, _V, _V, _V, _V, _V, _V, _V, _V, _V]),
+    "vsaogm_batch_set_timing": (ctypes.c_int, [_V, ctypes.c_int32]),
+    "vsaogm_batch_stage_times": (ctypes.c_int, [_V, _V, _V, ctypes.c_int32]),
 }
 
 
@@ -279,3 +288,101 @@ class Map:
         ny = np.empty(self.D, np.float32)
         _check(lib().vsaogm_get_axis_frequencies(self._h, _V(nx.ctypes.data), _V(ny.ctypes.data)))
         return nx, ny
+
+
+def _ptrs(values):
+    arr = (_V * len(values))()
+    for i, v in enumerate(values):
+        arr[i] = v
+    return arr
+
+
+class Batch:
+    """Up to MAX_BATCH maps stepped together: one launch per stage for all.
+
+    The batch refers to its maps (keep them alive).  Per-map inputs and
+    outputs are lists in the order of `maps`: xy (n_i, 2) float32, labels
+    (n_i,) uint8, heat (2, H_i, W_i), occ and ogm (H_i, W_i) float32, all
+    CUDA tensors.
+    """
+
+    def __init__(self, maps):
+        self.maps = list(maps)
+        h = _V()
+        handles = _ptrs([m.handle for m in self.maps])
+        _check(lib().vsaogm_batch_create(handles, len(self.maps), ctypes.byref(h)))
+        self._h = h
+        self._keep = None
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _check(lib().vsaogm_batch_destroy(self._h))
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def _args(self, xy, labels, heat, occ, ogm):
+        import torch
+        k = len(self.maps)
+        if not (len(xy) == len(labels) == len(heat) == len(occ) == k) or (
+                ogm is not None and len(ogm) != k):
+            raise ValueError(f"every per-map list needs {k} entries")
+        n = (ctypes.c_int64 * k)()
+        xs, ls, hs, os_, gs = [], [], [], [], []
+        for i, m in enumerate(self.maps):
+            n[i] = labels[i].shape[0]
+            xs.append(_dev(xy[i], torch.float32, (n[i], 2), "xy"))
+            ls.append(_dev(labels[i], torch.uint8, (n[i],), "labels"))
+            hs.append(_dev(heat[i], torch.float32, (2, m.H, m.W), "heat"))
+            os_.append(_dev(occ[i], torch.float32, (m.H, m.W), "occ"))
+            if ogm is not None:
+                gs.append(_dev(ogm[i], torch.float32, (m.H, m.W), "ogm"))
+        return (_ptrs(xs), _ptrs(ls), n, _ptrs(hs), _ptrs(os_),
+                _ptrs(gs) if ogm is not None else None)
+
+    def step(self, xy, labels, heat, occ, ogm=None, reset=True, stream=None):
+        a = self._args(xy, labels, heat, occ, ogm)
+        _check(lib().vsaogm_batch_step(self._h, *a, 1 if reset else 0, _stream(stream)))
+
+    def capture(self, xy, labels, heat, occ, ogm=None, reset=True, stream=None):
+        """Runs one step and captures it in a CUDA graph; replay() re-runs it
+        on the same buffers (refill the inputs in place, same point counts)."""
+        a = self._args(xy, labels, heat, occ, ogm)
+        self._keep = (xy, labels, heat, occ, ogm)  # the graph holds their addresses
+        _check(lib().vsaogm_batch_capture(self._h, *a, 1 if reset else 0, _stream(stream)))
+
+    def replay(self, stream=None):
+        _check(lib().vsaogm_batch_replay(self._h, _stream(stream)))
+
+    def autotune(self, xy, labels, heat, occ, stream=None):
+        """Times candidate shapes on these inputs, keeps the fastest and
+        returns it as a dict (overwrites the maps' memories)."""
+        a = self._args(xy, labels, heat, occ, None)
+        pw, ipc, dw = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        _check(lib().vsaogm_batch_autotune(self._h, *a[:5], _stream(stream), ctypes.byref(pw),
+                                           ctypes.byref(ipc), ctypes.byref(dw)))
+        return {"poly_warps": pw.value, "items_per_cta": ipc.value, "decode_waves": dw.value}
+
+    def set_timing(self, enable: bool = True):
+        _check(lib().vsaogm_batch_set_timing(self._h, 1 if enable else 0))
+
+    def stage_times(self, reset: bool = False):
+        """{stage: (milliseconds, kernel launches)} accumulated since the last reset."""
+        ms = (ctypes.c_double * len(STAGES))()
+        cnt = (ctypes.c_int64 * len(STAGES))()
+        _check(lib().vsaogm_batch_stage_times(self._h, ms, cnt, 1 if reset else 0))
+        return {s: (ms[i], cnt[i]) for i, s in enumerate(STAGES)}
+
+    def status(self, stream=None):
+        for m in self.maps:
+            m.status(stream)

@@ -92,3 +92,15 @@ def test_binding_refuses_missing_library(monkeypatch, tmp_path):
     monkeypatch.setattr(V, "_lib", None)
     with pytest.raises(RuntimeError, match="missing"):
         V.lib()
+
+
+def test_batch_create_rejects_bad_arguments_before_touching_the_gpu(L):
+    h = ctypes.c_void_p()
+    maps = (ctypes.c_void_p * (V.MAX_BATCH + 1))()
+    for count in (0, V.MAX_BATCH + 1):
+        assert L.vsaogm_batch_create(maps, count, ctypes.byref(h)) == V.E_INVAL
+        assert "batch holds" in L.vsaogm_last_error().decode()
+    assert L.vsaogm_batch_create(maps, 1, ctypes.byref(h)) == V.E_INVAL  # NULL map
+    assert not h.value
+    assert L.vsaogm_batch_destroy(None) == V.OK
+    assert L.vsaogm_batch_replay(None, None) == V.E_INVAL
