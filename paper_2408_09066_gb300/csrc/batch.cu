@@ -74,7 +74,7 @@ int build_decode_items(vsaogm_batch *b)
     std::vector<std::vector<DecodeBlock>> blocks(b->maps.size());
     size_t n_blocks = 0;
     for (size_t i = 0; i < b->maps.size(); ++i) {
-        region_blocks(b->maps[i], full_region(b->maps[i]), 128, 128, blocks[i]);
+        tc_blocks(b->maps[i], full_region(b->maps[i]), blocks[i]);
         n_blocks += blocks[i].size();
     }
     const int target = 152 * b->tune.decode_waves;
@@ -84,7 +84,8 @@ int build_decode_items(vsaogm_batch *b)
     for (size_t i = 0; i < b->maps.size(); ++i) {
         vsaogm_map *m = b->maps[i];
         const int D = m->cfg.D;
-        int s = std::max(1, std::min(s_all, (D + 31) / 32));
+        int s = std::max((D + kTcMaxKPerSplit - 1) / kTcMaxKPerSplit,
+                         std::min(s_all, (D + 31) / 32));
         const int kps = ((D + s - 1) / s + 31) / 32 * 32;
         s = (D + kps - 1) / kps;
         b->splits[i] = s;
@@ -237,15 +238,15 @@ int enqueue_step(vsaogm_batch *b, const float *const *xy, const uint8_t *const *
     BatchOutTable ot;
     memset(&ot, 0, sizeof(ot));
     size_t max_cells = 0;
-    int w_max = 0, h_max = 0;
+    int ent_blocks = 0;
     for (int i = 0; i < M; ++i) {
         vsaogm_map *m = b->maps[i];
         const int D = m->cfg.D, s = b->splits[i];
         const int kps = ((D + s - 1) / s + 31) / 32 * 32;
         const float u = tc_u_scale(m);
         dt.m[i] = BatchDecodeMap{m->omega, m->inv_norm, m->nu, m->col_off, m->row_off,
-                                 (float *)b->ws[i].dec_partial.ptr, m->status, D, kps,
-                                 m->cfg.grid_w, m->cfg.grid_h, u};
+                                 m->row_tile, (float *)b->ws[i].dec_partial.ptr, m->status, D,
+                                 kps, m->cfg.grid_w, m->cfg.grid_h, m->cfg.tiles_x, u};
         BatchMapOut &o = ot.m[i];
         o.partial = (const float *)b->ws[i].dec_partial.ptr;
         o.heat = heat[i];
@@ -260,16 +261,16 @@ int enqueue_step(vsaogm_batch *b, const float *const *xy, const uint8_t *const *
         o.r[0] = m->cfg.r_emp;
         o.r[1] = m->cfg.r_occ;
         o.mode = m->cfg.decode_mode;
+        o.blk_begin = ent_blocks;
+        ent_blocks += ((o.W + 31) / 32) * ((o.H + 31) / 32);
         max_cells = std::max(max_cells, (size_t)o.W * o.H);
-        w_max = std::max(w_max, o.W);
-        h_max = std::max(h_max, o.H);
     }
     dt.n_maps = ot.n_maps = M;
     if ((rc = launch_decode_tc_batch(dt, b->items, b->n_items, b->bf16, st))) return rc;
     if ((rc = launch_sums_batch(ot, max_cells, st))) return rc;
     counted[VSAOGM_STAGE_DECODE] = 3;
     mark();
-    if ((rc = launch_entropy_batch(ot, w_max, h_max, st))) return rc;
+    if ((rc = launch_entropy_batch(ot, st))) return rc;
     counted[VSAOGM_STAGE_ENTROPY] = 1;
     mark();
     return VSAOGM_OK;

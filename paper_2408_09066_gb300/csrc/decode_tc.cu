@@ -16,11 +16,17 @@
 // hi*hi + hi*lo + lo*hi with FP32 accumulation in tensor memory: about 16
 // significant bits per product.
 //
-// Pipeline per CTA (256 threads, one CTA per SM): all threads generate stage s
+// Blocks: up to 128 columns inside one tile column by up to 128 rows that may
+// cross tile rows (each row multiplies the memories of its own tile), so the
+// 128-row MMA tile is filled even when tiles are short.
+//
+// Pipeline per CTA (512 threads, one CTA per SM): all threads generate stage s
 // (32 frequencies) into one of two shared-memory buffers while the tensor
-// cores run stage s - 1 from the other; one thread issues the 24 MMAs of a
-// stage (2 classes x 3 products x 4 K-steps of 16) and commits them to the
-// buffer's mbarrier.  The epilogue reads the two 128 x N FP32 accumulators
+// cores run stage s - 1 from the other; the memories and frequencies of stage
+// s + 1 are loaded into registers meanwhile.  One thread issues the 24 MMAs
+// of a stage (2 classes x 3 products x 4 K-steps of 16) and commits them to
+// the buffer's mbarrier.  The 128-byte swizzle puts 4-byte element kk of row
+// m at byte m * 128 + ((kk / 4) xor (m mod 8)) * 16 + (kk mod 4) * 4.  The epilogue reads the two 128 x N FP32 accumulators
 // from tensor memory and writes per-slice partial maps; a second kernel sums
 // the slices in a fixed order and folds the per-class maxima (Eq.
 // non-linearities needs the map maximum).  Every wait is bounded: on time-out
@@ -42,16 +48,20 @@ using namespace sm100;
 constexpr int kM = 128;            // rows per block (MMA M)
 constexpr int kKS = 32;            // frequencies per stage (64 k' = 128 bytes per row)
 constexpr int kRowBytes = 128;
+constexpr int kThreads = 512;      // 16 warps generate the operands
+constexpr int kWarps = kThreads / 32;
+constexpr int kQ = kM / kWarps;    // rows (and columns) per thread
 constexpr int kATile = kM * kRowBytes;          // one A operand tile (16 KB)
 constexpr int kAStage = 4 * kATile;             // 2 classes x hi/lo (64 KB)
+constexpr int kWBytes = kMaxBlockTiles * 2 * kKS * 8;  // staged memories (8 KB)
+constexpr int kWPerThread = (kMaxBlockTiles * 2 * kKS + kThreads - 1) / kThreads;
 constexpr int kTmemCols = 256;                  // class psi accumulates at column 128 psi
 constexpr uint64_t kWaitNs = 2000000000ull;     // 2 s: far above any legitimate wait
 
-__device__ __forceinline__ uint32_t swz(int row, int kk)
-{
-    // byte offset of the 4-byte element kk (0..31) of a 128-byte row, 128B swizzle
-    return (uint32_t)(row * kRowBytes + ((((kk >> 2) ^ (row & 7)) << 4) | ((kk & 3) << 2)));
-}
+// Bytes of one pipeline stage for MMA width N: A (both classes, hi and lo),
+// B (hi and lo) and the staged memories.
+__host__ __device__ constexpr int stage_size(int N) { return kAStage + 2 * N * kRowBytes + kWBytes; }
+constexpr size_t kSmemMax = 1024 + 2 * (size_t)stage_size(kM);
 
 __device__ __forceinline__ float2 phasor(float nu, float d)
 {
@@ -83,26 +93,38 @@ __device__ __forceinline__ void split2(float x, float y, uint32_t &hi, uint32_t 
     }
 }
 
-// One (block of cells, frequency slice) item, executed by the whole CTA.
+// One (block of cells, frequency slice) item, executed by the whole CTA
+// (kThreads threads).  The block's columns lie in tile column b.tile; its rows
+// may cross tile rows (at most kMaxBlockTiles of them), each row using the
+// memories of its own tile: row j of the A operand is U_psi of tile
+// (row_tile[j], b.tile), so no MMA row is spent on padding at tile seams.
 template <bool BF16>
 __device__ __forceinline__ void decode_tc_body(
     const DecodeBlock b, const int split, const float2 *__restrict__ omega,
-    const float *__restrict__ inv_norm, const float *__restrict__ nu, int D, OutGeom og,
-    const float *__restrict__ col_off, const float *__restrict__ row_off, int k_per_split, int N,
-    float u_scale, float *__restrict__ partial, int *__restrict__ status)
+    const float *__restrict__ inv_norm, const float *__restrict__ nu, int D, int tiles_x,
+    const int *__restrict__ row_tile, OutGeom og, const float *__restrict__ col_off,
+    const float *__restrict__ row_off, int k_per_split, int N, float u_scale,
+    float *__restrict__ partial, int *__restrict__ status)
 {
     extern __shared__ uint8_t smem_raw[];
     __shared__ uint64_t empty_bar[2], done_bar;
     __shared__ uint32_t tmem_base_s;
     __shared__ int abort_s;
     uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    const int stage_bytes = kAStage + 2 * N * kRowBytes;
+    const int stage_bytes = stage_size(N);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int k_begin = split * k_per_split;
     const int k_end = min(D, k_begin + k_per_split);
     const int n_stages = (k_end - k_begin + kKS - 1) / kKS;
     const int ni = b.i1 - b.i0, nj = b.j1 - b.j0;
+    const int by0 = row_tile[b.j0];
+    const int nt = row_tile[b.j1 - 1] - by0 + 1;  // tile rows of the block
+    if (nt < 1 || nt > kMaxBlockTiles || N > kM || N < 16 || (N & 15)) {
+        // the host never builds such a block; refuse it rather than index past smem
+        if (tid == 0) atomicExch(status, VSAOGM_E_INVAL);
+        return;
+    }
 
     if (warp == 0) {
         tmem_alloc(&tmem_base_s, kTmemCols);
@@ -120,17 +142,49 @@ __device__ __forceinline__ void decode_tc_body(
     tc_fence_after_sync();
     const uint32_t tmem = tmem_base_s;
 
-    // Fixed per-thread geometry: frequency kk = lane, rows / columns warp + 8q.
-    float dy[kM / 8], dx[kM / 8];
+    // Fixed per-thread geometry: frequency kk = lane; rows / columns
+    // warp + kWarps q, whose 128-byte swizzle phase (row & 7) is warp & 7.
+    float dy[kQ], dx[kQ];
+    int tl[kQ];  // tile row of each A row, relative to by0
 #pragma unroll
-    for (int q = 0; q < kM / 8; ++q) {
-        int m = warp + 8 * q;
+    for (int q = 0; q < kQ; ++q) {
+        const int m = warp + kWarps * q;
         dy[q] = m < nj ? row_off[b.j0 + m] : 0.f;
+        tl[q] = m < nj ? min(max(row_tile[b.j0 + m] - by0, 0), nt - 1) : 0;
         dx[q] = m < ni ? col_off[b.i0 + m] : 0.f;
     }
-    const float w0s = inv_norm[2 * b.tile] * u_scale, w1s = inv_norm[2 * b.tile + 1] * u_scale;
-    const float2 *om0 = omega + (size_t)(2 * b.tile) * D;
-    const float2 *om1 = om0 + D;
+    const uint32_t soff =
+        (uint32_t)(warp * kRowBytes + ((((lane >> 2) ^ (warp & 7)) << 4) | ((lane & 3) << 2)));
+    // The memories of the stage's 32 frequencies for the block's tiles are
+    // staged (scaled by 1 / norm) in shared memory: entry e = (tile row,
+    // class, kk), two entries per thread.
+    constexpr int kWEnt = kMaxBlockTiles * 2 * kKS;
+    int w_mem[kWPerThread];
+    float w_scale[kWPerThread];
+#pragma unroll
+    for (int r = 0; r < kWPerThread; ++r) {
+        const int e = tid + kThreads * r;
+        const bool ev = e < nt * 2 * kKS;
+        const int mem = 2 * ((by0 + (e >> 6)) * tiles_x + b.tile) + ((e >> 5) & 1);
+        w_mem[r] = ev ? mem : -1;
+        w_scale[r] = ev ? inv_norm[mem] * u_scale : 0.f;
+    }
+    // prefetch registers: this thread's frequency and staged memory entries
+    float pnx = 0.f, pny = 0.f;
+    float2 pw[kWPerThread];
+    auto prefetch = [&](int s) {
+        const int k = k_begin + s * kKS + lane;
+        pnx = k < k_end ? nu[k] : 0.f;
+        pny = k < k_end ? nu[D + k] : 0.f;
+#pragma unroll
+        for (int r = 0; r < kWPerThread; ++r) {
+            const int kk = k_begin + s * kKS + ((tid + kThreads * r) & 31);
+            pw[r] = (w_mem[r] >= 0 && kk < k_end) ? omega[(size_t)w_mem[r] * D + kk]
+                                                   : make_float2(0.f, 0.f);
+        }
+    };
+    (void)kWEnt;
+    if (n_stages > 0) prefetch(0);
     const uint32_t idesc = idesc_f16(kM, N, BF16);
     uint32_t phase_bits = 0u;  // bit b: parity to wait for on buffer b
 
@@ -141,42 +195,45 @@ __device__ __forceinline__ void decode_tc_body(
                 atomicExch(&abort_s, 1);
             phase_bits ^= 1u << buf;
         }
+        uint8_t *st = smem + (size_t)buf * stage_bytes;
+        uint8_t *bh = st + kAStage, *bl = bh + N * kRowBytes;
+        float2 *sw = reinterpret_cast<float2 *>(bl + N * kRowBytes);
+#pragma unroll
+        for (int r = 0; r < kWPerThread; ++r)
+            if (w_mem[r] >= 0)
+                sw[tid + kThreads * r] = make_float2(pw[r].x * w_scale[r], pw[r].y * w_scale[r]);
+        const float nux = pnx, nuy = pny;
+        const bool kv = k_begin + s * kKS + lane < k_end;
         __syncthreads();
         if (abort_s) break;
-        uint8_t *st = smem + (size_t)buf * stage_bytes;
-        const int k = k_begin + s * kKS + lane;
-        const bool kv = k < k_end;
-        const float nux = kv ? nu[k] : 0.f, nuy = kv ? nu[D + k] : 0.f;
-        float2 w0 = kv ? om0[k] : make_float2(0.f, 0.f);
-        float2 w1 = kv ? om1[k] : make_float2(0.f, 0.f);
-        w0.x *= w0s; w0.y *= w0s;
-        w1.x *= w1s; w1.y *= w1s;
+        if (s + 1 < n_stages) prefetch(s + 1);  // in flight while this stage is generated
         // B operand: x phasors of the N columns
-        uint8_t *bh = st + kAStage, *bl = bh + N * kRowBytes;
 #pragma unroll
-        for (int q = 0; q < kM / 8; ++q) {
-            int n = warp + 8 * q;
+        for (int q = 0; q < kQ; ++q) {
+            const int n = warp + kWarps * q;
             if (n >= N) continue;
             float2 a = (kv && n < ni) ? phasor(nux, dx[q]) : make_float2(0.f, 0.f);
             uint32_t hi, lo;
             split2<BF16>(a.x, a.y, hi, lo);
-            *reinterpret_cast<uint32_t *>(bh + swz(n, lane)) = hi;
-            *reinterpret_cast<uint32_t *>(bl + swz(n, lane)) = lo;
+            *reinterpret_cast<uint32_t *>(bh + q * kWarps * kRowBytes + soff) = hi;
+            *reinterpret_cast<uint32_t *>(bl + q * kWarps * kRowBytes + soff) = lo;
         }
         // A operands: U_psi = conj(w_hat_psi) * y phasor, stored as (Re, -Im)
 #pragma unroll
-        for (int q = 0; q < kM / 8; ++q) {
-            int m = warp + 8 * q;
+        for (int q = 0; q < kQ; ++q) {
+            const int m = warp + kWarps * q;
             float2 e = (kv && m < nj) ? phasor(nuy, dy[q]) : make_float2(0.f, 0.f);
+            const float2 w0 = sw[(2 * tl[q]) * kKS + lane], w1 = sw[(2 * tl[q] + 1) * kKS + lane];
             float u0r = w0.x * e.x + w0.y * e.y, u0i = w0.x * e.y - w0.y * e.x;
             float u1r = w1.x * e.x + w1.y * e.y, u1i = w1.x * e.y - w1.y * e.x;
+            const uint32_t o = q * kWarps * kRowBytes + soff;
             uint32_t hi, lo;
             split2<BF16>(u0r, -u0i, hi, lo);
-            *reinterpret_cast<uint32_t *>(st + 0 * kATile + swz(m, lane)) = hi;
-            *reinterpret_cast<uint32_t *>(st + 1 * kATile + swz(m, lane)) = lo;
+            *reinterpret_cast<uint32_t *>(st + 0 * kATile + o) = hi;
+            *reinterpret_cast<uint32_t *>(st + 1 * kATile + o) = lo;
             split2<BF16>(u1r, -u1i, hi, lo);
-            *reinterpret_cast<uint32_t *>(st + 2 * kATile + swz(m, lane)) = hi;
-            *reinterpret_cast<uint32_t *>(st + 3 * kATile + swz(m, lane)) = lo;
+            *reinterpret_cast<uint32_t *>(st + 2 * kATile + o) = hi;
+            *reinterpret_cast<uint32_t *>(st + 3 * kATile + o) = lo;
         }
         fence_async_shared();
         __syncthreads();
@@ -206,11 +263,14 @@ __device__ __forceinline__ void decode_tc_body(
     if (!ok) atomicExch(&abort_s, 1);
     tc_fence_after_sync();
     __syncthreads();
+    // epilogue: warp w reads TMEM lanes 32 (w & 3) .. + 31 (its lane quarter),
+    // class (w >> 2) & 1, and one half of the 16-column chunks (w >> 3)
+    const int c = (warp >> 2) & 1, lane_base = 32 * (warp & 3), half = warp >> 3;
+    const int m = lane_base + lane;
+    const int nch = N / 16, ch0 = half ? (nch + 1) / 2 : 0, ch1 = half ? nch : (nch + 1) / 2;
+    float *out = partial + (((size_t)split * 2 + c) * og.OH) * og.OW;
     if (!abort_s && n_stages > 0) {
-        const int c = warp >> 2, lane_base = 32 * (warp & 3);
-        const int m = lane_base + lane;
-        float *out = partial + (((size_t)split * 2 + c) * og.OH) * og.OW;
-        for (int cc = 0; cc < N / 16; ++cc) {
+        for (int cc = ch0; cc < ch1; ++cc) {
             float v[16];
             tmem_ld_32x32b_x16(tmem + ((uint32_t)lane_base << 16) + 128u * c + cc * 16, v);
             if (m < nj) {
@@ -222,10 +282,8 @@ __device__ __forceinline__ void decode_tc_body(
         }
     } else if (!abort_s && n_stages == 0) {
         // no frequencies in this slice: its contribution is zero
-        const int c = warp >> 2, m = 32 * (warp & 3) + lane;
-        float *out = partial + (((size_t)split * 2 + c) * og.OH) * og.OW;
         if (m < nj)
-            for (int x = 0; x < ni; ++x)
+            for (int x = ch0 * 16; x < min(ni, ch1 * 16); ++x)
                 out[(size_t)(b.j0 + m - og.oy) * og.OW + (b.i0 - og.ox) + x] = 0.f;
     }
     if (abort_s && tid == 0) atomicExch(status, VSAOGM_E_TIMEOUT);
@@ -235,45 +293,74 @@ __device__ __forceinline__ void decode_tc_body(
 }
 
 template <bool BF16>
-__global__ void __launch_bounds__(256, 1) decode_tc_kernel(
+__global__ void __launch_bounds__(kThreads, 1) decode_tc_kernel(
     const BlockBatch blocks, const float2 *__restrict__ omega, const float *__restrict__ inv_norm,
-    const float *__restrict__ nu, int D, OutGeom og, const float *__restrict__ col_off,
-    const float *__restrict__ row_off, int k_per_split, int N, float u_scale,
-    float *__restrict__ partial, int *__restrict__ status)
+    const float *__restrict__ nu, int D, int tiles_x, const int *__restrict__ row_tile, OutGeom og,
+    const float *__restrict__ col_off, const float *__restrict__ row_off, int k_per_split, int N,
+    float u_scale, float *__restrict__ partial, int *__restrict__ status)
 {
-    decode_tc_body<BF16>(blocks.b[blockIdx.x], blockIdx.y, omega, inv_norm, nu, D, og, col_off,
-                         row_off, k_per_split, N, u_scale, partial, status);
+    decode_tc_body<BF16>(blocks.b[blockIdx.x], blockIdx.y, omega, inv_norm, nu, D, tiles_x,
+                         row_tile, og, col_off, row_off, k_per_split, N, u_scale, partial, status);
 }
 
 // Many maps in one launch: CTA q decodes item q of a device list of
 // (map, block, slice); each map's pointers come from the table.
 template <bool BF16>
-__global__ void __launch_bounds__(256, 1) decode_tc_batch_kernel(
+__global__ void __launch_bounds__(kThreads, 1) decode_tc_batch_kernel(
     const __grid_constant__ BatchDecodeTable tab, const BatchDecodeItem *__restrict__ items)
 {
     const BatchDecodeItem it = items[blockIdx.x];
     const BatchDecodeMap &M = tab.m[it.map];
     const int N = ((it.b.i1 - it.b.i0) + 15) / 16 * 16;
-    decode_tc_body<BF16>(it.b, it.split, M.omega, M.inv_norm, M.nu, M.D,
+    decode_tc_body<BF16>(it.b, it.split, M.omega, M.inv_norm, M.nu, M.D, M.tiles_x, M.row_tile,
                          OutGeom{0, 0, M.W, M.H}, M.col_off, M.row_off, M.k_per_split, N,
                          M.u_scale, M.partial, M.status);
 }
 
 }  // namespace
 
+// Blocks of at most 128 x 128 cells covering region r for the tensor-core
+// decode: columns inside one tile column, rows across at most kMaxBlockTiles
+// tile rows.
+void tc_blocks(const vsaogm_map *m, Region r, std::vector<DecodeBlock> &out)
+{
+    out.clear();
+    const std::vector<int> &yl = m->tile_last[1];  // tiles are monotonic in the row index
+    const int ty = m->cfg.tiles_y;
+    for (int bx = 0; bx < m->cfg.tiles_x; ++bx) {
+        const int x0 = std::max(r.x0, m->tile_first[0][bx]);
+        const int x1 = std::min(r.x1, m->tile_last[0][bx]);
+        if (x0 >= x1) continue;
+        for (int i0 = x0; i0 < x1; i0 += kM) {
+            const int i1 = std::min(i0 + kM, x1);
+            int by = 0;
+            for (int j0 = r.y0; j0 < r.y1;) {
+                while (by < ty - 1 && yl[by] <= j0) ++by;  // tile row of row j0
+                // rows up to the end of the kMaxBlockTiles-th tile row from by
+                int cap = j0 + 1;
+                for (int t = by; t < std::min(by + kMaxBlockTiles, ty); ++t) cap = std::max(cap, yl[t]);
+                const int j1 = std::min({j0 + kM, r.y1, cap});
+                out.push_back(DecodeBlock{bx, i0, j0, i1, j1});
+                j0 = j1;
+            }
+        }
+    }
+}
+
 int launch_decode_tc_batch(const BatchDecodeTable &tab, const BatchDecodeItem *items,
                            int n_items, bool bf16, cudaStream_t st)
 {
-    const size_t smem = 1024 + 2 * (size_t)(kAStage + 2 * 128 * kRowBytes);
     cudaError_t e;
     if (bf16) {
         e = cudaFuncSetAttribute(decode_tc_batch_kernel<true>,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e == cudaSuccess) decode_tc_batch_kernel<true><<<n_items, 256, smem, st>>>(tab, items);
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemMax);
+        if (e == cudaSuccess)
+            decode_tc_batch_kernel<true><<<n_items, kThreads, kSmemMax, st>>>(tab, items);
     } else {
         e = cudaFuncSetAttribute(decode_tc_batch_kernel<false>,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e == cudaSuccess) decode_tc_batch_kernel<false><<<n_items, 256, smem, st>>>(tab, items);
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemMax);
+        if (e == cudaSuccess)
+            decode_tc_batch_kernel<false><<<n_items, kThreads, kSmemMax, st>>>(tab, items);
     }
     if (e == cudaSuccess) e = cudaGetLastError();
     return e == cudaSuccess ? VSAOGM_OK : cuda_error(e, "batch decode");
@@ -292,26 +379,24 @@ int decode_tensor_cores(vsaogm_map *m, Region r, float *heat, cudaStream_t st)
     const int D = m->cfg.D;
     const bool bf16 = m->cfg.decode_prec == VSAOGM_DECODE_BF16X3;
     std::vector<DecodeBlock> blocks;
-    region_blocks(m, r, 128, kM, blocks);
+    tc_blocks(m, r, blocks);
     const int nb = (int)blocks.size();
-    // slices of the frequencies so that blocks x slices fills the 152 SMs once
-    int splits = std::max(1, std::min((D + kKS - 1) / kKS, 152 / std::max(nb, 1)));
+    // slices of the frequencies so that blocks x slices fills the 152 SMs once,
+    // and no slice longer than kTcMaxKPerSplit
+    int splits = std::max((D + kTcMaxKPerSplit - 1) / kTcMaxKPerSplit,
+                          std::min((D + kKS - 1) / kKS, 152 / std::max(nb, 1)));
     int kps = ((D + splits - 1) / splits + kKS - 1) / kKS * kKS;
     splits = (D + kps - 1) / kps;
     const size_t cells = (size_t)r.w() * r.h();
     int rc = ensure(m->ws.dec_partial, sizeof(float) * (size_t)splits * 2 * cells);
     if (rc) return rc;
-    float u_scale = 1.f;
-    if (!bf16) {
-        while (u_scale * u_scale * 4.f <= (float)D) u_scale *= 2.f;
-    }
-    const size_t smem_max = 1024 + 2 * (size_t)(kAStage + 2 * 128 * kRowBytes);
+    const float u_scale = tc_u_scale(m);
     cudaError_t e = bf16 ? cudaFuncSetAttribute(decode_tc_kernel<true>,
                                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                (int)smem_max)
+                                                (int)kSmemMax)
                          : cudaFuncSetAttribute(decode_tc_kernel<false>,
                                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                (int)smem_max);
+                                                (int)kSmemMax);
     if (e != cudaSuccess) return cuda_error(e, "decode: tensor cores");
     StageScope sc(m, VSAOGM_STAGE_DECODE, st);
     float *part = (float *)m->ws.dec_partial.ptr;
@@ -326,16 +411,16 @@ int decode_tensor_cores(vsaogm_map *m, Region r, float *heat, cudaStream_t st)
             widest = std::max(widest, batch.b[q].i1 - batch.b[q].i0);
         }
         const int N = (widest + 15) / 16 * 16;  // MMA N: the widest block, multiple of 16
-        const size_t smem = 1024 + 2 * (size_t)(kAStage + 2 * N * kRowBytes);
+        const size_t smem = 1024 + 2 * (size_t)stage_size(N);
         dim3 grid(batch.n, splits);
         if (bf16)
-            decode_tc_kernel<true><<<grid, 256, smem, st>>>(batch, m->omega, m->inv_norm, m->nu, D,
-                                                            og, m->col_off, m->row_off, kps, N,
-                                                            u_scale, part, m->status);
+            decode_tc_kernel<true><<<grid, kThreads, smem, st>>>(
+                batch, m->omega, m->inv_norm, m->nu, D, m->cfg.tiles_x, m->row_tile, og,
+                m->col_off, m->row_off, kps, N, u_scale, part, m->status);
         else
-            decode_tc_kernel<false><<<grid, 256, smem, st>>>(batch, m->omega, m->inv_norm, m->nu,
-                                                             D, og, m->col_off, m->row_off, kps, N,
-                                                             u_scale, part, m->status);
+            decode_tc_kernel<false><<<grid, kThreads, smem, st>>>(
+                batch, m->omega, m->inv_norm, m->nu, D, m->cfg.tiles_x, m->row_tile, og,
+                m->col_off, m->row_off, kps, N, u_scale, part, m->status);
         ++launches;
     }
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_error(e, "decode: tensor cores");

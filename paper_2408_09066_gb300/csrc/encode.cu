@@ -252,11 +252,13 @@ __global__ void __launch_bounds__(256) seg_scatter_kernel(const float2 *__restri
 //      2^-20 turns each) and the rounding of p1 - r when |p1 - r| outgrows
 //      |p1| (at most ulp(32.5)/2 = 2^-19 turns); about 4e-6 turns (2.5e-5
 //      rad) in the worst case, far less on average.
-//    Exact reduction (points far from their tile centre, e.g. outside the
-//      map): each product is reduced on its own, f_i = p_i - rint(p_i), which
-//      is exact; the product errors e_i = nu d - p_i are recovered with FMA
-//      (TwoProduct); g = (f1 + f2) + (e1 + e2) is reduced once more to
-//      [-1/2, 1/2].  The phase error is about 2^-24 turns.
+//    Exact reduction (points far from their tile centre, e.g. large tiles or
+//      points outside the map): each product is reduced against its own
+//      nearest integer with one FMA, f_i = fl(nu_i d_i - rint(p_i)), whose
+//      exact value is at most 1/2 + 2^-24 |p_i| in magnitude, so the FMA's
+//      single rounding costs at most 2^-25 turns; g = fl(f1 + f2) (|g| <= 1,
+//      another 2^-25) is reduced once more to [-1/2, 1/2] (exact).  The phase
+//      error is at most 3 * 2^-25 turns (6e-7 rad).
 template <int KPT, bool EXACT>
 __device__ __forceinline__ void encode_points(const float2 *sp, int len, const float (&nx)[KPT],
                                               const float (&ny)[KPT], float (&ar)[KPT],
@@ -273,11 +275,10 @@ __device__ __forceinline__ void encode_points(const float2 *sp, int len, const f
             float p2 = __fmul_rn(ny[j], q.y);
             float f;
             if (EXACT) {
-                float e1 = fmaf(nx[j], q.x, -p1);
-                float e2 = fmaf(ny[j], q.y, -p2);
-                float f1 = __fsub_rn(p1, __fsub_rn(__fadd_rn(p1, kMagic), kMagic));
-                float f2 = __fsub_rn(p2, __fsub_rn(__fadd_rn(p2, kMagic), kMagic));
-                float g = __fadd_rn(__fadd_rn(f1, f2), __fadd_rn(e1, e2));
+                // -rint(p) = M - (p + M), exactly
+                float n1 = __fsub_rn(kMagic, __fadd_rn(p1, kMagic));
+                float n2 = __fsub_rn(kMagic, __fadd_rn(p2, kMagic));
+                float g = __fadd_rn(fmaf(nx[j], q.x, n1), fmaf(ny[j], q.y, n2));
                 f = __fsub_rn(g, __fsub_rn(__fadd_rn(g, kMagic), kMagic));
             } else {
                 float r = __fsub_rn(__fadd_rn(__fadd_rn(p1, p2), kMagic), kMagic);
@@ -362,7 +363,6 @@ __global__ void __launch_bounds__(256) encode_chunk_kernel(const float2 *__restr
 //     on |pi f| <= pi/2 (sin to x^11, cos to x^12: truncation below 6e-8),
 //     squared as a complex number; the other pairs use MUFU sin/cos.  The
 //     phase reduction is the one of encode_points, lane by lane.
-__device__ __forceinline__ sm100::f32x2 neg2(sm100::f32x2 a) { return a ^ 0x8000000080000000ull; }
 
 template <int NP, int NPOLY, bool EXACT>
 __device__ __forceinline__ void encode_points_x2(const float2 *sp, int len,
@@ -394,11 +394,9 @@ __device__ __forceinline__ void encode_points_x2(const float2 *sp, int len,
             f32x2 p1 = mul2(nx[j], qx), p2 = mul2(ny[j], qy);
             f32x2 f;
             if (EXACT) {
-                f32x2 e1 = fma2(nx[j], qx, neg2(p1));
-                f32x2 e2 = fma2(ny[j], qy, neg2(p2));
-                f32x2 f1 = sub2(p1, sub2(add2(p1, kM), kM));
-                f32x2 f2 = sub2(p2, sub2(add2(p2, kM), kM));
-                f32x2 g = add2(add2(f1, f2), add2(e1, e2));
+                // as encode_points: f_i = fl(nu_i d_i - rint(p_i)) with one FMA
+                f32x2 n1 = sub2(kM, add2(p1, kM)), n2 = sub2(kM, add2(p2, kM));
+                f32x2 g = add2(fma2(nx[j], qx, n1), fma2(ny[j], qy, n2));
                 f = sub2(g, sub2(add2(g, kM), kM));
             } else {
                 // t = nu_x dx + nu_y dy with one rounding of the sum (FMA);
@@ -491,16 +489,14 @@ __device__ __forceinline__ void encode_chunk_x2_body(const float2 *__restrict__ 
             encode_points_x2<NP, P, false>(sp, len, nx, ny, ac, as);
         else
             encode_points_x2<NP, P, true>(sp, len, nx, ny, ac, as);
+    } else if (!fast) {
+        // the exact reduction leaves the FMA pipe no room for polynomial
+        // exponentials: every warp takes the MUFU path
+        encode_points_x2<NP, 0, true>(sp, len, nx, ny, ac, as);
     } else if ((int)(threadIdx.x >> 5) < poly_warps) {
-        if (fast)
-            encode_points_x2<NP, 1, false>(sp, len, nx, ny, ac, as);
-        else
-            encode_points_x2<NP, 1, true>(sp, len, nx, ny, ac, as);
+        encode_points_x2<NP, 1, false>(sp, len, nx, ny, ac, as);
     } else {
-        if (fast)
-            encode_points_x2<NP, 0, false>(sp, len, nx, ny, ac, as);
-        else
-            encode_points_x2<NP, 0, true>(sp, len, nx, ny, ac, as);
+        encode_points_x2<NP, 0, false>(sp, len, nx, ny, ac, as);
     }
 #pragma unroll
     for (int j = 0; j < NP; ++j) {

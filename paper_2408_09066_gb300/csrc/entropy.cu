@@ -6,10 +6,14 @@
 // A CTA owns a 32 x 32 block of output cells.  It stages the summand
 // h = -P_hat ln P_hat (0 for P_hat = 0) of both classes over the block plus a
 // halo of R = max(r_occ, r_emp) cells in shared memory (zero outside the grid,
-// which is the same as skipping off-grid neighbours), then sums each cell's
-// disk row by row using the exact integer half-widths of the disk.  With raw
-// input the non-linearity (P / max P)^2 of Eq. non-linearities is applied while
-// staging, so P_hat never makes a round trip through HBM.
+// which is the same as skipping off-grid neighbours), turns every staged row
+// into running sums, and sums each cell's disk row by row as differences of
+// two running sums at the exact integer half-widths of the disk (2 loads per
+// disk row instead of one per disk cell).  With raw input the non-linearity
+// (P / max P)^2 of Eq. non-linearities is applied while staging, so P_hat
+// never makes a round trip through HBM.  ln, exp and the reciprocals use the
+// fast hardware approximations: their errors (about 1e-6 relative) are far
+// below the probabilities' 1e-3 tolerance.
 #include <algorithm>
 
 #include "internal.cuh"
@@ -18,8 +22,7 @@ namespace vsaogm_impl {
 namespace {
 
 constexpr int kTB = 32;                       // output cells per block edge
-constexpr int kSW = kTB + 2 * kMaxRadius;     // staged edge (64)
-constexpr int kSP = kSW + 1;                  // padded row stride
+constexpr int kSW = kTB + 2 * kMaxRadius;     // largest staged edge (64)
 
 struct DiskParams {
     int r[2];                          // radius per class (0 = empty, 1 = occupied)
@@ -31,20 +34,23 @@ struct DiskParams {
 // grid, and writes output (x, y) of the ww x wh window, row stride ww.
 // The work of one CTA (the 32 x 32 output cells from window cell (bx0, by0)).
 // r: disk radius per class; hw: the disks' half-widths per class and dy, in
-// shared memory ([2][2 kMaxRadius + 1], -1 outside the disk).
+// shared memory ([2][2 kMaxRadius + 1], -1 outside the disk).  sh: dynamic
+// shared memory of staged_floats(R) floats.
 __device__ __forceinline__ void entropy_body(const float *__restrict__ heat, int W, int H, int wx0,
                                              int wy0, int ww, int wh, int raw,
                                              const unsigned *__restrict__ maxima, const int *r_c,
                                              const int *hw, unsigned mode, float rho,
                                              float *__restrict__ occ, float *__restrict__ ogm,
-                                             uint8_t *__restrict__ cls, int bx0, int by0)
+                                             uint8_t *__restrict__ cls, int bx0, int by0,
+                                             float *sh)
 {
-    __shared__ float sh[2][kSW][kSP];
     const unsigned act = mode & VSAOGM_ACT_MASK;
     const bool stencil = act == VSAOGM_ACT_ENTROPY;
     const int R = stencil ? max(r_c[0], r_c[1]) : 0;
     const int x0 = wx0 + bx0, y0 = wy0 + by0;                  // grid coordinates
-    const int edge = kTB + 2 * R;
+    // staged row: column 0 holds 0, column 1 + lx the summand at lx (after the
+    // prefix pass, the sum of the summands left of and at lx)
+    const int edge = kTB + 2 * R, pitch = edge + 1;
     float inv[2] = {1.f, 1.f};
     const bool norm = raw && !(mode & VSAOGM_MODE_NO_NORM);
     const bool square = raw && !(mode & VSAOGM_MODE_NO_SQUARE);
@@ -55,23 +61,59 @@ __device__ __forceinline__ void entropy_body(const float *__restrict__ heat, int
         }
     }
     const size_t cells = (size_t)W * H;
-    for (int c = 0; c < 2; ++c) {
-        for (int e = threadIdx.x; e < edge * edge; e += blockDim.x) {
-            int ly = e / edge, lx = e % edge;
-            int y = y0 - R + ly, x = x0 - R + lx;
-            float h = 0.f;
-            if (x >= 0 && x < W && y >= 0 && y < H) {
-                float v = heat[c * cells + (size_t)y * W + x];
-                if (norm) v *= inv[c];
-                if (square) v = v * v;
-                // entropy summand -v ln v (0 for v <= 0); other activations keep v
-                h = stencil ? (v > 0.f ? -v * logf(v) : 0.f) : v;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    // Stage: every load of the thread is issued before any is used (rows
+    // warp + 8 i, columns lane + 32 s of the staged square), so their
+    // latencies overlap.  Off-grid cells read as 0, whose summand is 0.
+    constexpr int kRows = kSW / 8, kStrips = kSW / 32;
+    float v[2][kRows][kStrips];
+#pragma unroll
+    for (int c = 0; c < 2; ++c)
+#pragma unroll
+        for (int i = 0; i < kRows; ++i)
+#pragma unroll
+            for (int q = 0; q < kStrips; ++q) {
+                const int ly = warp + 8 * i, lx = lane + 32 * q;
+                const int y = y0 - R + ly, x = x0 - R + lx;
+                v[c][i][q] = (ly < edge && lx < edge && x >= 0 && x < W && y >= 0 && y < H)
+                                 ? __ldg(heat + c * cells + (size_t)y * W + x)
+                                 : 0.f;
             }
-            sh[c][ly][lx] = h;
+#pragma unroll
+    for (int c = 0; c < 2; ++c)
+#pragma unroll
+        for (int i = 0; i < kRows; ++i) {
+            const int ly = warp + 8 * i;
+            if (ly >= edge) continue;
+            float *row = sh + (c * edge + ly) * pitch;
+            if (lane == 0) row[0] = 0.f;
+#pragma unroll
+            for (int q = 0; q < kStrips; ++q) {
+                const int lx = lane + 32 * q;
+                if (lx < edge) {
+                    float x = v[c][i][q];
+                    if (norm) x *= inv[c];
+                    if (square) x = x * x;
+                    // entropy summand -x ln x (0 for x <= 0); other activations keep x
+                    row[1 + lx] = stencil ? (x > 0.f ? -x * __logf(x) : 0.f) : x;
+                }
+            }
         }
-    }
     __syncthreads();
-    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    if (stencil) {
+        // running sums along each staged row, one thread per row
+        for (int rr = threadIdx.x; rr < 2 * edge; rr += blockDim.x) {
+            float *row = sh + rr * pitch + 1;
+            float acc = 0.f;
+#pragma unroll 8
+            for (int lx = 0; lx < edge; ++lx) {
+                acc += row[lx];
+                row[lx] = acc;
+            }
+        }
+        __syncthreads();
+    }
+    const int tx = lane, ty = warp;
     for (int q = 0; q < kTB / 8; ++q) {
         int ly = ty + 8 * q;
         int x = bx0 + tx, y = by0 + ly;  // window coordinates of the output cell
@@ -80,31 +122,41 @@ __device__ __forceinline__ void entropy_body(const float *__restrict__ heat, int
         for (int c = 0; c < 2; ++c) {
             if (!stencil) {
                 // per-cell activations of the decoding ablation
-                const float v = sh[c][ly][tx];
-                Hc[c] = act == VSAOGM_ACT_RELU      ? fmaxf(v, 0.f)
-                        : act == VSAOGM_ACT_TANH    ? tanhf(v)
-                        : act == VSAOGM_ACT_SIGMOID ? 1.0f / (1.0f + expf(-v))
-                                                    : v;
+                const float u = sh[(c * edge + ly) * pitch + 1 + tx];
+                Hc[c] = act == VSAOGM_ACT_RELU      ? fmaxf(u, 0.f)
+                        : act == VSAOGM_ACT_TANH    ? tanhf(u)
+                        : act == VSAOGM_ACT_SIGMOID ? 1.0f / (1.0f + expf(-u))
+                                                    : u;
                 continue;
             }
+            // the disk as rows dy of half-width w: each row's sum is the
+            // difference of two running sums
             const int r = r_c[c];
-            float s = 0.f;
+            const int *hwc = hw + c * (2 * kMaxRadius + 1) + kMaxRadius;
+            float acc = 0.f;
             for (int dy = -r; dy <= r; ++dy) {
-                const int w = hw[c * (2 * kMaxRadius + 1) + dy + kMaxRadius];
-                const float *row = &sh[c][R + ly + dy][R + tx];
-                for (int dx = -w; dx <= w; ++dx) s += row[dx];
+                const int w = hwc[dy];
+                const float *row = sh + (c * edge + R + ly + dy) * pitch + R + tx;
+                acc += row[w + 1] - row[-w];
             }
-            Hc[c] = s;
+            Hc[c] = acc;
         }
         // Eq. softmax for two classes, then Eq. psd and Eq. classification
-        float pr1 = 1.0f / (1.0f + expf(Hc[0] - Hc[1]));
-        float pr0 = 1.0f / (1.0f + expf(Hc[1] - Hc[0]));
+        float pr1 = __fdividef(1.0f, 1.0f + __expf(Hc[0] - Hc[1]));
+        float pr0 = __fdividef(1.0f, 1.0f + __expf(Hc[1] - Hc[0]));
         size_t o = (size_t)y * ww + x;
         occ[o] = pr1;
         float d = pr1 - pr0;
         if (ogm) ogm[o] = d;
         if (cls) cls[o] = d >= rho ? 1 : 0;
     }
+}
+
+// Floats of staged summands for halo R: two classes of (32 + 2R) rows of
+// pitch 32 + 2R + 1.
+__host__ __device__ inline size_t staged_floats(int R)
+{
+    return 2 * (size_t)(kTB + 2 * R) * (kTB + 2 * R + 1);
 }
 
 constexpr int kHW = 2 * kMaxRadius + 1;
@@ -120,20 +172,28 @@ __global__ void __launch_bounds__(256) entropy_kernel(const float *__restrict__ 
                                                       float *__restrict__ ogm,
                                                       uint8_t *__restrict__ cls)
 {
+    extern __shared__ float sh_dyn[];
     __shared__ int hw[2 * kHW];
     if (threadIdx.x < 2 * kHW) hw[threadIdx.x] = dp.hw[threadIdx.x / kHW][threadIdx.x % kHW];
     __syncthreads();
     entropy_body(heat, W, H, wx0, wy0, ww, wh, raw, maxima, dp.r, hw, mode, rho, occ, ogm, cls,
-                 blockIdx.x * kTB, blockIdx.y * kTB);
+                 blockIdx.x * kTB, blockIdx.y * kTB, sh_dyn);
 }
 
-// Every map of a batch in one launch: blockIdx.z is the map; the grid covers
-// the largest map and CTAs beyond a map's extent return at once.
+// Every map of a batch in one launch: CTA q takes block q of the list of all
+// maps' 32 x 32 blocks (map by binary search over the first block of each).
 __global__ void __launch_bounds__(256) entropy_batch_kernel(const __grid_constant__ BatchOutTable tab)
 {
-    const BatchMapOut &M = tab.m[blockIdx.z];
-    const int bx0 = blockIdx.x * kTB, by0 = blockIdx.y * kTB;
-    if (bx0 >= M.W || by0 >= M.H) return;
+    extern __shared__ float sh_dyn[];
+    const int q = blockIdx.x;
+    int lo = 0, hi = tab.n_maps - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (tab.m[mid].blk_begin <= q) lo = mid; else hi = mid - 1;
+    }
+    const BatchMapOut &M = tab.m[lo];
+    const int local = q - M.blk_begin, bxn = (M.W + kTB - 1) / kTB;
+    const int bx0 = (local % bxn) * kTB, by0 = (local / bxn) * kTB;
     __shared__ int hw[2 * kHW];
     if (threadIdx.x < 2 * kHW) {
         // half-width of the disk of class c at row offset dy (Eq. entropy-mask)
@@ -145,15 +205,21 @@ __global__ void __launch_bounds__(256) entropy_batch_kernel(const __grid_constan
     }
     __syncthreads();
     entropy_body(M.heat, M.W, M.H, 0, 0, M.W, M.H, 1, M.maxima, M.r, hw, M.mode, M.rho, M.occ,
-                 M.ogm, nullptr, bx0, by0);
+                 M.ogm, nullptr, bx0, by0, sh_dyn);
 }
 
 }  // namespace
 
-int launch_entropy_batch(const BatchOutTable &tab, int w_max, int h_max, cudaStream_t st)
+int launch_entropy_batch(const BatchOutTable &tab, cudaStream_t st)
 {
-    dim3 grid((w_max + kTB - 1) / kTB, (h_max + kTB - 1) / kTB, tab.n_maps);
-    entropy_batch_kernel<<<grid, 256, 0, st>>>(tab);
+    int blocks = 0, R = 0;
+    for (int i = 0; i < tab.n_maps; ++i) {
+        const BatchMapOut &M = tab.m[i];
+        if (M.blk_begin != blocks) return set_error(VSAOGM_E_INVAL, "batch entropy: block table");
+        blocks += ((M.W + kTB - 1) / kTB) * ((M.H + kTB - 1) / kTB);
+        if ((M.mode & VSAOGM_ACT_MASK) == VSAOGM_ACT_ENTROPY) R = std::max(R, std::max(M.r[0], M.r[1]));
+    }
+    entropy_batch_kernel<<<blocks, 256, staged_floats(R) * sizeof(float), st>>>(tab);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? VSAOGM_OK : cuda_error(e, "batch entropy");
 }
@@ -168,7 +234,10 @@ int entropy(vsaogm_map *m, const float *heat, Region r, Region win, bool raw_inp
         for (int d = 0; d < 2 * kMaxRadius + 1; ++d) dp.hw[c][d] = m->r_hw[c][d];
     dim3 grid((win.w() + kTB - 1) / kTB, (win.h() + kTB - 1) / kTB);
     StageScope sc(m, VSAOGM_STAGE_ENTROPY, st);
-    entropy_kernel<<<grid, 256, 0, st>>>(heat, r.w(), r.h(), win.x0 - r.x0, win.y0 - r.y0,
+    const unsigned act = m->cfg.decode_mode & VSAOGM_ACT_MASK;
+    const int R = act == VSAOGM_ACT_ENTROPY ? std::max(dp.r[0], dp.r[1]) : 0;
+    entropy_kernel<<<grid, 256, staged_floats(R) * sizeof(float), st>>>(
+                                         heat, r.w(), r.h(), win.x0 - r.x0, win.y0 - r.y0,
                                          win.w(), win.h(), raw_input ? 1 : 0, m->maxima, dp,
                                          m->cfg.decode_mode, m->cfg.rho, occ, ogm, cls);
     cudaError_t e = cudaGetLastError();

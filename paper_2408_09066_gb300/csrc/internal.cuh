@@ -43,6 +43,15 @@ struct DecodeBlock {
 
 // Blocks of one decode launch, passed by value as a kernel parameter.
 constexpr int kMaxLaunchBlocks = 128;
+// Tile rows one tensor-core decode block may span (its rows cross tile rows;
+// DecodeBlock.tile is then the tile column).
+constexpr int kMaxBlockTiles = 16;
+// Frequencies one tensor-core CTA accumulates in tensor memory.  The MMA's
+// FP32 accumulation is not correctly rounded (its error grows about linearly
+// with the number of MMAs summed into one accumulator: 1e-4 of max P after
+// all 8192 frequencies of a map), so longer sums are cut into slices that the
+// slice sum adds in FP32 with round-to-nearest.
+constexpr int kTcMaxKPerSplit = 2048;
 struct BlockBatch {
     int n;
     DecodeBlock b[kMaxLaunchBlocks];
@@ -91,9 +100,10 @@ struct BatchReduceTable {
 struct BatchDecodeMap {
     const float2 *omega;
     const float *inv_norm, *nu, *col_off, *row_off;
+    const int *row_tile;    // tile row of each cell row
     float *partial;         // [slices][2][H][W]
     int *status;
-    int D, k_per_split, W, H;
+    int D, k_per_split, W, H, tiles_x;
     float u_scale;
 };
 struct BatchDecodeTable {
@@ -123,6 +133,7 @@ struct BatchMapOut {
     float inv_scale, rho;
     int r[2];               // disk radius of class 0 (empty) and 1 (occupied)
     unsigned mode;
+    int blk_begin;          // first 32 x 32 entropy block of this map in the batch
 };
 struct BatchOutTable {
     int n_maps;
@@ -237,6 +248,8 @@ int sum_slices(vsaogm_map *m, const float *partial, int splits, size_t cells, fl
                float *heat, cudaStream_t st);
 // decode_tc.cu: split-precision tensor-core decode of region r (P and maxima)
 int decode_tensor_cores(vsaogm_map *m, Region r, float *heat, cudaStream_t st);
+// the tensor-core decode's blocks of region r (rows across tile rows)
+void tc_blocks(const vsaogm_map *m, Region r, std::vector<DecodeBlock> &out);
 
 // entropy.cu
 // heat holds the class maps of region r ([2][r.h()][r.w()]); the outputs cover
@@ -262,7 +275,7 @@ int launch_norms_batch(const BatchNormTable &tab, int total_memories, cudaStream
 int launch_sums_batch(const BatchOutTable &tab, size_t max_cells, cudaStream_t st);
 int launch_decode_tc_batch(const BatchDecodeTable &tab, const BatchDecodeItem *items,
                            int n_items, bool bf16, cudaStream_t st);
-int launch_entropy_batch(const BatchOutTable &tab, int w_max, int h_max, cudaStream_t st);
+int launch_entropy_batch(const BatchOutTable &tab, cudaStream_t st);
 float tc_u_scale(const vsaogm_map *m);
 
 inline Region full_region(const vsaogm_map *m)
