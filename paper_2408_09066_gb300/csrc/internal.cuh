@@ -104,7 +104,7 @@ struct BatchDecodeMap {
     float *partial;         // [slices][2][H][W]
     int *status;
     int D, k_per_split, W, H, tiles_x;
-    float u_scale;
+    float u_scale, res;
 };
 struct BatchDecodeTable {
     int n_maps;
