@@ -54,12 +54,14 @@ def parse_args():
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--decode", choices=["fp32", "bf16x3", "fp16x3"], default="bf16x3",
                    help="decode arithmetic of the headline path (fp32 plain is also timed)")
-    p.add_argument("--workload", choices=["paper", "toysim", "intel", "evilog", "batch64"],
+    p.add_argument("--workload", choices=["paper", "small", "toysim", "intel", "evilog",
+                                          "batch64"],
                    default="paper",
-                   help="paper: the 400x400 / 4x4 / D=8192 / 2.27M-point map; toysim, intel, "
-                        "evilog: shaped like the paper's dataset table (context rows); batch64: "
-                        "64 maps of uneven size stepped together (one launch per stage, CUDA "
-                        "graph, autotuned)")
+                   help="paper: the 400x400 / 4x4 / D=8192 / 2.27M-point map; small: one "
+                        "360-beam scan on a 64x64 / 1-tile / D=1024 map (latency); toysim, "
+                        "intel, evilog: shaped like the paper's dataset table (context rows); "
+                        "batch64: 64 maps of uneven size stepped together (one launch per "
+                        "stage, CUDA graph, autotuned)")
     p.add_argument("--no-cpu-baseline", action="store_true",
                    help="skip the oracle timing (for quick runs)")
     return p.parse_args()
@@ -288,13 +290,14 @@ METRIC = "points bundled/s + grid cells decoded/s at D=8192 vs FP32 plain; p50/p
 DATA = ("synthetic: seeded 100-scan lidar trajectory in a walled 40 m world with 40 "
         "obstacles (1080 beams, 30 m range, sigma 0.03 m, 20 empty samples per beam)")
 
-# DRAM traffic of one encode launch on this workload from an ncu capture, valid
+# DRAM traffic of one encode launch on this workload from an ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum = 22.49 MB + 86.92 MB), valid
 # only for the kernel source it was taken on (sha1 of csrc/encode.cu).
-ENCODE_TRAFFIC = {"sha1": None, "bytes": None}
+ENCODE_TRAFFIC = {"sha1": "e02b65a9abb134f26fff4960f884efe7d5456df6", "bytes": 109408512}
 
 
 def workload_config(wl, decode: str) -> dict:
-    return {"workload": f"paper-scale map {wl.W}x{wl.H} cells at {wl.res} m, "
+    return {"workload": f"{wl.name}: map {wl.W}x{wl.H} cells at {wl.res} m, "
                         f"{wl.tiles_x}x{wl.tiles_y} tiles, D={wl.D}, {wl.n} points",
             "grid": [wl.W, wl.H], "tiles": [wl.tiles_x, wl.tiles_y], "D": wl.D,
             "points_per_step": wl.n, "cells_per_step": wl.W * wl.H, "decode": decode,
@@ -305,7 +308,8 @@ def workload_config(wl, decode: str) -> dict:
 def make_workload(name: str, rank: int = 0):
     """The seeded workload of one rank (weak scaling: every rank its own map)."""
     from paper_2408_09066_gb300 import synth
-    makers = {"paper": (synth.paper_trajectory, 1002), "toysim": (synth.toysim_like, 2001),
+    makers = {"paper": (synth.paper_trajectory, 1002), "small": (synth.small_scan, 1001),
+              "toysim": (synth.toysim_like, 2001),
               "intel": (synth.intel_like, 2002), "evilog": (synth.evilog_like, 2003)}
     fn, seed = makers[name]
     return fn(seed=seed + rank)
