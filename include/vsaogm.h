@@ -53,6 +53,9 @@ extern "C" {
 #define VSAOGM_DECODE_FP32 0   /* FP32 SIMT, the reference GPU path          */
 #define VSAOGM_DECODE_BF16X3 1 /* tensor cores, split hi/lo bf16, FP32 accum */
 #define VSAOGM_DECODE_FP16X3 2 /* tensor cores, split hi/lo fp16, FP32 accum */
+#define VSAOGM_DECODE_FP8X3 3  /* tensor cores, split hi/lo e4m3, FP32 accum:
+                                  about 7 significant bits per product, the
+                                  precision study's lowest rung              */
 
 /* vsaogm_config.decode_mode: the toggles of the decoding ablation
  * (Sec. IV-D1: P_hat = f_ACT(f_NL(f_N(P))) with toggles delta_N, delta_NL,
@@ -267,7 +270,7 @@ int vsaogm_stage_times(vsaogm_map *map, double *ms, int64_t *launches, int reset
  * summation order inside each memory (one fixed order per map shape and point
  * set: a batch is deterministic run to run) and the decode slicing.
  *  - A batch refers to its maps; they must outlive it and keep their
- *    configuration.  Every map needs decode_prec BF16X3 or FP16X3 (the same
+ *    configuration.  Every map needs decode_prec BF16X3, FP16X3 or FP8X3 (the same
  *    for all), the deterministic bundling (no VSAOGM_FLAG_ATOMIC) and one
  *    device.  The batch owns its own scratch, so per-map calls on its maps
  *    never move memory a captured step uses.

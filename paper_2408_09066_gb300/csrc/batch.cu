@@ -40,7 +40,7 @@ struct Tuning {
 struct vsaogm_batch {
     std::vector<vsaogm_map *> maps;
     std::vector<Scratch> ws;                    // per map: sort, partials and decode slices
-    bool bf16 = true;
+    int decode_prec = VSAOGM_DECODE_BF16X3;     // shared by every map of the batch
     Tuning tune;
     int enc_ctas = 0;
     unsigned long long *counter = nullptr;      // encode work counter (device)
@@ -84,9 +84,10 @@ int build_decode_items(vsaogm_batch *b)
     for (size_t i = 0; i < b->maps.size(); ++i) {
         vsaogm_map *m = b->maps[i];
         const int D = m->cfg.D;
+        const int KS = tc_stage_freqs(b->decode_prec);
         int s = std::max((D + kTcMaxKPerSplit - 1) / kTcMaxKPerSplit,
-                         std::min(s_all, (D + 31) / 32));
-        const int kps = ((D + s - 1) / s + 31) / 32 * 32;
+                         std::min(s_all, (D + KS - 1) / KS));
+        const int kps = ((D + s - 1) / s + KS - 1) / KS * KS;
         s = (D + kps - 1) / kps;
         b->splits[i] = s;
         for (const DecodeBlock &blk : blocks[i])
@@ -241,8 +242,8 @@ int enqueue_step(vsaogm_batch *b, const float *const *xy, const uint8_t *const *
     int ent_blocks = 0;
     for (int i = 0; i < M; ++i) {
         vsaogm_map *m = b->maps[i];
-        const int D = m->cfg.D, s = b->splits[i];
-        const int kps = ((D + s - 1) / s + 31) / 32 * 32;
+        const int D = m->cfg.D, s = b->splits[i], KS = tc_stage_freqs(b->decode_prec);
+        const int kps = ((D + s - 1) / s + KS - 1) / KS * KS;
         const float u = tc_u_scale(m);
         dt.m[i] = BatchDecodeMap{m->omega, m->inv_norm, m->nu, m->col_off, m->row_off,
                                  m->row_tile, (float *)b->ws[i].dec_partial.ptr, m->status, D,
@@ -267,7 +268,7 @@ int enqueue_step(vsaogm_batch *b, const float *const *xy, const uint8_t *const *
         max_cells = std::max(max_cells, (size_t)o.W * o.H);
     }
     dt.n_maps = ot.n_maps = M;
-    if ((rc = launch_decode_tc_batch(dt, b->items, b->n_items, b->bf16, st))) return rc;
+    if ((rc = launch_decode_tc_batch(dt, b->items, b->n_items, b->decode_prec, st))) return rc;
     if ((rc = launch_sums_batch(ot, max_cells, st))) return rc;
     counted[VSAOGM_STAGE_DECODE] = 3;
     mark();
@@ -342,7 +343,7 @@ int vsaogm_batch_create(vsaogm_map *const *maps, int32_t count, vsaogm_batch **o
         if (!maps[i]) return batch_error(VSAOGM_E_INVAL, "NULL map in the batch");
         if (maps[i]->cfg.decode_prec == VSAOGM_DECODE_FP32)
             return batch_error(VSAOGM_E_INVAL, "batched decode runs on tensor cores: use "
-                                               "VSAOGM_DECODE_BF16X3 or VSAOGM_DECODE_FP16X3");
+                                               "VSAOGM_DECODE_BF16X3, FP16X3 or FP8X3");
         if (maps[i]->cfg.decode_prec != maps[0]->cfg.decode_prec)
             return batch_error(VSAOGM_E_INVAL, "all maps of a batch share decode_prec");
         if (maps[i]->device != maps[0]->device)
@@ -356,7 +357,7 @@ int vsaogm_batch_create(vsaogm_map *const *maps, int32_t count, vsaogm_batch **o
     if (!b) return set_error(VSAOGM_E_NOMEM, "host allocation");
     b->maps.assign(maps, maps + count);
     b->ws.resize(count);
-    b->bf16 = maps[0]->cfg.decode_prec == VSAOGM_DECODE_BF16X3;
+    b->decode_prec = maps[0]->cfg.decode_prec;
     b->enc_ctas = encode_batch_ctas();
     cudaError_t e = cudaMalloc((void **)&b->counter, sizeof(unsigned long long));
     for (int a = 0; a < kAuxStreams && e == cudaSuccess; ++a) {

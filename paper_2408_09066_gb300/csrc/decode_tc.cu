@@ -1,7 +1,7 @@
 // Decoding on the 5th-generation tensor cores (Eq. loc-query, split precision).
 //
-// For one block of up to 128 rows (y cells) x N columns (x cells) inside one
-// tile, and a slice of the frequencies k, both class maps are the real GEMM
+// For one block of up to 128 rows (y cells) x N columns (x cells) and a slice of
+// the frequencies k, both class maps are the real GEMM
 //   P_psi[m][n] = sum_k' Aop_psi[m][k'] * Bop[n][k'],
 //   Aop_psi[m][2k] = Re U_psi(j_m, k),  Aop_psi[m][2k+1] = -Im U_psi(j_m, k),
 //   Bop[n][2k]     = Re A(i_n, k),      Bop[n][2k+1]     =  Im A(i_n, k),
@@ -11,29 +11,32 @@
 // after an exact phase reduction, then the complex product), never read from
 // HBM, in the 128-byte-swizzled K-major layout the tensor cores read.
 //
-// Precision: each operand is split x = hi + lo in BF16 (or FP16, with U scaled
-// by a power of two to stay clear of FP16 subnormals) and the product is
-// hi*hi + hi*lo + lo*hi with FP32 accumulation in tensor memory: about 16
-// significant bits per product.
+// Precision: each operand is split x = hi + lo in BF16, FP16 or FP8 (e4m3) and
+// the product is hi*hi + hi*lo + lo*hi with FP32 accumulation in tensor memory:
+// about 16 significant bits per product with BF16 or FP16, about 7 with FP8.
+// U is scaled by a power of two for FP16 and FP8 to stay clear of their
+// subnormals.  A 128-byte operand row holds 32 complex frequencies in the
+// 16-bit formats (kind::f16 MMAs) and 64 in FP8 (kind::f8f6f4 MMAs).
 //
 // Blocks: up to 128 columns inside one tile column by up to 128 rows that may
 // cross tile rows (each row multiplies the memories of its own tile), so the
 // 128-row MMA tile is filled even when tiles are short.
 //
-// Pipeline per CTA (512 threads, one CTA per SM): all threads generate stage s
-// (32 frequencies) into one of two shared-memory buffers while the tensor
-// cores run stage s - 1 from the other; the memories and frequencies of stage
-// s + 1 are loaded into registers meanwhile.  One thread issues the 24 MMAs
-// of a stage (2 classes x 3 products x 4 K-steps of 16) and commits them to
-// the buffer's mbarrier.  The 128-byte swizzle puts 4-byte element kk of row
-// m at byte m * 128 + ((kk / 4) xor (m mod 8)) * 16 + (kk mod 4) * 4.  The epilogue reads the two 128 x N FP32 accumulators
-// from tensor memory and writes per-slice partial maps; a second kernel sums
-// the slices in a fixed order and folds the per-class maxima (Eq.
-// non-linearities needs the map maximum).  Every wait is bounded: on time-out
-// the CTA records VSAOGM_E_TIMEOUT, drains its MMAs, frees its tensor memory
-// and returns.
+// Pipeline per CTA (one CTA per SM): 16 producer warps generate stage s into one
+// of two shared-memory buffers while the tensor cores run stage s - 1 from the
+// other; the memories and frequencies of stage s + 1 are loaded into registers
+// meanwhile.  A 17th warp issues the 24 MMAs of a stage (2 classes x 3 products
+// x 4 K-steps of 32 bytes) and commits them to the buffer's mbarrier.  The
+// 128-byte swizzle puts 4-byte word kk of row m at byte
+// m * 128 + ((kk / 4) xor (m mod 8)) * 16 + (kk mod 4) * 4.  The epilogue reads
+// the two 128 x N FP32 accumulators from tensor memory and writes per-slice
+// partial maps; a second kernel sums the slices in a fixed order and folds the
+// per-class maxima (Eq. non-linearities needs the map maximum).  Every wait is
+// bounded: on time-out the CTA records VSAOGM_E_TIMEOUT, drains its MMAs, frees
+// its tensor memory and returns.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
+#include <cuda_fp8.h>
 
 #include <algorithm>
 
@@ -45,8 +48,9 @@ namespace {
 
 using namespace sm100;
 
+enum TcPrec { kPrecBF16 = 0, kPrecFP16 = 1, kPrecFP8 = 2 };
+
 constexpr int kM = 128;            // rows per block (MMA M)
-constexpr int kKS = 32;            // frequencies per stage (64 k' = 128 bytes per row)
 constexpr int kRowBytes = 128;
 constexpr int kProducers = 512;    // 16 warps generate the operands ...
 constexpr int kWarps = kProducers / 32;
@@ -54,15 +58,21 @@ constexpr int kThreads = kProducers + 32;  // ... and one more issues the MMAs
 constexpr int kQ = kM / kWarps;    // rows (and columns) per thread
 constexpr int kATile = kM * kRowBytes;          // one A operand tile (16 KB)
 constexpr int kAStage = 4 * kATile;             // 2 classes x hi/lo (64 KB)
-constexpr int kWBytes = kMaxBlockTiles * 2 * kKS * 8;  // staged memories (8 KB)
-constexpr int kWPerThread = (kMaxBlockTiles * 2 * kKS + kProducers - 1) / kProducers;
 constexpr int kTmemCols = 256;                  // class psi accumulates at column 128 psi
 constexpr uint64_t kWaitNs = 2000000000ull;     // 2 s: far above any legitimate wait
 
+// Frequencies per stage (one 128-byte operand row).
+__host__ __device__ constexpr int stage_freqs(int prec) { return prec == kPrecFP8 ? 64 : 32; }
+// Bytes of the staged memories of one stage: (tile row, class, frequency) float2.
+__host__ __device__ constexpr int w_bytes(int prec) { return kMaxBlockTiles * 2 * stage_freqs(prec) * 8; }
 // Bytes of one pipeline stage for MMA width N: A (both classes, hi and lo),
 // B (hi and lo) and the staged memories.
-__host__ __device__ constexpr int stage_size(int N) { return kAStage + 2 * N * kRowBytes + kWBytes; }
-constexpr size_t kSmemMax = 1024 + 2 * (size_t)stage_size(kM);
+__host__ __device__ constexpr int stage_size(int prec, int N)
+{
+    return kAStage + 2 * N * kRowBytes + w_bytes(prec);
+}
+__host__ __device__ constexpr size_t smem_max(int prec) { return 1024 + 2 * (size_t)stage_size(prec, kM); }
+static_assert(smem_max(kPrecFP8) <= 232448, "two FP8 stages fit in shared memory");
 
 __device__ __forceinline__ float2 phasor(float nu, float d)
 {
@@ -81,10 +91,12 @@ __device__ __forceinline__ float2 cmul(float2 a, float2 b)
     return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
 
-template <bool BF16>
-__device__ __forceinline__ void split2(float x, float y, uint32_t &hi, uint32_t &lo)
+// Splits two 16-bit operand values (x, y) into a 4-byte word of hi parts and
+// one of lo parts, x = hi + lo up to the rounding of lo.
+template <int P>
+__device__ __forceinline__ void split_pair(float x, float y, uint32_t &hi, uint32_t &lo)
 {
-    if (BF16) {
+    if (P == kPrecBF16) {
         __nv_bfloat162 h = __floats2bfloat162_rn(x, y);
         const uint32_t hb = *reinterpret_cast<uint32_t *>(&h);
         // bf16 -> f32 is a shift of the bit pattern; both residuals in one packed sub
@@ -102,6 +114,44 @@ __device__ __forceinline__ void split2(float x, float y, uint32_t &hi, uint32_t 
     }
 }
 
+// The same for four FP8 (e4m3) values (x, y, z, w) in one word.  Conversions
+// saturate; the scaled operands stay far below e4m3's 448.
+__device__ __forceinline__ void split_quad_e4m3(float x, float y, float z, float w, uint32_t &hi,
+                                                uint32_t &lo)
+{
+    const __nv_fp8x2_storage_t h0 =
+        __nv_cvt_float2_to_fp8x2(make_float2(x, y), __NV_SATFINITE, __NV_E4M3);
+    const __nv_fp8x2_storage_t h1 =
+        __nv_cvt_float2_to_fp8x2(make_float2(z, w), __NV_SATFINITE, __NV_E4M3);
+    const float2 f0 = __half22float2(__half2(__nv_cvt_fp8x2_to_halfraw2(h0, __NV_E4M3)));
+    const float2 f1 = __half22float2(__half2(__nv_cvt_fp8x2_to_halfraw2(h1, __NV_E4M3)));
+    const __nv_fp8x2_storage_t l0 =
+        __nv_cvt_float2_to_fp8x2(make_float2(x - f0.x, y - f0.y), __NV_SATFINITE, __NV_E4M3);
+    const __nv_fp8x2_storage_t l1 =
+        __nv_cvt_float2_to_fp8x2(make_float2(z - f1.x, w - f1.y), __NV_SATFINITE, __NV_E4M3);
+    hi = (uint32_t)h0 | ((uint32_t)h1 << 16);
+    lo = (uint32_t)l0 | ((uint32_t)l1 << 16);
+}
+
+template <int P>
+__device__ __forceinline__ void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc,
+                                    uint32_t acc)
+{
+    if (P == kPrecFP8)
+        mma_f8f6f4(d, a, b, idesc, acc);
+    else
+        mma_f16(d, a, b, idesc, acc);
+}
+
+// Instruction descriptor: FP32 accumulation, K-major A and B; the format
+// fields are 0 = FP16 / 1 = BF16 for kind::f16 and 0 = E4M3 (both operands)
+// for kind::f8f6f4.
+template <int P>
+__host__ __device__ constexpr uint32_t idesc_of(int N)
+{
+    return idesc_f16(kM, N, P == kPrecBF16);
+}
+
 // One (block of cells, frequency slice) item, executed by the whole CTA:
 // kProducers threads (16 warps) generate the operands, one more warp issues
 // the MMAs.  The block's columns lie in tile column b.tile; its rows may cross
@@ -116,7 +166,10 @@ __device__ __forceinline__ void split2(float x, float y, uint32_t &hi, uint32_t 
 // memories are staged by all of them for all of them.  Every wait is bounded;
 // after a time-out the CTA stops waiting, records VSAOGM_E_TIMEOUT, drains
 // and frees its tensor memory.
-template <bool BF16>
+//
+// Producer lane l owns frequencies FPL l .. FPL l + FPL - 1 of the stage (FPL =
+// 1 for 16-bit operands, 2 for FP8): one 4-byte word per operand row.
+template <int P>
 __device__ __forceinline__ void decode_tc_body(
     const DecodeBlock b, const int split, const float2 *__restrict__ omega,
     const float *__restrict__ inv_norm, const float *__restrict__ nu, int D, int tiles_x,
@@ -124,18 +177,23 @@ __device__ __forceinline__ void decode_tc_body(
     const float *__restrict__ row_off, float res, int k_per_split, int N, float u_scale,
     float *__restrict__ partial, int *__restrict__ status)
 {
+    constexpr int KS = stage_freqs(P);       // frequencies per stage
+    constexpr int FPL = KS / 32;             // frequencies per producer lane
+    constexpr int kWEnt = kMaxBlockTiles * 2 * KS;
+    constexpr int kWPerThread = kWEnt / kProducers;
+    static_assert(kWEnt % kProducers == 0, "staged memories split evenly");
     extern __shared__ uint8_t smem_raw[];
     __shared__ uint64_t full_bar[2], empty_bar[2], done_bar;
     __shared__ uint32_t tmem_base_s;
     __shared__ int abort_s;
     volatile int *abort_v = &abort_s;
     uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    const int stage_bytes = stage_size(N);
+    const int stage_bytes = stage_size(P, N);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int k_begin = split * k_per_split;
     const int k_end = min(D, k_begin + k_per_split);
-    const int n_stages = (k_end - k_begin + kKS - 1) / kKS;
+    const int n_stages = (k_end - k_begin + KS - 1) / KS;
     const int ni = b.i1 - b.i0, nj = b.j1 - b.j0;
     const int by0 = row_tile[b.j0];
     const int nt = row_tile[b.j1 - 1] - by0 + 1;  // tile rows of the block
@@ -165,7 +223,7 @@ __device__ __forceinline__ void decode_tc_body(
 
     if (warp == kWarps) {
         // ------------------------------------------------------ MMA warp
-        const uint32_t idesc = idesc_f16(kM, N, BF16);
+        const uint32_t idesc = idesc_of<P>(N);
         for (int s = 0; s < n_stages; ++s) {
             const int buf = s & 1;
             if (!*abort_v && !mbar_wait(&full_bar[buf], (uint32_t)(s >> 1) & 1u, kWaitNs))
@@ -177,16 +235,16 @@ __device__ __forceinline__ void decode_tc_body(
                 const uint32_t blo = bhi + (uint32_t)(N * kRowBytes);
 #pragma unroll
                 for (int kk = 0; kk < 4; ++kk) {
-                    const uint32_t off = kk * 32;  // 16 elements of 2 bytes
+                    const uint32_t off = kk * 32;  // one K-step: 32 bytes of each row
                     const uint64_t dbh = desc_k_sw128(bhi + off), dbl = desc_k_sw128(blo + off);
 #pragma unroll
                     for (int c = 0; c < 2; ++c) {
                         const uint64_t dah = desc_k_sw128(a0 + (2 * c) * kATile + off);
                         const uint64_t dal = desc_k_sw128(a0 + (2 * c + 1) * kATile + off);
                         const uint32_t d = tmem + 128u * c;
-                        mma_f16(d, dah, dbh, idesc, (s > 0 || kk > 0) ? 1u : 0u);
-                        mma_f16(d, dah, dbl, idesc, 1u);
-                        mma_f16(d, dal, dbh, idesc, 1u);
+                        mma<P>(d, dah, dbh, idesc, (s > 0 || kk > 0) ? 1u : 0u);
+                        mma<P>(d, dah, dbl, idesc, 1u);
+                        mma<P>(d, dal, dbh, idesc, 1u);
                     }
                 }
                 mma_commit(&empty_bar[buf]);
@@ -198,8 +256,8 @@ __device__ __forceinline__ void decode_tc_body(
         __syncwarp();
     } else {
         // ------------------------------------------------------ producers
-        // Fixed per-thread geometry: frequency kk = lane; rows / columns
-        // warp + kWarps q, whose 128-byte swizzle phase (row & 7) is warp & 7.
+        // Fixed per-thread geometry: rows / columns warp + kWarps q, whose
+        // 128-byte swizzle phase (row & 7) is warp & 7.
         float dy[kQ], dx[kQ];
         int tl[kQ];  // tile row of each A row, relative to by0
 #pragma unroll
@@ -211,7 +269,7 @@ __device__ __forceinline__ void decode_tc_body(
         }
         const uint32_t soff = (uint32_t)(warp * kRowBytes +
                                          ((((lane >> 2) ^ (warp & 7)) << 4) | ((lane & 3) << 2)));
-        // The memories of a stage's 32 frequencies for the block's tiles are
+        // The memories of a stage's KS frequencies for the block's tiles are
         // staged (scaled by 1 / norm) in the stage buffer's W area: entry
         // e = (tile row, class, kk), kWPerThread entries per thread.
         int w_mem[kWPerThread];
@@ -219,21 +277,24 @@ __device__ __forceinline__ void decode_tc_body(
 #pragma unroll
         for (int r = 0; r < kWPerThread; ++r) {
             const int e = tid + kProducers * r;
-            const bool ev = e < nt * 2 * kKS;
-            const int mem = 2 * ((by0 + (e >> 6)) * tiles_x + b.tile) + ((e >> 5) & 1);
+            const bool ev = e < nt * 2 * KS;
+            const int mem = 2 * ((by0 + e / (2 * KS)) * tiles_x + b.tile) + ((e / KS) & 1);
             w_mem[r] = ev ? mem : -1;
             w_scale[r] = ev ? inv_norm[mem] * u_scale : 0.f;
         }
-        // prefetch registers: this thread's frequency and staged memory entries
-        float pnx = 0.f, pny = 0.f;
+        // prefetch registers: this lane's frequencies and staged memory entries
+        float pnx[FPL], pny[FPL];
         float2 pw[kWPerThread];
         auto prefetch = [&](int s) {
-            const int k = k_begin + s * kKS + lane;
-            pnx = k < k_end ? nu[k] : 0.f;
-            pny = k < k_end ? nu[D + k] : 0.f;
+#pragma unroll
+            for (int j = 0; j < FPL; ++j) {
+                const int k = k_begin + s * KS + FPL * lane + j;
+                pnx[j] = k < k_end ? nu[k] : 0.f;
+                pny[j] = k < k_end ? nu[D + k] : 0.f;
+            }
 #pragma unroll
             for (int r = 0; r < kWPerThread; ++r) {
-                const int kk = k_begin + s * kKS + ((tid + kProducers * r) & 31);
+                const int kk = k_begin + s * KS + (tid + kProducers * r) % KS;
                 pw[r] = (w_mem[r] >= 0 && kk < k_end) ? omega[(size_t)w_mem[r] * D + kk]
                                                        : make_float2(0.f, 0.f);
             }
@@ -248,11 +309,18 @@ __device__ __forceinline__ void decode_tc_body(
                     sw[tid + kProducers * r] =
                         make_float2(pw[r].x * w_scale[r], pw[r].y * w_scale[r]);
         };
+#pragma unroll
+        for (int j = 0; j < FPL; ++j) pnx[j] = pny[j] = 0.f;
         if (n_stages > 0) {
             prefetch(0);
             stage_w(0);
         }
-        float nux = pnx, nuy = pny;
+        float nux[FPL], nuy[FPL];
+#pragma unroll
+        for (int j = 0; j < FPL; ++j) {
+            nux[j] = pnx[j];
+            nuy[j] = pny[j];
+        }
         named_bar_sync(1, kProducers);
         uint32_t phase_bits = 0u;  // bit b: parity to wait for on empty_bar[b]
         const float step_d = kWarps * res;  // offset between a thread's consecutive rows / columns
@@ -267,22 +335,35 @@ __device__ __forceinline__ void decode_tc_body(
             uint8_t *st = smem + (size_t)buf * stage_bytes;
             uint8_t *bh = st + kAStage, *bl = bh + N * kRowBytes;
             const float2 *sw = reinterpret_cast<const float2 *>(bl + N * kRowBytes);
-            const bool kv = k_begin + s * kKS + lane < k_end;
+            bool kv[FPL];
+#pragma unroll
+            for (int j = 0; j < FPL; ++j) kv[j] = k_begin + s * KS + FPL * lane + j < k_end;
             if (s + 1 < n_stages) prefetch(s + 1);  // in flight while this stage is generated
             // B operand: x phasors of the N columns.  Column warp + 16 (q + 1)
             // is 16 cells right of column warp + 16 q in the same tile, so its
             // phasor is the previous one times exp(i 2 pi nu_x 16 res).
             {
-                const float2 rot = phasor(nux, step_d);
-                float2 a = phasor(nux, dx[0]);
+                float2 rot[FPL], a[FPL];
+#pragma unroll
+                for (int j = 0; j < FPL; ++j) {
+                    rot[j] = phasor(nux[j], step_d);
+                    a[j] = phasor(nux[j], dx[0]);
+                }
 #pragma unroll
                 for (int q = 0; q < kQ; ++q) {
                     const int n = warp + kWarps * q;
                     if (n >= N) break;
-                    if (q > 0) a = cmul(a, rot);
-                    const float2 v = (kv && n < ni) ? a : make_float2(0.f, 0.f);
+                    float2 v[FPL];
+#pragma unroll
+                    for (int j = 0; j < FPL; ++j) {
+                        if (q > 0) a[j] = cmul(a[j], rot[j]);
+                        v[j] = (kv[j] && n < ni) ? a[j] : make_float2(0.f, 0.f);
+                    }
                     uint32_t hi, lo;
-                    split2<BF16>(v.x, v.y, hi, lo);
+                    if (FPL == 1)
+                        split_pair<P>(v[0].x, v[0].y, hi, lo);
+                    else
+                        split_quad_e4m3(v[0].x, v[0].y, v[FPL - 1].x, v[FPL - 1].y, hi, lo);
                     *reinterpret_cast<uint32_t *>(bh + q * kWarps * kRowBytes + soff) = hi;
                     *reinterpret_cast<uint32_t *>(bl + q * kWarps * kRowBytes + soff) = lo;
                 }
@@ -292,30 +373,54 @@ __device__ __forceinline__ void decode_tc_body(
             // the next tile (warp-uniform): there the phasor and the memories
             // are reloaded.
             {
-                const float2 rot = phasor(nuy, step_d);
-                float2 e = phasor(nuy, dy[0]);
-                float2 w0 = sw[(2 * tl[0]) * kKS + lane], w1 = sw[(2 * tl[0] + 1) * kKS + lane];
+                float2 rot[FPL], e[FPL], w0[FPL], w1[FPL];
+                auto load_w = [&](int t) {
+#pragma unroll
+                    for (int j = 0; j < FPL; ++j) {
+                        w0[j] = sw[(2 * t) * KS + FPL * lane + j];
+                        w1[j] = sw[(2 * t + 1) * KS + FPL * lane + j];
+                    }
+                };
+#pragma unroll
+                for (int j = 0; j < FPL; ++j) {
+                    rot[j] = phasor(nuy[j], step_d);
+                    e[j] = phasor(nuy[j], dy[0]);
+                }
+                load_w(tl[0]);
 #pragma unroll
                 for (int q = 0; q < kQ; ++q) {
                     const int m = warp + kWarps * q;
                     if (q > 0) {
                         if (tl[q] != tl[q - 1]) {
-                            e = phasor(nuy, dy[q]);
-                            w0 = sw[(2 * tl[q]) * kKS + lane];
-                            w1 = sw[(2 * tl[q] + 1) * kKS + lane];
+#pragma unroll
+                            for (int j = 0; j < FPL; ++j) e[j] = phasor(nuy[j], dy[q]);
+                            load_w(tl[q]);
                         } else {
-                            e = cmul(e, rot);
+#pragma unroll
+                            for (int j = 0; j < FPL; ++j) e[j] = cmul(e[j], rot[j]);
                         }
                     }
-                    const float2 v = (kv && m < nj) ? e : make_float2(0.f, 0.f);
-                    float u0r = w0.x * v.x + w0.y * v.y, u0i = w0.x * v.y - w0.y * v.x;
-                    float u1r = w1.x * v.x + w1.y * v.y, u1i = w1.x * v.y - w1.y * v.x;
+                    float u0r[FPL], u0i[FPL], u1r[FPL], u1i[FPL];
+#pragma unroll
+                    for (int j = 0; j < FPL; ++j) {
+                        const float2 v = (kv[j] && m < nj) ? e[j] : make_float2(0.f, 0.f);
+                        u0r[j] = w0[j].x * v.x + w0[j].y * v.y;
+                        u0i[j] = w0[j].x * v.y - w0[j].y * v.x;
+                        u1r[j] = w1[j].x * v.x + w1[j].y * v.y;
+                        u1i[j] = w1[j].x * v.y - w1[j].y * v.x;
+                    }
                     const uint32_t o = q * kWarps * kRowBytes + soff;
                     uint32_t hi, lo;
-                    split2<BF16>(u0r, -u0i, hi, lo);
+                    if (FPL == 1)
+                        split_pair<P>(u0r[0], -u0i[0], hi, lo);
+                    else
+                        split_quad_e4m3(u0r[0], -u0i[0], u0r[FPL - 1], -u0i[FPL - 1], hi, lo);
                     *reinterpret_cast<uint32_t *>(st + 0 * kATile + o) = hi;
                     *reinterpret_cast<uint32_t *>(st + 1 * kATile + o) = lo;
-                    split2<BF16>(u1r, -u1i, hi, lo);
+                    if (FPL == 1)
+                        split_pair<P>(u1r[0], -u1i[0], hi, lo);
+                    else
+                        split_quad_e4m3(u1r[0], -u1i[0], u1r[FPL - 1], -u1i[FPL - 1], hi, lo);
                     *reinterpret_cast<uint32_t *>(st + 2 * kATile + o) = hi;
                     *reinterpret_cast<uint32_t *>(st + 3 * kATile + o) = lo;
                 }
@@ -328,14 +433,17 @@ __device__ __forceinline__ void decode_tc_body(
             // readers finished before the previous producer barrier)
             if (s + 1 < n_stages) {
                 stage_w(s + 1);
-                nux = pnx;
-                nuy = pny;
+#pragma unroll
+                for (int j = 0; j < FPL; ++j) {
+                    nux[j] = pnx[j];
+                    nuy[j] = pny[j];
+                }
             }
             named_bar_sync(1, kProducers);
         }
     }
     // epilogue (producers): warp w reads TMEM lanes 32 (w & 3) .. + 31 (its lane
-    // quarter), class (w >> 2) & 1, and one half of the 16-column chunks (w >> 3)
+    // quarter), class (w >> 2) & 1, and one half of the 16-column chunks (w >> 3);
     // always drain (bounded), even after a time-out: tensor memory is freed below
     if (!mbar_wait(&done_bar, 0u, kWaitNs)) atomicExch(&abort_s, 1);
     tc_fence_after_sync();
@@ -369,33 +477,53 @@ __device__ __forceinline__ void decode_tc_body(
     if (warp == 0) tmem_dealloc(tmem, kTmemCols);
 }
 
-template <bool BF16>
+template <int P>
 __global__ void __launch_bounds__(kThreads, 1) decode_tc_kernel(
     const BlockBatch blocks, const float2 *__restrict__ omega, const float *__restrict__ inv_norm,
     const float *__restrict__ nu, int D, int tiles_x, const int *__restrict__ row_tile, OutGeom og,
     const float *__restrict__ col_off, const float *__restrict__ row_off, float res,
     int k_per_split, int N, float u_scale, float *__restrict__ partial, int *__restrict__ status)
 {
-    decode_tc_body<BF16>(blocks.b[blockIdx.x], blockIdx.y, omega, inv_norm, nu, D, tiles_x,
-                         row_tile, og, col_off, row_off, res, k_per_split, N, u_scale, partial,
-                         status);
+    decode_tc_body<P>(blocks.b[blockIdx.x], blockIdx.y, omega, inv_norm, nu, D, tiles_x, row_tile,
+                      og, col_off, row_off, res, k_per_split, N, u_scale, partial, status);
 }
 
 // Many maps in one launch: CTA q decodes item q of a device list of
 // (map, block, slice); each map's pointers come from the table.
-template <bool BF16>
+template <int P>
 __global__ void __launch_bounds__(kThreads, 1) decode_tc_batch_kernel(
     const __grid_constant__ BatchDecodeTable tab, const BatchDecodeItem *__restrict__ items)
 {
     const BatchDecodeItem it = items[blockIdx.x];
     const BatchDecodeMap &M = tab.m[it.map];
     const int N = ((it.b.i1 - it.b.i0) + 15) / 16 * 16;
-    decode_tc_body<BF16>(it.b, it.split, M.omega, M.inv_norm, M.nu, M.D, M.tiles_x, M.row_tile,
-                         OutGeom{0, 0, M.W, M.H}, M.col_off, M.row_off, M.res,
-                         M.k_per_split, N, M.u_scale, M.partial, M.status);
+    decode_tc_body<P>(it.b, it.split, M.omega, M.inv_norm, M.nu, M.D, M.tiles_x, M.row_tile,
+                      OutGeom{0, 0, M.W, M.H}, M.col_off, M.row_off, M.res, M.k_per_split, N,
+                      M.u_scale, M.partial, M.status);
+}
+
+int prec_of(int decode_prec)
+{
+    return decode_prec == VSAOGM_DECODE_FP8X3   ? kPrecFP8
+           : decode_prec == VSAOGM_DECODE_FP16X3 ? kPrecFP16
+                                                 : kPrecBF16;
+}
+
+template <int P>
+cudaError_t set_smem_attributes()
+{
+    cudaError_t e = cudaFuncSetAttribute(decode_tc_kernel<P>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem_max(P));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(decode_tc_batch_kernel<P>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max(P));
+    return e;
 }
 
 }  // namespace
+
+int tc_stage_freqs(int decode_prec) { return stage_freqs(prec_of(decode_prec)); }
 
 // Blocks of at most 128 x 128 cells covering region r for the tensor-core
 // decode: columns inside one tile column, rows across at most kMaxBlockTiles
@@ -426,28 +554,31 @@ void tc_blocks(const vsaogm_map *m, Region r, std::vector<DecodeBlock> &out)
 }
 
 int launch_decode_tc_batch(const BatchDecodeTable &tab, const BatchDecodeItem *items,
-                           int n_items, bool bf16, cudaStream_t st)
+                           int n_items, int decode_prec, cudaStream_t st)
 {
-    cudaError_t e;
-    if (bf16) {
-        e = cudaFuncSetAttribute(decode_tc_batch_kernel<true>,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemMax);
-        if (e == cudaSuccess)
-            decode_tc_batch_kernel<true><<<n_items, kThreads, kSmemMax, st>>>(tab, items);
-    } else {
-        e = cudaFuncSetAttribute(decode_tc_batch_kernel<false>,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemMax);
-        if (e == cudaSuccess)
-            decode_tc_batch_kernel<false><<<n_items, kThreads, kSmemMax, st>>>(tab, items);
+    const int P = prec_of(decode_prec);
+    cudaError_t e = P == kPrecFP8    ? set_smem_attributes<kPrecFP8>()
+                    : P == kPrecFP16 ? set_smem_attributes<kPrecFP16>()
+                                     : set_smem_attributes<kPrecBF16>();
+    if (e == cudaSuccess) {
+        const size_t smem = smem_max(P);
+        if (P == kPrecFP8)
+            decode_tc_batch_kernel<kPrecFP8><<<n_items, kThreads, smem, st>>>(tab, items);
+        else if (P == kPrecFP16)
+            decode_tc_batch_kernel<kPrecFP16><<<n_items, kThreads, smem, st>>>(tab, items);
+        else
+            decode_tc_batch_kernel<kPrecBF16><<<n_items, kThreads, smem, st>>>(tab, items);
+        e = cudaGetLastError();
     }
-    if (e == cudaSuccess) e = cudaGetLastError();
     return e == cudaSuccess ? VSAOGM_OK : cuda_error(e, "batch decode");
 }
 
+// Power-of-two scale of U for the FP16 and FP8 operands (U = conj(w_hat) x
+// phasor has |U_k| ~ 1 / sqrt(D)): u with 4 u^2 <= D, undone by the slice sum.
 float tc_u_scale(const vsaogm_map *m)
 {
     float u = 1.f;
-    if (m->cfg.decode_prec == VSAOGM_DECODE_FP16X3)
+    if (m->cfg.decode_prec == VSAOGM_DECODE_FP16X3 || m->cfg.decode_prec == VSAOGM_DECODE_FP8X3)
         while (u * u * 4.f <= (float)m->cfg.D) u *= 2.f;
     return u;
 }
@@ -455,26 +586,24 @@ float tc_u_scale(const vsaogm_map *m)
 int decode_tensor_cores(vsaogm_map *m, Region r, float *heat, cudaStream_t st)
 {
     const int D = m->cfg.D;
-    const bool bf16 = m->cfg.decode_prec == VSAOGM_DECODE_BF16X3;
+    const int P = prec_of(m->cfg.decode_prec);
+    const int KS = stage_freqs(P);
     std::vector<DecodeBlock> blocks;
     tc_blocks(m, r, blocks);
     const int nb = (int)blocks.size();
     // slices of the frequencies so that blocks x slices fills the 152 SMs once,
     // and no slice longer than kTcMaxKPerSplit
     int splits = std::max((D + kTcMaxKPerSplit - 1) / kTcMaxKPerSplit,
-                          std::min((D + kKS - 1) / kKS, 152 / std::max(nb, 1)));
-    int kps = ((D + splits - 1) / splits + kKS - 1) / kKS * kKS;
+                          std::min((D + KS - 1) / KS, 152 / std::max(nb, 1)));
+    int kps = ((D + splits - 1) / splits + KS - 1) / KS * KS;
     splits = (D + kps - 1) / kps;
     const size_t cells = (size_t)r.w() * r.h();
     int rc = ensure(m->ws.dec_partial, sizeof(float) * (size_t)splits * 2 * cells);
     if (rc) return rc;
     const float u_scale = tc_u_scale(m);
-    cudaError_t e = bf16 ? cudaFuncSetAttribute(decode_tc_kernel<true>,
-                                                cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                (int)kSmemMax)
-                         : cudaFuncSetAttribute(decode_tc_kernel<false>,
-                                                cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                (int)kSmemMax);
+    cudaError_t e = P == kPrecFP8    ? set_smem_attributes<kPrecFP8>()
+                    : P == kPrecFP16 ? set_smem_attributes<kPrecFP16>()
+                                     : set_smem_attributes<kPrecBF16>();
     if (e != cudaSuccess) return cuda_error(e, "decode: tensor cores");
     StageScope sc(m, VSAOGM_STAGE_DECODE, st);
     float *part = (float *)m->ws.dec_partial.ptr;
@@ -489,16 +618,19 @@ int decode_tensor_cores(vsaogm_map *m, Region r, float *heat, cudaStream_t st)
             widest = std::max(widest, batch.b[q].i1 - batch.b[q].i0);
         }
         const int N = (widest + 15) / 16 * 16;  // MMA N: the widest block, multiple of 16
-        const size_t smem = 1024 + 2 * (size_t)stage_size(N);
+        const size_t smem = 1024 + 2 * (size_t)stage_size(P, N);
         dim3 grid(batch.n, splits);
-        if (bf16)
-            decode_tc_kernel<true><<<grid, kThreads, smem, st>>>(
-                batch, m->omega, m->inv_norm, m->nu, D, m->cfg.tiles_x, m->row_tile, og,
-                m->col_off, m->row_off, m->cfg.resolution, kps, N, u_scale, part, m->status);
+#define VSAOGM_LAUNCH_TC(PP)                                                                   \
+    decode_tc_kernel<PP><<<grid, kThreads, smem, st>>>(                                        \
+        batch, m->omega, m->inv_norm, m->nu, D, m->cfg.tiles_x, m->row_tile, og, m->col_off,    \
+        m->row_off, m->cfg.resolution, kps, N, u_scale, part, m->status)
+        if (P == kPrecFP8)
+            VSAOGM_LAUNCH_TC(kPrecFP8);
+        else if (P == kPrecFP16)
+            VSAOGM_LAUNCH_TC(kPrecFP16);
         else
-            decode_tc_kernel<false><<<grid, kThreads, smem, st>>>(
-                batch, m->omega, m->inv_norm, m->nu, D, m->cfg.tiles_x, m->row_tile, og,
-                m->col_off, m->row_off, m->cfg.resolution, kps, N, u_scale, part, m->status);
+            VSAOGM_LAUNCH_TC(kPrecBF16);
+#undef VSAOGM_LAUNCH_TC
         ++launches;
     }
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_error(e, "decode: tensor cores");

@@ -274,7 +274,9 @@ int launch_reduce_batch(const BatchReduceTable &tab, int d_max, cudaStream_t st)
 int launch_norms_batch(const BatchNormTable &tab, int total_memories, cudaStream_t st);
 int launch_sums_batch(const BatchOutTable &tab, size_t max_cells, cudaStream_t st);
 int launch_decode_tc_batch(const BatchDecodeTable &tab, const BatchDecodeItem *items,
-                           int n_items, bool bf16, cudaStream_t st);
+                           int n_items, int decode_prec, cudaStream_t st);
+// frequencies per tensor-core stage for a decode_prec (slices are multiples of it)
+int tc_stage_freqs(int decode_prec);
 int launch_entropy_batch(const BatchOutTable &tab, cudaStream_t st);
 float tc_u_scale(const vsaogm_map *m);
 

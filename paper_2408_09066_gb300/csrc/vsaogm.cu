@@ -174,7 +174,7 @@ int validate(const vsaogm_config *c)
         return set_error(VSAOGM_E_INVAL, "disk radii must be in [0, %d]", kMaxRadius);
     if (!std::isfinite(c->rho)) return set_error(VSAOGM_E_INVAL, "rho must be finite");
     if (c->decode_prec != VSAOGM_DECODE_FP32 && c->decode_prec != VSAOGM_DECODE_BF16X3 &&
-        c->decode_prec != VSAOGM_DECODE_FP16X3)
+        c->decode_prec != VSAOGM_DECODE_FP16X3 && c->decode_prec != VSAOGM_DECODE_FP8X3)
         return set_error(VSAOGM_E_INVAL, "unknown decode_prec %d", c->decode_prec);
     if (c->flags & ~(VSAOGM_FLAG_CHECKED | VSAOGM_FLAG_ATOMIC))
         return set_error(VSAOGM_E_INVAL, "unknown flags 0x%x", c->flags);

@@ -24,7 +24,10 @@ TOL_OMEGA, TOL_P, TOL_PR = 3e-5, 1e-4, 1e-3
 # product), so they can differ by a few 1e-5 (6.3e-5 seen on a 423^2-cell
 # D = 8192 map); both stay inside TOL_P of the oracle
 TOL_SELF_P, TOL_SELF_PR = TOL_P, TOL_PR
-PRECS = [V.DECODE_BF16X3, V.DECODE_FP16X3]
+PRECS = [V.DECODE_BF16X3, V.DECODE_FP16X3, V.DECODE_FP8X3]
+# raw maps P of the FP8 split (about 8 significant bits per operand value: held
+# to the P_hat bound, see the tensor-core decode tests for the derivation)
+TOL_P_PREC = {V.DECODE_BF16X3: 1e-4, V.DECODE_FP16X3: 1e-4, V.DECODE_FP8X3: 1e-2}
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -87,9 +90,9 @@ def _omega_c(got):
     return o[..., 0] + 1j * o[..., 1]
 
 
-def _check(got, want, what=""):
+def _check(got, want, what="", tol_p=TOL_P):
     assert normwise(_omega_c(got["omega"]), want["omega"]) <= TOL_OMEGA, what
-    assert normwise(got["P"], want["P"]) <= TOL_P, what
+    assert normwise(got["P"], want["P"]) <= tol_p, what
     assert np.abs(got["occ"] - want["pr1"]).max() <= TOL_PR, what
     assert np.abs(got["ogm"] - want["ogm"]).max() <= 2 * TOL_PR, what
 
@@ -101,7 +104,7 @@ def test_batch_matches_oracle(prec):
     try:
         r.batch.step(r.xy, r.lab, r.heat, r.occ, r.ogm)
         for w, cfg, got in zip(r.wls, r.cfgs, r.host()):
-            _check(got, _oracle(cfg, w.xy, w.labels), w.name)
+            _check(got, _oracle(cfg, w.xy, w.labels), w.name, TOL_P_PREC[prec])
     finally:
         r.close()
 
