@@ -50,14 +50,42 @@ __device__ __forceinline__ int tile_along(const float *bnd, int nb, float x)
     return lo;
 }
 
-// Segment 2 beta + psi, or S for a point that is rejected.
+// Segment (2 beta + psi) pt.n + patch, or S for a point that is rejected.
+// The patch is the one containing the point's offset from its tile centre
+// (clamped to the tile's edge patches; any deterministic rule would do, since
+// a patch only groups points for summation).
 __device__ __forceinline__ int point_segment(float x, float y, unsigned lab, const AxisDev &ax,
-                                             const AxisDev &ay, int S)
+                                             const AxisDev &ay, const PatchDev &pt, int S)
 {
     if (lab > 1u || !isfinite(x) || !isfinite(y)) return S;
     int bx = tile_along(ax.bnd_lo, ax.n_tiles - 1, x);
     int by = tile_along(ay.bnd_lo, ay.n_tiles - 1, y);
-    return 2 * (by * ax.n_tiles + bx) + (int)lab;
+    const int mem = 2 * (by * ax.n_tiles + bx) + (int)lab;
+    if (pt.n == 1) return mem;
+    const float ux = (x - (float)ax.centre[bx] + pt.hw_x) * pt.inv_pw_x;
+    const float uy = (y - (float)ay.centre[by] + pt.hw_y) * pt.inv_pw_y;
+    const int px = (int)floorf(fminf(fmaxf(ux, 0.f), (float)(pt.nx - 1)));
+    const int py = (int)floorf(fminf(fmaxf(uy, 0.f), (float)(pt.ny - 1)));
+    return mem * pt.n + py * pt.nx + px;
+}
+
+// Multiplies (re, im) by exp(i 2 pi (nu_x cx + nu_y cy)): the phasor that turns a
+// partial memory summed relative to a patch centre (cx, cy) into the tile's
+// frame.  The phase is reduced exactly (each product against its own nearest
+// integer with one FMA, as in the exact point reduction).
+__device__ __forceinline__ void patch_rotate(float nux, float nuy, float cx, float cy, float &re,
+                                             float &im)
+{
+    const float kM = 12582912.0f;
+    const float p1 = __fmul_rn(nux, cx), p2 = __fmul_rn(nuy, cy);
+    const float n1 = __fsub_rn(kM, __fadd_rn(p1, kM)), n2 = __fsub_rn(kM, __fadd_rn(p2, kM));
+    const float g = __fadd_rn(fmaf(nux, cx, n1), fmaf(nuy, cy, n2));
+    const float f = __fsub_rn(g, __fsub_rn(__fadd_rn(g, kM), kM));
+    float sn, cs;
+    __sincosf(__fmul_rn(f, 6.28318530717958647692f), &sn, &cs);
+    const float r = re * cs - im * sn;
+    im = re * sn + im * cs;
+    re = r;
 }
 
 // Block-wide exclusive scan of v over kScanThreads threads; returns the prefix
@@ -91,8 +119,8 @@ __device__ int block_exclusive_scan(int v, int *total)
 // 1. Per-block histogram over segments 0..S (S = rejected).
 __global__ void __launch_bounds__(256) seg_count_kernel(const float2 *__restrict__ xy,
                                                         const uint8_t *__restrict__ lab, int n,
-                                                        AxisDev ax, AxisDev ay, int S,
-                                                        int *__restrict__ hist)
+                                                        AxisDev ax, AxisDev ay, PatchDev pt,
+                                                        int S, int *__restrict__ hist)
 {
     extern __shared__ int cnt[];  // [S + 1]
     const int S1 = S + 1;
@@ -105,7 +133,7 @@ __global__ void __launch_bounds__(256) seg_count_kernel(const float2 *__restrict
         int seg = -1;
         if (i < n) {
             float2 p = xy[i];
-            seg = point_segment(p.x, p.y, lab[i], ax, ay, S);
+            seg = point_segment(p.x, p.y, lab[i], ax, ay, pt, S);
         }
         unsigned peers = __match_any_sync(0xffffffffu, seg);
         if (seg >= 0 && lane == __ffs(peers) - 1) atomicAdd(&cnt[seg], __popc(peers));
@@ -178,8 +206,8 @@ __global__ void __launch_bounds__(kScanThreads) seg_meta_kernel(int *__restrict_
 // 4. Stable scatter into segment order, tile-centred coordinates.
 __global__ void __launch_bounds__(256) seg_scatter_kernel(const float2 *__restrict__ xy,
                                                           const uint8_t *__restrict__ lab, int n,
-                                                          AxisDev ax, AxisDev ay, int S,
-                                                          const int *__restrict__ blk_off,
+                                                          AxisDev ax, AxisDev ay, PatchDev pt,
+                                                          int S, const int *__restrict__ blk_off,
                                                           const int *__restrict__ meta,
                                                           float2 *__restrict__ sorted)
 {
@@ -198,7 +226,7 @@ __global__ void __launch_bounds__(256) seg_scatter_kernel(const float2 *__restri
         int seg = -1;
         if (i < n) {
             float2 p = xy[i];
-            seg = point_segment(p.x, p.y, lab[i], ax, ay, S);
+            seg = point_segment(p.x, p.y, lab[i], ax, ay, pt, S);
         }
         unsigned peers = __match_any_sync(0xffffffffu, seg);
         if (seg >= 0 && lane == __ffs(peers) - 1) mine[seg] += __popc(peers);
@@ -223,7 +251,7 @@ __global__ void __launch_bounds__(256) seg_scatter_kernel(const float2 *__restri
         float2 p = make_float2(0.f, 0.f);
         if (i < n) {
             p = xy[i];
-            seg = point_segment(p.x, p.y, lab[i], ax, ay, S);
+            seg = point_segment(p.x, p.y, lab[i], ax, ay, pt, S);
         }
         unsigned peers = __match_any_sync(0xffffffffu, seg);
         int dst = 0;
@@ -232,11 +260,14 @@ __global__ void __launch_bounds__(256) seg_scatter_kernel(const float2 *__restri
         if (seg >= 0 && lane == __ffs(peers) - 1) mine[seg] += __popc(peers);
         __syncwarp();
         if (seg >= 0 && seg < S) {
-            int beta = seg >> 1;
-            int bx = beta % ax.n_tiles, by = beta / ax.n_tiles;
-            // FP64 once per point: the offset from the tile centre, then f32.
-            float dx = (float)((double)p.x - ax.centre[bx]);
-            float dy = (float)((double)p.y - ay.centre[by]);
+            const int mem = seg / pt.n, patch = seg - mem * pt.n;
+            const int beta = mem >> 1;
+            const int bx = beta % ax.n_tiles, by = beta / ax.n_tiles;
+            // FP64 once per point: the offset from the tile (or patch) centre, then f32.
+            const double cx = pt.n > 1 ? (double)pt.cx[patch % pt.nx] : 0.0;
+            const double cy = pt.n > 1 ? (double)pt.cy[patch / pt.nx] : 0.0;
+            float dx = (float)((double)p.x - ax.centre[bx] - cx);
+            float dy = (float)((double)p.y - ay.centre[by] - cy);
             sorted[dst] = make_float2(dx, dy);
         }
     }
@@ -298,7 +329,7 @@ __global__ void __launch_bounds__(256) encode_chunk_kernel(const float2 *__restr
                                                            const int *__restrict__ n_chunks,
                                                            const float *__restrict__ nu, int D,
                                                            float nu_max_x, float nu_max_y,
-                                                           float2 *__restrict__ out)
+                                                           PatchDev pt, float2 *__restrict__ out)
 {
     __shared__ float2 sp[kMaxChunk];
     __shared__ unsigned s_bound[2];
@@ -341,12 +372,18 @@ __global__ void __launch_bounds__(256) encode_chunk_kernel(const float2 *__restr
         encode_points<KPT, false>(sp, len, nx, ny, ar, ai);
     else
         encode_points<KPT, true>(sp, len, nx, ny, ar, ai);
+    const int mem = ch.x / pt.n, patch = ch.x - mem * pt.n;
+    if (pt.n > 1) {
+        const float cx = pt.cx[patch % pt.nx], cy = pt.cy[patch / pt.nx];
+#pragma unroll
+        for (int j = 0; j < KPT; ++j) patch_rotate(nx[j], ny[j], cx, cy, ar[j], ai[j]);
+    }
 #pragma unroll
     for (int j = 0; j < KPT; ++j) {
         int k = kbase + j * 256;
         if (k < D) {
             if (ATOMIC) {
-                float2 *w = out + (size_t)ch.x * D + k;
+                float2 *w = out + (size_t)mem * D + k;
                 atomicAdd(&w->x, ar[j]);
                 atomicAdd(&w->y, ai[j]);
             } else {
@@ -448,8 +485,9 @@ __device__ __forceinline__ void encode_chunk_x2_body(const float2 *__restrict__ 
                                                      int c, int slice,
                                                      const float *__restrict__ nu, int D,
                                                      float nu_max_x, float nu_max_y,
-                                                     int poly_warps, float2 *__restrict__ out,
-                                                     float2 *sp, unsigned *s_bound)
+                                                     int poly_warps, const PatchDev &pt,
+                                                     float2 *__restrict__ out, float2 *sp,
+                                                     unsigned *s_bound)
 {
     using namespace sm100;
     const int len = ch.z - ch.y;
@@ -498,16 +536,21 @@ __device__ __forceinline__ void encode_chunk_x2_body(const float2 *__restrict__ 
     } else {
         encode_points_x2<NP, 0, false>(sp, len, nx, ny, ac, as);
     }
+    const int mem = ch.x / pt.n, patch = ch.x - mem * pt.n;
+    const float pcx = pt.n > 1 ? pt.cx[patch % pt.nx] : 0.f;
+    const float pcy = pt.n > 1 ? pt.cy[patch / pt.nx] : 0.f;
 #pragma unroll
     for (int j = 0; j < NP; ++j) {
         const float2 cr = unpack2(ac[j]), si = unpack2(as[j]);
+        const float2 vx = unpack2(nx[j]), vy = unpack2(ny[j]);
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
             int k = kbase + (2 * j + h) * 256;
             float re = h ? cr.y : cr.x, im = h ? si.y : si.x;
+            if (pt.n > 1) patch_rotate(h ? vx.y : vx.x, h ? vy.y : vy.x, pcx, pcy, re, im);
             if (k < D) {
                 if (ATOMIC) {
-                    float2 *w = out + (size_t)ch.x * D + k;
+                    float2 *w = out + (size_t)mem * D + k;
                     atomicAdd(&w->x, re);
                     atomicAdd(&w->y, im);
                 } else {
@@ -524,7 +567,7 @@ __global__ void __launch_bounds__(256) encode_chunk_x2_kernel(const float2 *__re
                                                               const int *__restrict__ n_chunks,
                                                               const float *__restrict__ nu, int D,
                                                               float nu_max_x, float nu_max_y,
-                                                              int poly_warps,
+                                                              int poly_warps, PatchDev pt,
                                                               float2 *__restrict__ out)
 {
     __shared__ float2 sp[kMaxChunk];
@@ -532,7 +575,7 @@ __global__ void __launch_bounds__(256) encode_chunk_x2_kernel(const float2 *__re
     const int c = blockIdx.x;
     if (c >= *n_chunks) return;
     encode_chunk_x2_body<NP, NPOLY, ATOMIC>(pts, chunks[c], c, blockIdx.y, nu, D, nu_max_x,
-                                            nu_max_y, poly_warps, out, sp, s_bound);
+                                            nu_max_y, poly_warps, pt, out, sp, s_bound);
 }
 
 // 5''. Many maps in one persistent launch.  Work items are (map, chunk,
@@ -561,8 +604,8 @@ __global__ void __launch_bounds__(256) encode_batch_kernel(const __grid_constant
         const int c = (int)(local / M.slices), slice = (int)(local % M.slices);
         if (c < *M.n_chunks)
             encode_chunk_x2_body<4, -1, false>(M.pts, M.chunks[c], c, slice, M.nu, M.D,
-                                               M.nu_max_x, M.nu_max_y, tab.poly_warps, M.out, sp,
-                                               s_bound);
+                                               M.nu_max_x, M.nu_max_y, tab.poly_warps, M.pt,
+                                               M.out, sp, s_bound);
         __syncthreads();  // the staging buffers are reused by the next item
     }
 }
@@ -579,10 +622,10 @@ __global__ void __launch_bounds__(256) reduce_batch_kernel(const __grid_constant
         if (tab.m[mid].seg_begin <= gs) lo = mid; else hi = mid - 1;
     }
     const BatchReduceMap &M = tab.m[lo];
-    const int s = gs - M.seg_begin;
+    const int s = gs - M.seg_begin;  // memory of this map; its patches' chunks are contiguous
     const int k = blockIdx.y * blockDim.x + threadIdx.x;
     if (k >= M.D) return;
-    const int c0 = M.cbeg[s], c1 = M.cbeg[s + 1];
+    const int c0 = M.cbeg[s * M.patches], c1 = M.cbeg[(s + 1) * M.patches];
     if (c0 == c1) return;
     float sr = 0.f, si = 0.f;
     for (int c = c0; c < c1; ++c) {
@@ -594,15 +637,17 @@ __global__ void __launch_bounds__(256) reduce_batch_kernel(const __grid_constant
     M.omega[(size_t)s * M.D + k] = make_float2(w.x + sr, w.y + si);
 }
 
-// 6. omega[s][k] += sum of the partial memories of segment s, in chunk order.
+// 6. omega[s][k] += sum of the partial memories of memory s (the chunks of its
+//    `patches` segments, which are contiguous), in chunk order.
 __global__ void __launch_bounds__(256) reduce_partials_kernel(const float2 *__restrict__ partial,
                                                               const int *__restrict__ cbeg, int D,
+                                                              int patches,
                                                               float2 *__restrict__ omega)
 {
     const int s = blockIdx.y;
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= D) return;
-    const int c0 = cbeg[s], c1 = cbeg[s + 1];
+    const int c0 = cbeg[s * patches], c1 = cbeg[(s + 1) * patches];
     if (c0 == c1) return;
     float sr = 0.f, si = 0.f;
     for (int c = c0; c < c1; ++c) {
@@ -621,35 +666,35 @@ constexpr int kAutoPolyWarps4 = 6;  // 4 pairs per thread: 6/32 of the exponenti
 constexpr int kAutoPolyWarps2 = 3;  // 2 pairs per thread: 3/16
 
 template <int NP, int NPOLY>
-cudaError_t launch_x2(const vsaogm_map *m, const float2 *pts, const int4 *chunks,
-                      const int *n_chunks, float2 *out, int max_chunks, bool atomic,
-                      int pw, cudaStream_t st)
+cudaError_t launch_x2(const vsaogm_map *m, const PatchDev &pt, const float2 *pts,
+                      const int4 *chunks, const int *n_chunks, float2 *out, int max_chunks,
+                      bool atomic, int pw, cudaStream_t st)
 {
     const int D = m->cfg.D;
     dim3 grid(max_chunks, (D + 512 * NP - 1) / (512 * NP));
     if (atomic)
         encode_chunk_x2_kernel<NP, NPOLY, true><<<grid, 256, 0, st>>>(
-            pts, chunks, n_chunks, m->nu, D, m->nu_max[0], m->nu_max[1], pw, out);
+            pts, chunks, n_chunks, m->nu, D, m->nu_max[0], m->nu_max[1], pw, pt, out);
     else
         encode_chunk_x2_kernel<NP, NPOLY, false><<<grid, 256, 0, st>>>(
-            pts, chunks, n_chunks, m->nu, D, m->nu_max[0], m->nu_max[1], pw, out);
+            pts, chunks, n_chunks, m->nu, D, m->nu_max[0], m->nu_max[1], pw, pt, out);
     return cudaGetLastError();
 }
 
-cudaError_t launch_packed(const vsaogm_map *m, int np, const float2 *pts, const int4 *chunks,
-                          const int *n_chunks, float2 *out, int max_chunks, bool atomic,
-                          cudaStream_t st)
+cudaError_t launch_packed(const vsaogm_map *m, const PatchDev &pt, int np, const float2 *pts,
+                          const int4 *chunks, const int *n_chunks, float2 *out, int max_chunks,
+                          bool atomic, cudaStream_t st)
 {
     const int npoly = std::min(m->encode_poly_pairs, np);
     const int pw = m->encode_poly_warps >= 0 ? m->encode_poly_warps
                                              : (np == 4 ? kAutoPolyWarps4 : kAutoPolyWarps2);
     if (npoly == 0 && pw > 0) {  // mixed: some warps with one polynomial pair
         if (np == 4)
-            return launch_x2<4, -1>(m, pts, chunks, n_chunks, out, max_chunks, atomic, pw, st);
-        return launch_x2<2, -1>(m, pts, chunks, n_chunks, out, max_chunks, atomic, pw, st);
+            return launch_x2<4, -1>(m, pt, pts, chunks, n_chunks, out, max_chunks, atomic, pw, st);
+        return launch_x2<2, -1>(m, pt, pts, chunks, n_chunks, out, max_chunks, atomic, pw, st);
     }
 #define VSA_X2(NPV, NPOLYV) \
-    launch_x2<NPV, NPOLYV>(m, pts, chunks, n_chunks, out, max_chunks, atomic, 0, st)
+    launch_x2<NPV, NPOLYV>(m, pt, pts, chunks, n_chunks, out, max_chunks, atomic, 0, st)
     if (np == 4) {
         switch (npoly) {
             case 0: return VSA_X2(4, 0);
@@ -667,19 +712,30 @@ cudaError_t launch_packed(const vsaogm_map *m, int np, const float2 *pts, const 
 }
 
 template <int KPT>
-cudaError_t launch_encode(const vsaogm_map *m, const float2 *pts, const int4 *chunks,
-                          const int *n_chunks, float2 *out, int max_chunks, bool atomic,
-                          cudaStream_t st)
+cudaError_t launch_encode(const vsaogm_map *m, const PatchDev &pt, const float2 *pts,
+                          const int4 *chunks, const int *n_chunks, float2 *out, int max_chunks,
+                          bool atomic, cudaStream_t st)
 {
     const int D = m->cfg.D;
     dim3 grid(max_chunks, (D + 256 * KPT - 1) / (256 * KPT));
     if (atomic)
-        encode_chunk_kernel<KPT, true><<<grid, 256, 0, st>>>(pts, chunks, n_chunks, m->nu, D,
-                                                             m->nu_max[0], m->nu_max[1], out);
+        encode_chunk_kernel<KPT, true><<<grid, 256, 0, st>>>(
+            pts, chunks, n_chunks, m->nu, D, m->nu_max[0], m->nu_max[1], pt, out);
     else
-        encode_chunk_kernel<KPT, false><<<grid, 256, 0, st>>>(pts, chunks, n_chunks, m->nu, D,
-                                                              m->nu_max[0], m->nu_max[1], out);
+        encode_chunk_kernel<KPT, false><<<grid, 256, 0, st>>>(
+            pts, chunks, n_chunks, m->nu, D, m->nu_max[0], m->nu_max[1], pt, out);
     return cudaGetLastError();
+}
+
+// The whole tile as its one patch (no rotation): the allocation-free path.
+PatchDev single_patch()
+{
+    PatchDev p;
+    p.n = p.nx = p.ny = 1;
+    p.hw_x = p.hw_y = 0.f;
+    p.inv_pw_x = p.inv_pw_y = 0.f;
+    p.cx = p.cy = nullptr;
+    return p;
 }
 
 }  // namespace
@@ -705,7 +761,7 @@ int reserve_encode(vsaogm_map *m, int64_t n64)
 {
     const int n = (int)std::min<int64_t>(n64, kMaxBatch);
     if (n <= 0) return VSAOGM_OK;
-    const int S1 = m->S + 1, D = m->cfg.D;
+    const int SP = m->S * m->patches.n, S1 = SP + 1, D = m->cfg.D;
     int kpt, chunk;
     encode_shape(m, n, D, &kpt, &chunk);
     const int nb = (n + kSortBlock - 1) / kSortBlock;
@@ -740,7 +796,7 @@ int reserve_encode(vsaogm_map *m, int64_t n64)
         if (a >= n) break;
         lo = a + 1;
     }
-    max_chunks += m->S;
+    max_chunks += SP;
     int rc;
     if ((rc = ensure(m->ws.blk_hist, sizeof(int) * (size_t)nb * S1))) return rc;
     if ((rc = ensure(m->ws.seg_meta, sizeof(int) * (size_t)(3 * S1 + 2)))) return rc;
@@ -758,7 +814,8 @@ int reserve_encode(vsaogm_map *m, int64_t n64)
 static int sort_stage(vsaogm_map *m, Scratch &ws, const float *xy_f, const uint8_t *lab, int n,
                       int chunk, bool need_partial, cudaStream_t st, int *max_chunks_out)
 {
-    const int S = m->S, S1 = S + 1, D = m->cfg.D;
+    const PatchDev &pt = m->patches;
+    const int S = m->S * pt.n, S1 = S + 1, D = m->cfg.D;
     const int nb = (n + kSortBlock - 1) / kSortBlock;
     const int max_chunks = (n + chunk - 1) / chunk + S;
     *max_chunks_out = max_chunks;
@@ -782,10 +839,11 @@ static int sort_stage(vsaogm_map *m, Scratch &ws, const float *xy_f, const uint8
                                   (int)smem_scatter)) != cudaSuccess)
         return cuda_error(e, "encode: shared memory");
     StageScope sc(m, VSAOGM_STAGE_SORT, st);
-    seg_count_kernel<<<nb, 256, smem_count, st>>>(xy, lab, n, ax, ay, S, hist);
+    seg_count_kernel<<<nb, 256, smem_count, st>>>(xy, lab, n, ax, ay, pt, S, hist);
     seg_scan_kernel<<<S1, kScanThreads, 0, st>>>(hist, nb, S1, meta);
     seg_meta_kernel<<<1, kScanThreads, 0, st>>>(meta, S, chunk, chunks, m->rejected);
-    seg_scatter_kernel<<<nb, 256, smem_scatter, st>>>(xy, lab, n, ax, ay, S, hist, meta, sorted);
+    seg_scatter_kernel<<<nb, 256, smem_scatter, st>>>(xy, lab, n, ax, ay, pt, S, hist, meta,
+                                                      sorted);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_error(e, "encode: sort");
     sc.end(4);
     return VSAOGM_OK;
@@ -799,7 +857,7 @@ int batch_sort(vsaogm_map *m, Scratch &ws, const float *xy, const uint8_t *lab, 
 
 void batch_encode_entry(const vsaogm_map *m, const Scratch &ws, BatchEncodeMap *e)
 {
-    const int S1 = m->S + 1;
+    const int S1 = m->S * m->patches.n + 1;
     const int *meta = (const int *)ws.seg_meta.ptr;
     e->pts = (const float2 *)ws.sorted.ptr;
     e->chunks = (const int4 *)ws.chunks.ptr;
@@ -810,16 +868,18 @@ void batch_encode_entry(const vsaogm_map *m, const Scratch &ws, BatchEncodeMap *
     e->slices = (m->cfg.D + 2047) / 2048;  // the batched kernel holds 8 frequencies a thread
     e->nu_max_x = m->nu_max[0];
     e->nu_max_y = m->nu_max[1];
+    e->pt = m->patches;
 }
 
 void batch_reduce_entry(const vsaogm_map *m, const Scratch &ws, BatchReduceMap *e)
 {
-    const int S1 = m->S + 1;
+    const int S1 = m->S * m->patches.n + 1;
     const int *meta = (const int *)ws.seg_meta.ptr;
     e->partial = (const float2 *)ws.partial.ptr;
     e->cbeg = meta + 2 * S1 + 1;
     e->omega = m->omega;
     e->D = m->cfg.D;
+    e->patches = m->patches.n;
 }
 
 int encode_batch_ctas()
@@ -854,7 +914,8 @@ int encode_bundle(vsaogm_map *m, const float *xy_f, const uint8_t *lab, int64_t 
                   cudaStream_t st)
 {
     const int n = (int)n64;
-    const int S = m->S, S1 = S + 1, D = m->cfg.D;
+    const PatchDev &pt = m->patches;
+    const int S = m->S * pt.n, S1 = S + 1, D = m->cfg.D;
     const bool atomic = (m->cfg.flags & VSAOGM_FLAG_ATOMIC) != 0;
     int kpt, chunk;
     encode_shape(m, n, D, &kpt, &chunk);
@@ -881,10 +942,10 @@ int encode_bundle(vsaogm_map *m, const float *xy_f, const uint8_t *lab, int64_t 
         return cuda_error(e, "encode: shared memory");
     {
         StageScope sc(m, VSAOGM_STAGE_SORT, st);
-        seg_count_kernel<<<nb, 256, smem_count, st>>>(xy, lab, n, ax, ay, S, hist);
+        seg_count_kernel<<<nb, 256, smem_count, st>>>(xy, lab, n, ax, ay, pt, S, hist);
         seg_scan_kernel<<<S1, kScanThreads, 0, st>>>(hist, nb, S1, meta);
         seg_meta_kernel<<<1, kScanThreads, 0, st>>>(meta, S, chunk, chunks, m->rejected);
-        seg_scatter_kernel<<<nb, 256, smem_scatter, st>>>(xy, lab, n, ax, ay, S, hist, meta,
+        seg_scatter_kernel<<<nb, 256, smem_scatter, st>>>(xy, lab, n, ax, ay, pt, S, hist, meta,
                                                           sorted);
         if ((e = cudaGetLastError()) != cudaSuccess) return cuda_error(e, "encode: sort");
         sc.end(4);
@@ -895,21 +956,22 @@ int encode_bundle(vsaogm_map *m, const float *xy_f, const uint8_t *lab, int64_t 
     {
         StageScope sc(m, VSAOGM_STAGE_ENCODE, st);
         if (m->encode_packed)
-            e = launch_packed(m, kpt / 2, sorted, chunks, n_chunks, out, max_chunks, atomic, st);
+            e = launch_packed(m, pt, kpt / 2, sorted, chunks, n_chunks, out, max_chunks, atomic,
+                              st);
         else if (kpt == 4)
-            e = launch_encode<4>(m, sorted, chunks, n_chunks, out, max_chunks, atomic, st);
+            e = launch_encode<4>(m, pt, sorted, chunks, n_chunks, out, max_chunks, atomic, st);
         else if (kpt == 2)
-            e = launch_encode<2>(m, sorted, chunks, n_chunks, out, max_chunks, atomic, st);
+            e = launch_encode<2>(m, pt, sorted, chunks, n_chunks, out, max_chunks, atomic, st);
         else
-            e = launch_encode<1>(m, sorted, chunks, n_chunks, out, max_chunks, atomic, st);
+            e = launch_encode<1>(m, pt, sorted, chunks, n_chunks, out, max_chunks, atomic, st);
         if (e != cudaSuccess) return cuda_error(e, "encode: bundle");
         sc.end(1);
     }
     if (!atomic) {
         StageScope sc(m, VSAOGM_STAGE_REDUCE, st);
-        dim3 grid((D + 255) / 256, S);
+        dim3 grid((D + 255) / 256, m->S);
         reduce_partials_kernel<<<grid, 256, 0, st>>>((const float2 *)m->ws.partial.ptr, cbeg, D,
-                                                     m->omega);
+                                                     pt.n, m->omega);
         if ((e = cudaGetLastError()) != cudaSuccess) return cuda_error(e, "encode: reduce");
         sc.end(1);
     }
@@ -946,6 +1008,8 @@ static size_t align256(size_t b) { return (b + 255) / 256 * 256; }
 static int encode_bundle_noalloc(vsaogm_map *m, const float *xy_f, const uint8_t *lab, int n,
                                  cudaStream_t st)
 {
+    // one patch per tile: the scratch bound below stays the one of the memories
+    const PatchDev pt = single_patch();
     const int S = m->S, S1 = S + 1, D = m->cfg.D;
     int kpt, chunk;
     encode_shape(m, n, D, &kpt, &chunk);
@@ -981,19 +1045,21 @@ static int encode_bundle_noalloc(vsaogm_map *m, const float *xy_f, const uint8_t
     // Every scratch word these kernels read is written earlier in the same call
     // (histograms, offsets, chunk table, sorted points), so nothing has to be
     // cleared; bundling adds straight into the map's memories with atomics.
-    seg_count_kernel<<<nb, 256, sizeof(int) * S1, st>>>(xy, lab, n, ax, ay, S, hist);
+    seg_count_kernel<<<nb, 256, sizeof(int) * S1, st>>>(xy, lab, n, ax, ay, pt, S, hist);
     seg_scan_kernel<<<S1, kScanThreads, 0, st>>>(hist, nb, S1, meta);
     seg_meta_kernel<<<1, kScanThreads, 0, st>>>(meta, S, chunk, chunks, m->rejected);
-    seg_scatter_kernel<<<nb, 256, smem_scatter, st>>>(xy, lab, n, ax, ay, S, hist, meta, sorted);
+    seg_scatter_kernel<<<nb, 256, smem_scatter, st>>>(xy, lab, n, ax, ay, pt, S, hist, meta,
+                                                      sorted);
     const int *n_chunks = meta + S1 + S1 + 1 + S + 1;
     if (m->encode_packed)
-        e = launch_packed(m, kpt / 2, sorted, chunks, n_chunks, m->omega, max_chunks, true, st);
+        e = launch_packed(m, pt, kpt / 2, sorted, chunks, n_chunks, m->omega, max_chunks, true,
+                          st);
     else if (kpt == 4)
-        e = launch_encode<4>(m, sorted, chunks, n_chunks, m->omega, max_chunks, true, st);
+        e = launch_encode<4>(m, pt, sorted, chunks, n_chunks, m->omega, max_chunks, true, st);
     else if (kpt == 2)
-        e = launch_encode<2>(m, sorted, chunks, n_chunks, m->omega, max_chunks, true, st);
+        e = launch_encode<2>(m, pt, sorted, chunks, n_chunks, m->omega, max_chunks, true, st);
     else
-        e = launch_encode<1>(m, sorted, chunks, n_chunks, m->omega, max_chunks, true, st);
+        e = launch_encode<1>(m, pt, sorted, chunks, n_chunks, m->omega, max_chunks, true, st);
     if (e == cudaSuccess) e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_error(e, "encode_noalloc");
     return VSAOGM_OK;

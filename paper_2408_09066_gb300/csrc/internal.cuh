@@ -27,6 +27,17 @@ struct AxisDev {
     const double *centre;   // [n_tiles]: tile centres, FP64
 };
 
+// Patches: for bundling only, a tile too wide for the fast phase reduction is
+// cut into nx x ny patches; a chunk's points are summed relative to their
+// patch's centre and the chunk's partial memory is then turned into the tile
+// frame by one phasor per frequency.  n = 1: the tile is its own patch.
+struct PatchDev {
+    int n, nx, ny;              // patches per tile (n = nx ny), along x and along y
+    float hw_x, hw_y;           // tile half extents, metres
+    float inv_pw_x, inv_pw_y;   // patches per metre along x and y
+    const float *cx, *cy;       // [nx], [ny]: patch centres relative to the tile centre
+};
+
 // Cell table of one axis: the tile of each cell (Algorithm 1's rule applied to
 // the cell centre) and the cell centre relative to that tile's centre.
 struct CellAxisDev {
@@ -80,6 +91,7 @@ struct BatchEncodeMap {
     long long item_begin;   // first work item of this map
     int D, slices;
     float nu_max_x, nu_max_y;
+    PatchDev pt;
 };
 struct BatchEncodeTable {
     int n_maps, poly_warps;
@@ -88,9 +100,10 @@ struct BatchEncodeTable {
 };
 struct BatchReduceMap {
     const float2 *partial;
-    const int *cbeg;        // chunk range of each segment [S + 1]
+    const int *cbeg;        // chunk range of each segment [S patches + 1]
     float2 *omega;
-    int D, seg_begin;       // first global segment of this map
+    int D, seg_begin;       // first global memory of this map
+    int patches;            // segments (patches) per memory
 };
 struct BatchReduceTable {
     int n_maps, total_segs;
@@ -193,6 +206,8 @@ struct vsaogm_map {
     double *centre_x, *centre_y; // [tiles]
     int *col_tile, *row_tile;    // [W], [H]
     float *col_off, *row_off;    // [W], [H]
+    vsaogm_impl::PatchDev patches;  // bundling patches (device tables below)
+    float *patch_cx, *patch_cy;  // [patches.nx], [patches.ny]
     std::vector<int> tile_first[2], tile_last[2];  // per axis (x, y): cells of each tile
     int *status;                           // first error code recorded by a kernel
     int r_hw[2][2 * vsaogm_impl::kMaxRadius + 1];  // disk half-widths per class and dy

@@ -141,7 +141,7 @@ void free_map(vsaogm_map *m)
     if (!m) return;
     void *ptrs[] = {m->nu, m->omega, m->inv_norm, m->maxima, m->rejected, m->bnd_x_lo,
                     m->bnd_y_lo, m->centre_x, m->centre_y, m->col_tile, m->row_tile,
-                    m->col_off, m->row_off, m->status};
+                    m->col_off, m->row_off, m->status, m->patch_cx, m->patch_cy};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     free_scratch(m->ws);
@@ -335,6 +335,32 @@ int vsaogm_create(const vsaogm_config *cfg, vsaogm_map **out)
             (rc = upload(&m->col_tile, ax.cell_tile)) || (rc = upload(&m->row_tile, ay.cell_tile)) ||
             (rc = upload(&m->col_off, ax.cell_off)) || (rc = upload(&m->row_off, ay.cell_off)))
             break;
+        // Bundling patches: a tile wider than the fast phase reduction allows
+        // (|nu| * offset below 32 turns) is cut so that every patch's points lie
+        // within 30 / nu_max of its centre.  At most 4096 segments in all.
+        {
+            int pnx = std::max(1, (int)std::ceil(m->tile_w * m->nu_max[0] / 60.0));
+            int pny = std::max(1, (int)std::ceil(m->tile_h * m->nu_max[1] / 60.0));
+            if (const char *v = getenv("VSAOGM_ENCODE_PATCHES"))
+                if (atoi(v) == 0) pnx = pny = 1;
+            while ((long long)m->S * pnx * pny > 4096 && (pnx > 1 || pny > 1)) {
+                if (pnx >= pny) --pnx; else --pny;
+            }
+            std::vector<float> cxs(pnx), cys(pny);
+            for (int p = 0; p < pnx; ++p) cxs[p] = (float)(-0.5 * m->tile_w + (p + 0.5) * m->tile_w / pnx);
+            for (int p = 0; p < pny; ++p) cys[p] = (float)(-0.5 * m->tile_h + (p + 0.5) * m->tile_h / pny);
+            if ((rc = upload(&m->patch_cx, cxs)) || (rc = upload(&m->patch_cy, cys))) break;
+            PatchDev &pt = m->patches;
+            pt.nx = pnx;
+            pt.ny = pny;
+            pt.n = pnx * pny;
+            pt.hw_x = (float)(0.5 * m->tile_w);
+            pt.hw_y = (float)(0.5 * m->tile_h);
+            pt.inv_pw_x = (float)(pnx / m->tile_w);
+            pt.inv_pw_y = (float)(pny / m->tile_h);
+            pt.cx = m->patch_cx;
+            pt.cy = m->patch_cy;
+        }
         // cells of each tile per axis; decode blocks are cut from these per call
         m->tile_first[0] = ax.first;
         m->tile_last[0] = ax.last;

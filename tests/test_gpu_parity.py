@@ -294,3 +294,34 @@ def test_paper_scale_trajectory_sampled():
     assert np.abs(ogm - (2 * occ - 1)).max() <= 1e-6
     assert np.array_equal(got["cls"], oracle.classify_f32(ogm, cfg.rho))
     assert got["Phat"].max() == pytest.approx(1.0, abs=1e-6)
+
+
+@pytest.mark.parametrize("patches", ["auto", "0"])
+def test_bundling_patches_in_wide_tiles(monkeypatch, patches):
+    """One 40 m tile (its points up to 28 m from the centre): by default each
+    chunk is summed relative to the centre of its 40/6 m patch and turned into
+    the tile frame afterwards; with patches switched off the far points take
+    the exact phase reduction.  Both match the oracle, as do points far
+    outside the map."""
+    if patches == "0":
+        monkeypatch.setenv("VSAOGM_ENCODE_PATCHES", "0")
+    else:
+        monkeypatch.delenv("VSAOGM_ENCODE_PATCHES", raising=False)
+    wl = synth.paper_trajectory(n_scans=6, D=2048)
+    far = np.array([[-100.0, 50.0], [40.0, -3.0], [19.99, 19.99]], np.float32)
+    xy = np.concatenate([wl.xy, far])
+    lab = np.concatenate([wl.labels, np.array([0, 1, 1], np.uint8)])
+    cfg = V.default_config(D=2048, grid_w=400, grid_h=400, resolution=0.1, x_min=-20.0,
+                           y_min=-20.0, tiles_x=1, tiles_y=1, length_scale=0.1, seed=77)
+    _check_all(cfg, run_gpu(cfg, xy, lab), _oracle_all(cfg, xy, lab))
+
+
+def test_single_point_far_from_a_wide_tile_centre():
+    """A single point 19 m from the centre of a 40 m tile: a fast-reduced phasor
+    relative to its patch, times the exactly reduced patch rotation."""
+    cfg = V.default_config(D=4096, grid_w=400, grid_h=400, resolution=0.1, x_min=-20.0,
+                           y_min=-20.0, tiles_x=1, tiles_y=1, seed=78)
+    pts = np.array([[19.3, -18.7]], np.float32)
+    got = run_gpu(cfg, pts, np.array([1], np.uint8))
+    want = _oracle_all(cfg, pts, np.array([1], np.uint8))
+    assert np.abs(got["omega"] - want["omega"]).max() <= TOL_OMEGA
