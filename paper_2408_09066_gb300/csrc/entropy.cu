@@ -161,6 +161,137 @@ __host__ __device__ inline size_t staged_floats(int R)
 
 constexpr int kHW = 2 * kMaxRadius + 1;
 
+// Half-width of the disk of radius r at row offset dy (Eq. entropy-mask: the
+// cells with dx^2 + dy^2 <= r^2), -1 outside the disk.
+__host__ __device__ constexpr int disk_hw(int r, int dy)
+{
+    int w = -1;
+    if (dy >= -r && dy <= r)
+        while ((w + 1) * (w + 1) + dy * dy <= r * r) ++w;
+    return w;
+}
+
+// The entropy stencil for the common case of one disk radius R (<= 8) for
+// both classes: the same computation as entropy_body with every loop bound,
+// staged extent and disk half-width known at compile time, so no instruction
+// is spent on loop control or on staging rows that do not exist.
+template <int R>
+__device__ __forceinline__ void entropy_fixed_body(const float *__restrict__ heat, int W, int H,
+                                                   int wx0, int wy0, int ww, int wh, int raw,
+                                                   const unsigned *__restrict__ maxima,
+                                                   unsigned mode, float rho,
+                                                   float *__restrict__ occ,
+                                                   float *__restrict__ ogm,
+                                                   uint8_t *__restrict__ cls, int bx0, int by0,
+                                                   float *sh)
+{
+    constexpr int E = kTB + 2 * R, PITCH = E + 1;
+    constexpr int ROWS = (E + 7) / 8, STRIPS = (E + 31) / 32;
+    const int x0 = wx0 + bx0, y0 = wy0 + by0;
+    float inv[2] = {1.f, 1.f};
+    const bool norm = raw && !(mode & VSAOGM_MODE_NO_NORM);
+    const bool square = raw && !(mode & VSAOGM_MODE_NO_SQUARE);
+    if (norm) {
+        for (int c = 0; c < 2; ++c) {
+            float m = ordered_to_float(maxima[c]);
+            inv[c] = m > 0.f ? 1.0f / m : 0.f;
+        }
+    }
+    const size_t cells = (size_t)W * H;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    float v[2][ROWS][STRIPS];
+#pragma unroll
+    for (int c = 0; c < 2; ++c)
+#pragma unroll
+        for (int i = 0; i < ROWS; ++i)
+#pragma unroll
+            for (int q = 0; q < STRIPS; ++q) {
+                const int ly = warp + 8 * i, lx = lane + 32 * q;
+                const int y = y0 - R + ly, x = x0 - R + lx;
+                v[c][i][q] = (ly < E && lx < E && x >= 0 && x < W && y >= 0 && y < H)
+                                 ? __ldg(heat + c * cells + (size_t)y * W + x)
+                                 : 0.f;
+            }
+#pragma unroll
+    for (int c = 0; c < 2; ++c)
+#pragma unroll
+        for (int i = 0; i < ROWS; ++i) {
+            const int ly = warp + 8 * i;
+            if (ly >= E) continue;
+            float *row = sh + (c * E + ly) * PITCH;
+            if (lane == 0) row[0] = 0.f;
+#pragma unroll
+            for (int q = 0; q < STRIPS; ++q) {
+                const int lx = lane + 32 * q;
+                if (lx < E) {
+                    float x = v[c][i][q];
+                    if (norm) x *= inv[c];
+                    if (square) x = x * x;
+                    row[1 + lx] = x > 0.f ? -x * __logf(x) : 0.f;
+                }
+            }
+        }
+    __syncthreads();
+    if ((int)threadIdx.x < 2 * E) {
+        float *row = sh + threadIdx.x * PITCH + 1;
+        float acc = 0.f;
+#pragma unroll
+        for (int lx = 0; lx < E; ++lx) {
+            acc += row[lx];
+            row[lx] = acc;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < kTB / 8; ++q) {
+        const int ly = warp + 8 * q;
+        const int x = bx0 + lane, y = by0 + ly;
+        if (x >= ww || y >= wh) continue;
+        float Hc[2];
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+            float acc = 0.f;
+#pragma unroll
+            for (int dy = -R; dy <= R; ++dy) {
+                const int w = disk_hw(R, dy);
+                const float *row = sh + (c * E + R + ly + dy) * PITCH + R + lane;
+                acc += row[w + 1] - row[-w];
+            }
+            Hc[c] = acc;
+        }
+        const float pr1 = __fdividef(1.0f, 1.0f + __expf(Hc[0] - Hc[1]));
+        const float pr0 = __fdividef(1.0f, 1.0f + __expf(Hc[1] - Hc[0]));
+        const size_t o = (size_t)y * ww + x;
+        occ[o] = pr1;
+        const float d = pr1 - pr0;
+        if (ogm) ogm[o] = d;
+        if (cls) cls[o] = d >= rho ? 1 : 0;
+    }
+}
+
+// Radius of the fixed-radius stencil, or -1 when the generic one is needed
+// (another activation, two radii, or a radius above 8).
+__host__ inline int fixed_radius(unsigned mode, int r0, int r1)
+{
+    if ((mode & VSAOGM_ACT_MASK) != VSAOGM_ACT_ENTROPY || r0 != r1 || r0 > 8) return -1;
+    return r0;
+}
+
+template <int R>
+__global__ void __launch_bounds__(256) entropy_fixed_kernel(const float *__restrict__ heat, int W,
+                                                            int H, int wx0, int wy0, int ww, int wh,
+                                                            int raw,
+                                                            const unsigned *__restrict__ maxima,
+                                                            unsigned mode, float rho,
+                                                            float *__restrict__ occ,
+                                                            float *__restrict__ ogm,
+                                                            uint8_t *__restrict__ cls)
+{
+    extern __shared__ float sh_dyn[];
+    entropy_fixed_body<R>(heat, W, H, wx0, wy0, ww, wh, raw, maxima, mode, rho, occ, ogm, cls,
+                          blockIdx.x * kTB, blockIdx.y * kTB, sh_dyn);
+}
+
 // heat: the class maps of a W x H grid of cells (the whole map, or a decoded
 // region of it); the grid of CTAs covers window cells (wx0 + x, wy0 + y) of
 // that grid and writes output (x, y) of the ww x wh window, row stride ww.
@@ -208,6 +339,22 @@ __global__ void __launch_bounds__(256) entropy_batch_kernel(const __grid_constan
                  M.ogm, nullptr, bx0, by0, sh_dyn);
 }
 
+template <int R>
+__global__ void __launch_bounds__(256) entropy_fixed_batch_kernel(const __grid_constant__ BatchOutTable tab)
+{
+    extern __shared__ float sh_dyn[];
+    const int q = blockIdx.x;
+    int lo = 0, hi = tab.n_maps - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (tab.m[mid].blk_begin <= q) lo = mid; else hi = mid - 1;
+    }
+    const BatchMapOut &M = tab.m[lo];
+    const int local = q - M.blk_begin, bxn = (M.W + kTB - 1) / kTB;
+    entropy_fixed_body<R>(M.heat, M.W, M.H, 0, 0, M.W, M.H, 1, M.maxima, M.mode, M.rho, M.occ,
+                          M.ogm, nullptr, (local % bxn) * kTB, (local / bxn) * kTB, sh_dyn);
+}
+
 }  // namespace
 
 int launch_entropy_batch(const BatchOutTable &tab, cudaStream_t st)
@@ -219,7 +366,20 @@ int launch_entropy_batch(const BatchOutTable &tab, cudaStream_t st)
         blocks += ((M.W + kTB - 1) / kTB) * ((M.H + kTB - 1) / kTB);
         if ((M.mode & VSAOGM_ACT_MASK) == VSAOGM_ACT_ENTROPY) R = std::max(R, std::max(M.r[0], M.r[1]));
     }
-    entropy_batch_kernel<<<blocks, 256, staged_floats(R) * sizeof(float), st>>>(tab);
+    // one radius for both classes of every map: the fixed-radius stencil
+    int fixed = tab.n_maps > 0 ? fixed_radius(tab.m[0].mode, tab.m[0].r[0], tab.m[0].r[1]) : -1;
+    for (int i = 1; i < tab.n_maps && fixed >= 0; ++i)
+        if (fixed_radius(tab.m[i].mode, tab.m[i].r[0], tab.m[i].r[1]) != fixed) fixed = -1;
+    const size_t smem = staged_floats(R) * sizeof(float);
+    switch (fixed) {
+#define VSAOGM_FIXED_BATCH(RR) \
+    case RR: entropy_fixed_batch_kernel<RR><<<blocks, 256, smem, st>>>(tab); break;
+        VSAOGM_FIXED_BATCH(0) VSAOGM_FIXED_BATCH(1) VSAOGM_FIXED_BATCH(2) VSAOGM_FIXED_BATCH(3)
+        VSAOGM_FIXED_BATCH(4) VSAOGM_FIXED_BATCH(5) VSAOGM_FIXED_BATCH(6) VSAOGM_FIXED_BATCH(7)
+        VSAOGM_FIXED_BATCH(8)
+#undef VSAOGM_FIXED_BATCH
+        default: entropy_batch_kernel<<<blocks, 256, smem, st>>>(tab);
+    }
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? VSAOGM_OK : cuda_error(e, "batch entropy");
 }
@@ -236,10 +396,26 @@ int entropy(vsaogm_map *m, const float *heat, Region r, Region win, bool raw_inp
     StageScope sc(m, VSAOGM_STAGE_ENTROPY, st);
     const unsigned act = m->cfg.decode_mode & VSAOGM_ACT_MASK;
     const int R = act == VSAOGM_ACT_ENTROPY ? std::max(dp.r[0], dp.r[1]) : 0;
-    entropy_kernel<<<grid, 256, staged_floats(R) * sizeof(float), st>>>(
-                                         heat, r.w(), r.h(), win.x0 - r.x0, win.y0 - r.y0,
-                                         win.w(), win.h(), raw_input ? 1 : 0, m->maxima, dp,
-                                         m->cfg.decode_mode, m->cfg.rho, occ, ogm, cls);
+    const size_t smem = staged_floats(R) * sizeof(float);
+    const int fixed = fixed_radius(m->cfg.decode_mode, dp.r[0], dp.r[1]);
+    switch (fixed) {
+#define VSAOGM_FIXED(RR)                                                                          \
+    case RR:                                                                                      \
+        entropy_fixed_kernel<RR><<<grid, 256, smem, st>>>(heat, r.w(), r.h(), win.x0 - r.x0,      \
+                                                          win.y0 - r.y0, win.w(), win.h(),        \
+                                                          raw_input ? 1 : 0, m->maxima,           \
+                                                          m->cfg.decode_mode, m->cfg.rho, occ,    \
+                                                          ogm, cls);                              \
+        break;
+        VSAOGM_FIXED(0) VSAOGM_FIXED(1) VSAOGM_FIXED(2) VSAOGM_FIXED(3) VSAOGM_FIXED(4)
+        VSAOGM_FIXED(5) VSAOGM_FIXED(6) VSAOGM_FIXED(7) VSAOGM_FIXED(8)
+#undef VSAOGM_FIXED
+        default:
+            entropy_kernel<<<grid, 256, smem, st>>>(heat, r.w(), r.h(), win.x0 - r.x0,
+                                                    win.y0 - r.y0, win.w(), win.h(),
+                                                    raw_input ? 1 : 0, m->maxima, dp,
+                                                    m->cfg.decode_mode, m->cfg.rho, occ, ogm, cls);
+    }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_error(e, "entropy");
     sc.end(1);
