@@ -373,41 +373,44 @@ __device__ __forceinline__ void decode_tc_body(
             // the next tile (warp-uniform): there the phasor and the memories
             // are reloaded.
             {
-                float2 rot[FPL], e[FPL], w0[FPL], w1[FPL];
-                auto load_w = [&](int t) {
+                // U_psi of the thread's current row; the next row of the same
+                // tile is U_psi times exp(i 2 pi nu_y 16 res)
+                float2 rot[FPL], u0[FPL], u1[FPL];
+                auto start_row = [&](int q) {
 #pragma unroll
                     for (int j = 0; j < FPL; ++j) {
-                        w0[j] = sw[(2 * t) * KS + FPL * lane + j];
-                        w1[j] = sw[(2 * t + 1) * KS + FPL * lane + j];
+                        const float2 e = phasor(nuy[j], dy[q]);
+                        const float2 w0 = sw[(2 * tl[q]) * KS + FPL * lane + j];
+                        const float2 w1 = sw[(2 * tl[q] + 1) * KS + FPL * lane + j];
+                        u0[j] = make_float2(w0.x * e.x + w0.y * e.y, w0.x * e.y - w0.y * e.x);
+                        u1[j] = make_float2(w1.x * e.x + w1.y * e.y, w1.x * e.y - w1.y * e.x);
                     }
                 };
 #pragma unroll
-                for (int j = 0; j < FPL; ++j) {
-                    rot[j] = phasor(nuy[j], step_d);
-                    e[j] = phasor(nuy[j], dy[0]);
-                }
-                load_w(tl[0]);
+                for (int j = 0; j < FPL; ++j) rot[j] = phasor(nuy[j], step_d);
+                start_row(0);
 #pragma unroll
                 for (int q = 0; q < kQ; ++q) {
                     const int m = warp + kWarps * q;
                     if (q > 0) {
                         if (tl[q] != tl[q - 1]) {
-#pragma unroll
-                            for (int j = 0; j < FPL; ++j) e[j] = phasor(nuy[j], dy[q]);
-                            load_w(tl[q]);
+                            start_row(q);
                         } else {
 #pragma unroll
-                            for (int j = 0; j < FPL; ++j) e[j] = cmul(e[j], rot[j]);
+                            for (int j = 0; j < FPL; ++j) {
+                                u0[j] = cmul(u0[j], rot[j]);
+                                u1[j] = cmul(u1[j], rot[j]);
+                            }
                         }
                     }
                     float u0r[FPL], u0i[FPL], u1r[FPL], u1i[FPL];
 #pragma unroll
                     for (int j = 0; j < FPL; ++j) {
-                        const float2 v = (kv[j] && m < nj) ? e[j] : make_float2(0.f, 0.f);
-                        u0r[j] = w0[j].x * v.x + w0[j].y * v.y;
-                        u0i[j] = w0[j].x * v.y - w0[j].y * v.x;
-                        u1r[j] = w1[j].x * v.x + w1[j].y * v.y;
-                        u1i[j] = w1[j].x * v.y - w1[j].y * v.x;
+                        const bool ok = kv[j] && m < nj;
+                        u0r[j] = ok ? u0[j].x : 0.f;
+                        u0i[j] = ok ? u0[j].y : 0.f;
+                        u1r[j] = ok ? u1[j].x : 0.f;
+                        u1i[j] = ok ? u1[j].y : 0.f;
                     }
                     const uint32_t o = q * kWarps * kRowBytes + soff;
                     uint32_t hi, lo;
