@@ -30,8 +30,9 @@ def main():
     max_points = max(len(s[1]) for r in fleet for s in r.scans)
     srv = serving.Server(cfgs, max_points=max_points, max_window=512, n_slots=a.slots)
     try:
-        # warm-up: one closed batch touching every robot
-        srv.run(serving.poisson_requests(fleet, 2000.0, 0.05, a.query_frac, seed=99),
+        # warm-up: closed batches touching every robot with both request kinds,
+        # so no measured request pays for a first launch of a kernel
+        srv.run(serving.poisson_requests(fleet, 2000.0, 0.5, a.query_frac, seed=99),
                 realtime=False)
         for i, rate in enumerate(float(x) for x in a.rates.split(",")):
             reqs = serving.poisson_requests(fleet, rate, a.duration, a.query_frac, seed=i)
