@@ -35,10 +35,14 @@ SM_MAX_MHZ = 2070.0
 MUFU_PER_SM_CLK = 16          # sin/cos ops per SM per clock (measured 15.2 at max clock)
 FP32_FMA_PER_SM_CLK = 128
 # FMA-pipe lane-ops per complex exponential in encode_chunk_x2_kernel (counted
-# from its code): phase 5 (mul, fma, two adds for rint, sub) + 2 pi scale 1 +
-# MUFU argument scaling 1 + accumulate 2; polynomial path: phase 5 +
-# half-angle Taylor and complex square 19 + accumulate 2.
-MUFU_PATH_FMA = 9
+# from its code) for chunks whose phases stay below 4 turns, which bundling
+# patches make every chunk inside the map: phase 2 (mul, fma) + 2 pi scale 1 +
+# MUFU argument scaling 1 + accumulate 2, no reduction (MUFU's own costs it
+# less than 5e-6 rad there); polynomial path: phase with reduction 5 +
+# half-angle Taylor and complex square 19 + accumulate 2.  Chunks beyond 4
+# turns (points outside the map, or patches capped by the segment limit)
+# reduce first: 9 lane-ops on the MUFU path.
+MUFU_PATH_FMA = 6
 POLY_PATH_FMA = 26
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 CLOCK_FIELDS = ("index,pci.bus_id,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"

@@ -175,18 +175,19 @@ int enqueue_step(vsaogm_batch *b, const float *const *xy, const uint8_t *const *
     for (int i = 0; i < M; ++i) {
         vsaogm_map *m = b->maps[i];
         int max_chunks = 0;
+        const PatchDev &pt = choose_patches(m, n[i]);
         if (n[i] > 0) {
-            if ((rc = batch_sort(m, b->ws[i], xy[i], lab[i], (int)n[i], chunk,
+            if ((rc = batch_sort(m, b->ws[i], pt, xy[i], lab[i], (int)n[i], chunk,
                                  b->aux[i % kAuxStreams], &max_chunks)))
                 return rc;
             counted[VSAOGM_STAGE_SORT] += 4;
         }
         BatchEncodeMap &em = et.m[i];
-        batch_encode_entry(m, b->ws[i], &em);
+        batch_encode_entry(m, b->ws[i], pt, &em);
         em.item_begin = items;
         items += (long long)max_chunks * em.slices;
         if (n[i] == 0) em.slices = 1;  // no items: max_chunks = 0
-        batch_reduce_entry(m, b->ws[i], &rt.m[i]);
+        batch_reduce_entry(m, b->ws[i], pt, &rt.m[i]);
         rt.m[i].seg_begin = segs;
         segs += n[i] > 0 ? m->S : 0;
         d_max = std::max(d_max, m->cfg.D);
@@ -496,7 +497,7 @@ int vsaogm_batch_autotune(vsaogm_batch *b, const float *const *xy, const uint8_t
     Tuning best = b->tune;
     float best_ms = 1e30f;
     // encode shape first (decode fixed), then the decode slicing
-    const int pws[] = {4, 5, 6, 7}, ipcs[] = {4, 8, 16};
+    const int pws[] = {5, 6, 7, 8}, ipcs[] = {4, 8, 16};
     for (int pw : pws)
         for (int ipc : ipcs) {
             if (rc) break;

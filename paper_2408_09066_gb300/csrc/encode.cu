@@ -401,7 +401,12 @@ __global__ void __launch_bounds__(256) encode_chunk_kernel(const float2 *__restr
 //     squared as a complex number; the other pairs use MUFU sin/cos.  The
 //     phase reduction is the one of encode_points, lane by lane.
 
-template <int NP, int NPOLY, bool EXACT>
+// TIER 0 (every |nu d| of the chunk below 4 turns): the MUFU lanes take
+// sin/cos of 2 pi t without reducing t (MUFU's own argument reduction costs it
+// about 1e-7 x |2 pi t| <= 5e-6 rad here, measured on GB300, less than the
+// reduction's 3 operations would save); the polynomial lanes reduce t first.
+// TIER 1: the fast reduction.  TIER 2: the exact reduction.
+template <int NP, int NPOLY, int TIER>
 __device__ __forceinline__ void encode_points_x2(const float2 *sp, int len,
                                                  const sm100::f32x2 (&nx)[NP],
                                                  const sm100::f32x2 (&ny)[NP],
@@ -428,19 +433,20 @@ __device__ __forceinline__ void encode_points_x2(const float2 *sp, int len,
         const f32x2 qx = pack2(q.x, q.x), qy = pack2(q.y, q.y);
 #pragma unroll
         for (int j = 0; j < NP; ++j) {
-            f32x2 p1 = mul2(nx[j], qx), p2 = mul2(ny[j], qy);
-            f32x2 f;
-            if (EXACT) {
+            f32x2 p2 = mul2(ny[j], qy);
+            f32x2 f, t;
+            if (TIER == 2) {
                 // as encode_points: f_i = fl(nu_i d_i - rint(p_i)) with one FMA
+                f32x2 p1 = mul2(nx[j], qx);
                 f32x2 n1 = sub2(kM, add2(p1, kM)), n2 = sub2(kM, add2(p2, kM));
                 f32x2 g = add2(fma2(nx[j], qx, n1), fma2(ny[j], qy, n2));
                 f = sub2(g, sub2(add2(g, kM), kM));
             } else {
                 // t = nu_x dx + nu_y dy with one rounding of the sum (FMA);
                 // t - rint(t) is exact.  Error at most ulp(64)/2 + ulp(32)/2
-                // = 2.9e-6 turns for |t| < 64.
-                f32x2 t = fma2(nx[j], qx, p2);
-                f = sub2(t, sub2(add2(t, kM), kM));
+                // = 2.9e-6 turns for |t| < 64 (3.6e-7 for |t| < 8).
+                t = fma2(nx[j], qx, p2);
+                if (TIER == 1 || j < NPOLY) f = sub2(t, sub2(add2(t, kM), kM));
             }
             f32x2 cr, si;
             if (j < NPOLY) {
@@ -460,7 +466,7 @@ __device__ __forceinline__ void encode_points_x2(const float2 *sp, int len,
                 cr = mul2(sub2(c, s), add2(c, s));  // cos 2x = (c - s)(c + s)
                 si = mul2(add2(c, c), s);           // sin 2x = 2 c s
             } else {
-                float2 a = unpack2(mul2(f, kTwoPi));
+                float2 a = unpack2(mul2(TIER == 0 ? t : f, kTwoPi));
                 float s0, c0, s1, c1;
                 __sincosf(a.x, &s0, &c0);
                 __sincosf(a.y, &s1, &c1);
@@ -519,22 +525,31 @@ __device__ __forceinline__ void encode_chunk_x2_body(const float2 *__restrict__ 
         atomicMax(&s_bound[1], __float_as_uint(my));
     }
     __syncthreads();
-    const bool fast = __uint_as_float(s_bound[0]) * nu_max_x < 32.0f &&
-                      __uint_as_float(s_bound[1]) * nu_max_y < 32.0f;
+    const float ex = __uint_as_float(s_bound[0]) * nu_max_x;
+    const float ey = __uint_as_float(s_bound[1]) * nu_max_y;
+    const int tier = (ex < 4.0f && ey < 4.0f) ? 0 : (ex < 32.0f && ey < 32.0f) ? 1 : 2;
     if (NPOLY >= 0) {
         constexpr int P = NPOLY < 0 ? 0 : NPOLY;
-        if (fast)
-            encode_points_x2<NP, P, false>(sp, len, nx, ny, ac, as);
+        if (tier == 0)
+            encode_points_x2<NP, P, 0>(sp, len, nx, ny, ac, as);
+        else if (tier == 1)
+            encode_points_x2<NP, P, 1>(sp, len, nx, ny, ac, as);
         else
-            encode_points_x2<NP, P, true>(sp, len, nx, ny, ac, as);
-    } else if (!fast) {
+            encode_points_x2<NP, P, 2>(sp, len, nx, ny, ac, as);
+    } else if (tier == 2) {
         // the exact reduction leaves the FMA pipe no room for polynomial
         // exponentials: every warp takes the MUFU path
-        encode_points_x2<NP, 0, true>(sp, len, nx, ny, ac, as);
+        encode_points_x2<NP, 0, 2>(sp, len, nx, ny, ac, as);
     } else if ((int)(threadIdx.x >> 5) < poly_warps) {
-        encode_points_x2<NP, 1, false>(sp, len, nx, ny, ac, as);
+        if (tier == 0)
+            encode_points_x2<NP, 1, 0>(sp, len, nx, ny, ac, as);
+        else
+            encode_points_x2<NP, 1, 1>(sp, len, nx, ny, ac, as);
     } else {
-        encode_points_x2<NP, 0, false>(sp, len, nx, ny, ac, as);
+        if (tier == 0)
+            encode_points_x2<NP, 0, 0>(sp, len, nx, ny, ac, as);
+        else
+            encode_points_x2<NP, 0, 1>(sp, len, nx, ny, ac, as);
     }
     const int mem = ch.x / pt.n, patch = ch.x - mem * pt.n;
     const float pcx = pt.n > 1 ? pt.cx[patch % pt.nx] : 0.f;
@@ -661,9 +676,12 @@ __global__ void __launch_bounds__(256) reduce_partials_kernel(const float2 *__re
 
 // Warps per CTA (of 8) that evaluate one frequency pair by polynomial when the
 // map does not say otherwise: the share of exponentials moved from the MUFU
-// pipe to the FMA pipe that balanced the two pipes on GB300.
-constexpr int kAutoPolyWarps4 = 6;  // 4 pairs per thread: 6/32 of the exponentials
-constexpr int kAutoPolyWarps2 = 3;  // 2 pairs per thread: 3/16
+// pipe to the FMA pipe that balanced the two pipes on GB300 (measured sweeps).
+// Chunks whose phases stay below 4 turns spend fewer FMA operations on the MUFU
+// path, so more exponentials go to the polynomial there.
+constexpr int kAutoPolyWarps4Near = 8;  // 4 pairs per thread, phases below 4 turns: 8/32
+constexpr int kAutoPolyWarps4 = 6;      // 4 pairs per thread otherwise: 6/32
+constexpr int kAutoPolyWarps2 = 3;      // 2 pairs per thread: 3/16
 
 template <int NP, int NPOLY>
 cudaError_t launch_x2(const vsaogm_map *m, const PatchDev &pt, const float2 *pts,
@@ -686,8 +704,12 @@ cudaError_t launch_packed(const vsaogm_map *m, const PatchDev &pt, int np, const
                           bool atomic, cudaStream_t st)
 {
     const int npoly = std::min(m->encode_poly_pairs, np);
-    const int pw = m->encode_poly_warps >= 0 ? m->encode_poly_warps
-                                             : (np == 4 ? kAutoPolyWarps4 : kAutoPolyWarps2);
+    // every point inside the map lies within half a patch of its patch centre
+    const bool near = m->tile_w / (2.0 * pt.nx) * m->nu_max[0] < 4.0 &&
+                      m->tile_h / (2.0 * pt.ny) * m->nu_max[1] < 4.0;
+    const int pw = m->encode_poly_warps >= 0
+                       ? m->encode_poly_warps
+                       : (np == 4 ? (near ? kAutoPolyWarps4Near : kAutoPolyWarps4) : kAutoPolyWarps2);
     if (npoly == 0 && pw > 0) {  // mixed: some warps with one polynomial pair
         if (np == 4)
             return launch_x2<4, -1>(m, pt, pts, chunks, n_chunks, out, max_chunks, atomic, pw, st);
@@ -761,7 +783,7 @@ int reserve_encode(vsaogm_map *m, int64_t n64)
 {
     const int n = (int)std::min<int64_t>(n64, kMaxBatch);
     if (n <= 0) return VSAOGM_OK;
-    const int SP = m->S * m->patches.n, S1 = SP + 1, D = m->cfg.D;
+    const int SP = m->S * std::max(m->patches[0].n, m->patches[1].n), S1 = SP + 1, D = m->cfg.D;
     int kpt, chunk;
     encode_shape(m, n, D, &kpt, &chunk);
     const int nb = (n + kSortBlock - 1) / kSortBlock;
@@ -811,10 +833,10 @@ int reserve_encode(vsaogm_map *m, int64_t n64)
 // Stage 1 of encode + bundle for one map: tile assignment and the stable
 // counting sort into segment order with chunks of at most `chunk` points, in
 // the map's scratch (grown if needed).  Returns the chunk-table bound.
-static int sort_stage(vsaogm_map *m, Scratch &ws, const float *xy_f, const uint8_t *lab, int n,
-                      int chunk, bool need_partial, cudaStream_t st, int *max_chunks_out)
+static int sort_stage(vsaogm_map *m, Scratch &ws, const PatchDev &pt, const float *xy_f,
+                      const uint8_t *lab, int n, int chunk, bool need_partial, cudaStream_t st,
+                      int *max_chunks_out)
 {
-    const PatchDev &pt = m->patches;
     const int S = m->S * pt.n, S1 = S + 1, D = m->cfg.D;
     const int nb = (n + kSortBlock - 1) / kSortBlock;
     const int max_chunks = (n + chunk - 1) / chunk + S;
@@ -849,15 +871,23 @@ static int sort_stage(vsaogm_map *m, Scratch &ws, const float *xy_f, const uint8
     return VSAOGM_OK;
 }
 
-int batch_sort(vsaogm_map *m, Scratch &ws, const float *xy, const uint8_t *lab, int n, int chunk,
-               cudaStream_t st, int *max_chunks)
+int batch_sort(vsaogm_map *m, Scratch &ws, const PatchDev &pt, const float *xy,
+               const uint8_t *lab, int n, int chunk, cudaStream_t st, int *max_chunks)
 {
-    return sort_stage(m, ws, xy, lab, n, chunk, true, st, max_chunks);
+    return sort_stage(m, ws, pt, xy, lab, n, chunk, true, st, max_chunks);
 }
 
-void batch_encode_entry(const vsaogm_map *m, const Scratch &ws, BatchEncodeMap *e)
+const PatchDev &choose_patches(const vsaogm_map *m, int64_t n)
 {
-    const int S1 = m->S * m->patches.n + 1;
+    const PatchDev &fine = m->patches[1], &coarse = m->patches[0];
+    if (fine.n == coarse.n) return coarse;
+    return n >= (int64_t)512 * m->S * fine.n ? fine : coarse;
+}
+
+void batch_encode_entry(const vsaogm_map *m, const Scratch &ws, const PatchDev &pt,
+                        BatchEncodeMap *e)
+{
+    const int S1 = m->S * pt.n + 1;
     const int *meta = (const int *)ws.seg_meta.ptr;
     e->pts = (const float2 *)ws.sorted.ptr;
     e->chunks = (const int4 *)ws.chunks.ptr;
@@ -868,18 +898,19 @@ void batch_encode_entry(const vsaogm_map *m, const Scratch &ws, BatchEncodeMap *
     e->slices = (m->cfg.D + 2047) / 2048;  // the batched kernel holds 8 frequencies a thread
     e->nu_max_x = m->nu_max[0];
     e->nu_max_y = m->nu_max[1];
-    e->pt = m->patches;
+    e->pt = pt;
 }
 
-void batch_reduce_entry(const vsaogm_map *m, const Scratch &ws, BatchReduceMap *e)
+void batch_reduce_entry(const vsaogm_map *m, const Scratch &ws, const PatchDev &pt,
+                        BatchReduceMap *e)
 {
-    const int S1 = m->S * m->patches.n + 1;
+    const int S1 = m->S * pt.n + 1;
     const int *meta = (const int *)ws.seg_meta.ptr;
     e->partial = (const float2 *)ws.partial.ptr;
     e->cbeg = meta + 2 * S1 + 1;
     e->omega = m->omega;
     e->D = m->cfg.D;
-    e->patches = m->patches.n;
+    e->patches = pt.n;
 }
 
 int encode_batch_ctas()
@@ -914,7 +945,7 @@ int encode_bundle(vsaogm_map *m, const float *xy_f, const uint8_t *lab, int64_t 
                   cudaStream_t st)
 {
     const int n = (int)n64;
-    const PatchDev &pt = m->patches;
+    const PatchDev &pt = choose_patches(m, n64);
     const int S = m->S * pt.n, S1 = S + 1, D = m->cfg.D;
     const bool atomic = (m->cfg.flags & VSAOGM_FLAG_ATOMIC) != 0;
     int kpt, chunk;

@@ -15,6 +15,7 @@
 // fast hardware approximations: their errors (about 1e-6 relative) are far
 // below the probabilities' 1e-3 tolerance.
 #include <algorithm>
+#include <utility>
 
 #include "internal.cuh"
 
@@ -171,6 +172,22 @@ __host__ __device__ constexpr int disk_hw(int r, int dy)
     return w;
 }
 
+// One disk row (offset DY) of a cell's disk sum as the difference of two
+// running sums; `base` points at the cell's column in its own row.  The row's
+// half-width is a template constant.
+template <int R, int DY, int PITCH>
+__device__ __forceinline__ float disk_row(const float *base)
+{
+    constexpr int w = disk_hw(R, DY);
+    static_assert(w >= 0, "rows of the disk only");
+    return base[DY * PITCH + w + 1] - base[DY * PITCH - w];
+}
+template <int R, int PITCH, int... I>
+__device__ __forceinline__ float disk_sum(const float *base, std::integer_sequence<int, I...>)
+{
+    return (0.f + ... + disk_row<R, I - R, PITCH>(base));
+}
+
 // The entropy stencil for the common case of one disk radius R (<= 8) for
 // both classes: the same computation as entropy_body with every loop bound,
 // staged extent and disk half-width known at compile time, so no instruction
@@ -249,16 +266,9 @@ __device__ __forceinline__ void entropy_fixed_body(const float *__restrict__ hea
         if (x >= ww || y >= wh) continue;
         float Hc[2];
 #pragma unroll
-        for (int c = 0; c < 2; ++c) {
-            float acc = 0.f;
-#pragma unroll
-            for (int dy = -R; dy <= R; ++dy) {
-                const int w = disk_hw(R, dy);
-                const float *row = sh + (c * E + R + ly + dy) * PITCH + R + lane;
-                acc += row[w + 1] - row[-w];
-            }
-            Hc[c] = acc;
-        }
+        for (int c = 0; c < 2; ++c)
+            Hc[c] = disk_sum<R, PITCH>(sh + (c * E + R + ly) * PITCH + R + lane,
+                                       std::make_integer_sequence<int, 2 * R + 1>{});
         const float pr1 = __fdividef(1.0f, 1.0f + __expf(Hc[0] - Hc[1]));
         const float pr0 = __fdividef(1.0f, 1.0f + __expf(Hc[1] - Hc[0]));
         const size_t o = (size_t)y * ww + x;

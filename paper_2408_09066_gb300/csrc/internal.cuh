@@ -206,8 +206,10 @@ struct vsaogm_map {
     double *centre_x, *centre_y; // [tiles]
     int *col_tile, *row_tile;    // [W], [H]
     float *col_off, *row_off;    // [W], [H]
-    vsaogm_impl::PatchDev patches;  // bundling patches (device tables below)
-    float *patch_cx, *patch_cy;  // [patches.nx], [patches.ny]
+    // bundling patches: [0] coarse (phases below 32 turns), [1] fine (below 4
+    // turns); device tables of patch centres below
+    vsaogm_impl::PatchDev patches[2];
+    float *patch_cx[2], *patch_cy[2];
     std::vector<int> tile_first[2], tile_last[2];  // per axis (x, y): cells of each tile
     int *status;                           // first error code recorded by a kernel
     int r_hw[2][2 * vsaogm_impl::kMaxRadius + 1];  // disk half-widths per class and dy
@@ -276,12 +278,18 @@ int entropy(vsaogm_map *m, const float *heat, Region r, Region win, bool raw_inp
 // misc kernels (decode.cu)
 int add_memories(float2 *dst, const float2 *src, int64_t count, cudaStream_t st);
 
+// The patching for a call of n points: the fine one when its segments hold
+// enough points each to pay for their fixed costs, else the coarse one.
+const PatchDev &choose_patches(const vsaogm_map *m, int64_t n);
+
 // batched (many-map) stages, used by batch.cu; `ws` is scratch the batch owns
 // (not the map's), so per-map calls never move memory a captured step uses
-int batch_sort(vsaogm_map *m, Scratch &ws, const float *xy, const uint8_t *lab, int n, int chunk,
-               cudaStream_t st, int *max_chunks);
-void batch_encode_entry(const vsaogm_map *m, const Scratch &ws, BatchEncodeMap *e);
-void batch_reduce_entry(const vsaogm_map *m, const Scratch &ws, BatchReduceMap *e);
+int batch_sort(vsaogm_map *m, Scratch &ws, const PatchDev &pt, const float *xy,
+               const uint8_t *lab, int n, int chunk, cudaStream_t st, int *max_chunks);
+void batch_encode_entry(const vsaogm_map *m, const Scratch &ws, const PatchDev &pt,
+                        BatchEncodeMap *e);
+void batch_reduce_entry(const vsaogm_map *m, const Scratch &ws, const PatchDev &pt,
+                        BatchReduceMap *e);
 int encode_batch_ctas();
 int launch_encode_batch(const BatchEncodeTable &tab, unsigned long long *counter, int ctas,
                         cudaStream_t st);

@@ -141,7 +141,8 @@ void free_map(vsaogm_map *m)
     if (!m) return;
     void *ptrs[] = {m->nu, m->omega, m->inv_norm, m->maxima, m->rejected, m->bnd_x_lo,
                     m->bnd_y_lo, m->centre_x, m->centre_y, m->col_tile, m->row_tile,
-                    m->col_off, m->row_off, m->status, m->patch_cx, m->patch_cy};
+                    m->col_off, m->row_off, m->status, m->patch_cx[0], m->patch_cy[0],
+                    m->patch_cx[1], m->patch_cy[1]};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     free_scratch(m->ws);
@@ -335,12 +336,15 @@ int vsaogm_create(const vsaogm_config *cfg, vsaogm_map **out)
             (rc = upload(&m->col_tile, ax.cell_tile)) || (rc = upload(&m->row_tile, ay.cell_tile)) ||
             (rc = upload(&m->col_off, ax.cell_off)) || (rc = upload(&m->row_off, ay.cell_off)))
             break;
-        // Bundling patches: a tile wider than the fast phase reduction allows
-        // (|nu| * offset below 32 turns) is cut so that every patch's points lie
-        // within 30 / nu_max of its centre.  At most 4096 segments in all.
-        {
-            int pnx = std::max(1, (int)std::ceil(m->tile_w * m->nu_max[0] / 60.0));
-            int pny = std::max(1, (int)std::ceil(m->tile_h * m->nu_max[1] / 60.0));
+        // Bundling patches.  Coarse: every patch's points lie within 30 / nu_max
+        // of its centre (phases below 32 turns: the fast reduction).  Fine:
+        // within 3.9 / nu_max (below 4 turns: MUFU sin/cos on unreduced phases).
+        // At most 4096 segments each; beyond that, patches are larger and their
+        // chunks take the next path.
+        for (int level = 0; level < 2 && rc == VSAOGM_OK; ++level) {
+            const double reach = level == 0 ? 60.0 : 7.8;  // patch width x nu_max
+            int pnx = std::max(1, (int)std::ceil(m->tile_w * m->nu_max[0] / reach));
+            int pny = std::max(1, (int)std::ceil(m->tile_h * m->nu_max[1] / reach));
             if (const char *v = getenv("VSAOGM_ENCODE_PATCHES"))
                 if (atoi(v) == 0) pnx = pny = 1;
             while ((long long)m->S * pnx * pny > 4096 && (pnx > 1 || pny > 1)) {
@@ -349,8 +353,9 @@ int vsaogm_create(const vsaogm_config *cfg, vsaogm_map **out)
             std::vector<float> cxs(pnx), cys(pny);
             for (int p = 0; p < pnx; ++p) cxs[p] = (float)(-0.5 * m->tile_w + (p + 0.5) * m->tile_w / pnx);
             for (int p = 0; p < pny; ++p) cys[p] = (float)(-0.5 * m->tile_h + (p + 0.5) * m->tile_h / pny);
-            if ((rc = upload(&m->patch_cx, cxs)) || (rc = upload(&m->patch_cy, cys))) break;
-            PatchDev &pt = m->patches;
+            if ((rc = upload(&m->patch_cx[level], cxs)) || (rc = upload(&m->patch_cy[level], cys)))
+                break;
+            PatchDev &pt = m->patches[level];
             pt.nx = pnx;
             pt.ny = pny;
             pt.n = pnx * pny;
@@ -358,9 +363,10 @@ int vsaogm_create(const vsaogm_config *cfg, vsaogm_map **out)
             pt.hw_y = (float)(0.5 * m->tile_h);
             pt.inv_pw_x = (float)(pnx / m->tile_w);
             pt.inv_pw_y = (float)(pny / m->tile_h);
-            pt.cx = m->patch_cx;
-            pt.cy = m->patch_cy;
+            pt.cx = m->patch_cx[level];
+            pt.cy = m->patch_cy[level];
         }
+        if (rc != VSAOGM_OK) break;
         // cells of each tile per axis; decode blocks are cut from these per call
         m->tile_first[0] = ax.first;
         m->tile_last[0] = ax.last;
