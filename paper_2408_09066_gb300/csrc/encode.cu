@@ -12,8 +12,12 @@
 //   5. encode_chunk : one CTA per (chunk, slice of k); each thread keeps KPT
 //                     frequencies in registers, walks the chunk's points from
 //                     shared memory and accumulates exp(i 2 pi nu . p) with
-//                     MUFU sin/cos after an exact reduction of the phase to
-//                     [-1/2, 1/2] turns.  Partial memories go to scratch ...
+//                     MUFU sin/cos (or a polynomial on the FMA pipe) of the
+//                     phase, reduced to [-1/2, 1/2] turns unless it stays
+//                     below 4 turns.  Points are taken relative to the centre
+//                     of their bundling patch, and each chunk's sum is turned
+//                     into the tile frame afterwards.  Partial memories go to
+//                     scratch ...
 //   6. reduce       : ... and are summed per segment in a fixed order, so the
 //                     result does not depend on scheduling.  With
 //                     VSAOGM_FLAG_ATOMIC step 5 adds into the memories with

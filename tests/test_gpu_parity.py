@@ -4,7 +4,10 @@ Tolerances (normwise error = max|gpu - oracle| / max|oracle|):
   * memories omega: 3e-5.  Each phasor carries at most 2.5e-5 rad of phase
     error from the kernel's fast phase reduction (|nu . offset| < 32 turns;
     far points take an exact reduction, about 4e-7 rad) plus about 4e-7 from
-    MUFU sin/cos; a memory of one point is a single phasor, so the bound is
+    MUFU sin/cos; below 4 turns (every point inside the map, in its bundling
+    patch) the phase goes unreduced to MUFU, whose own argument reduction
+    costs about 1e-7 x |2 pi t| <= 5e-6 rad (measured on GB300), about 1e-5
+    rad in all.  A memory of one point is a single phasor, so the bound is
     reached there, while sums of many phasors average it down;
   * quasi-probabilities P and P_hat of the FP32 decode: 1e-4;
   * occupancy Pr(psi = 1) and OGM: 1e-3 absolute (the entropy sums up to
