@@ -335,9 +335,9 @@ __device__ __forceinline__ void decode_tc_body(
             uint8_t *st = smem + (size_t)buf * stage_bytes;
             uint8_t *bh = st + kAStage, *bl = bh + N * kRowBytes;
             const float2 *sw = reinterpret_cast<const float2 *>(bl + N * kRowBytes);
-            bool kv[FPL];
-#pragma unroll
-            for (int j = 0; j < FPL; ++j) kv[j] = k_begin + s * KS + FPL * lane + j < k_end;
+            // No masking below: frequencies past the slice's end have staged
+            // memories 0, so their U and hence their products vanish; rows and
+            // columns past the block (its MMA padding) are never written out.
             if (s + 1 < n_stages) prefetch(s + 1);  // in flight while this stage is generated
             // B operand: x phasors of the N columns.  Column warp + 16 (q + 1)
             // is 16 cells right of column warp + 16 q in the same tile, so its
@@ -353,17 +353,14 @@ __device__ __forceinline__ void decode_tc_body(
                 for (int q = 0; q < kQ; ++q) {
                     const int n = warp + kWarps * q;
                     if (n >= N) break;
-                    float2 v[FPL];
 #pragma unroll
-                    for (int j = 0; j < FPL; ++j) {
+                    for (int j = 0; j < FPL; ++j)
                         if (q > 0) a[j] = cmul(a[j], rot[j]);
-                        v[j] = (kv[j] && n < ni) ? a[j] : make_float2(0.f, 0.f);
-                    }
                     uint32_t hi, lo;
                     if (FPL == 1)
-                        split_pair<P>(v[0].x, v[0].y, hi, lo);
+                        split_pair<P>(a[0].x, a[0].y, hi, lo);
                     else
-                        split_quad_e4m3(v[0].x, v[0].y, v[FPL - 1].x, v[FPL - 1].y, hi, lo);
+                        split_quad_e4m3(a[0].x, a[0].y, a[FPL - 1].x, a[FPL - 1].y, hi, lo);
                     *reinterpret_cast<uint32_t *>(bh + q * kWarps * kRowBytes + soff) = hi;
                     *reinterpret_cast<uint32_t *>(bl + q * kWarps * kRowBytes + soff) = lo;
                 }
@@ -391,7 +388,6 @@ __device__ __forceinline__ void decode_tc_body(
                 start_row(0);
 #pragma unroll
                 for (int q = 0; q < kQ; ++q) {
-                    const int m = warp + kWarps * q;
                     if (q > 0) {
                         if (tl[q] != tl[q - 1]) {
                             start_row(q);
@@ -403,27 +399,18 @@ __device__ __forceinline__ void decode_tc_body(
                             }
                         }
                     }
-                    float u0r[FPL], u0i[FPL], u1r[FPL], u1i[FPL];
-#pragma unroll
-                    for (int j = 0; j < FPL; ++j) {
-                        const bool ok = kv[j] && m < nj;
-                        u0r[j] = ok ? u0[j].x : 0.f;
-                        u0i[j] = ok ? u0[j].y : 0.f;
-                        u1r[j] = ok ? u1[j].x : 0.f;
-                        u1i[j] = ok ? u1[j].y : 0.f;
-                    }
                     const uint32_t o = q * kWarps * kRowBytes + soff;
                     uint32_t hi, lo;
                     if (FPL == 1)
-                        split_pair<P>(u0r[0], -u0i[0], hi, lo);
+                        split_pair<P>(u0[0].x, -u0[0].y, hi, lo);
                     else
-                        split_quad_e4m3(u0r[0], -u0i[0], u0r[FPL - 1], -u0i[FPL - 1], hi, lo);
+                        split_quad_e4m3(u0[0].x, -u0[0].y, u0[FPL - 1].x, -u0[FPL - 1].y, hi, lo);
                     *reinterpret_cast<uint32_t *>(st + 0 * kATile + o) = hi;
                     *reinterpret_cast<uint32_t *>(st + 1 * kATile + o) = lo;
                     if (FPL == 1)
-                        split_pair<P>(u1r[0], -u1i[0], hi, lo);
+                        split_pair<P>(u1[0].x, -u1[0].y, hi, lo);
                     else
-                        split_quad_e4m3(u1r[0], -u1i[0], u1r[FPL - 1], -u1i[FPL - 1], hi, lo);
+                        split_quad_e4m3(u1[0].x, -u1[0].y, u1[FPL - 1].x, -u1[FPL - 1].y, hi, lo);
                     *reinterpret_cast<uint32_t *>(st + 2 * kATile + o) = hi;
                     *reinterpret_cast<uint32_t *>(st + 3 * kATile + o) = lo;
                 }
