@@ -324,7 +324,8 @@ int vsaogm_batch_replay(vsaogm_batch *batch, void *stream);
  * steps with reset, so the maps' memories are overwritten) and keeps the
  * fastest: the share of phasors the encode evaluates by polynomial instead
  * of the special-function unit, the encode work per persistent CTA (which
- * sets the chunk size) and the decode work items per SM.  Synchronous.
+ * sets the chunk size), the decode work items per SM and how many points a
+ * map must hold per bundling patch before the finer patches pay.  Synchronous.
  * Drops a captured step (capture again after tuning).  Outputs (nullable):
  * the chosen values.                                                        */
 int vsaogm_batch_autotune(vsaogm_batch *batch, const float *const *xy_dev,

@@ -31,7 +31,9 @@ namespace {
 constexpr int kAuxStreams = 8;
 
 struct Tuning {
-    int poly_warps = 6;       // warps (of 8) evaluating one frequency pair by polynomial
+    int poly_warps = 8;       // warps (of 8) evaluating one frequency pair by polynomial,
+                              // for maps whose phases stay below 4 turns (2 fewer otherwise)
+    int fine_min = 512;       // points per segment that warrant the fine bundling patches
     int items_per_cta = 8;    // encode work items per persistent CTA (sets the chunk size)
     int decode_waves = 2;     // decode items per SM
 };
@@ -175,7 +177,7 @@ int enqueue_step(vsaogm_batch *b, const float *const *xy, const uint8_t *const *
     for (int i = 0; i < M; ++i) {
         vsaogm_map *m = b->maps[i];
         int max_chunks = 0;
-        const PatchDev &pt = choose_patches(m, n[i]);
+        const PatchDev &pt = choose_patches(m, n[i], b->tune.fine_min);
         if (n[i] > 0) {
             if ((rc = batch_sort(m, b->ws[i], pt, xy[i], lab[i], (int)n[i], chunk,
                                  b->aux[i % kAuxStreams], &max_chunks)))
@@ -184,6 +186,8 @@ int enqueue_step(vsaogm_batch *b, const float *const *xy, const uint8_t *const *
         }
         BatchEncodeMap &em = et.m[i];
         batch_encode_entry(m, b->ws[i], pt, &em);
+        em.poly_warps = patches_near(m, pt) ? b->tune.poly_warps
+                                            : std::max(0, b->tune.poly_warps - 2);
         em.item_begin = items;
         items += (long long)max_chunks * em.slices;
         if (n[i] == 0) em.slices = 1;  // no items: max_chunks = 0
@@ -497,7 +501,7 @@ int vsaogm_batch_autotune(vsaogm_batch *b, const float *const *xy, const uint8_t
     Tuning best = b->tune;
     float best_ms = 1e30f;
     // encode shape first (decode fixed), then the decode slicing
-    const int pws[] = {5, 6, 7, 8}, ipcs[] = {4, 8, 16};
+    const int pws[] = {6, 7, 8}, ipcs[] = {4, 8, 16};
     for (int pw : pws)
         for (int ipc : ipcs) {
             if (rc) break;
@@ -515,6 +519,19 @@ int vsaogm_batch_autotune(vsaogm_batch *b, const float *const *xy, const uint8_t
     for (int w : waves) {
         if (rc) break;
         b->tune.decode_waves = w;
+        float ms;
+        if ((rc = time_step(&ms))) break;
+        if (ms < best_ms) {
+            best_ms = ms;
+            best = b->tune;
+        }
+    }
+    b->tune = best;
+    // how dense a map's points must be for the fine bundling patches
+    const int fines[] = {128, 2048};
+    for (int f : fines) {
+        if (rc) break;
+        b->tune.fine_min = f;
         float ms;
         if ((rc = time_step(&ms))) break;
         if (ms < best_ms) {

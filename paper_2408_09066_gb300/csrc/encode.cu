@@ -623,7 +623,7 @@ __global__ void __launch_bounds__(256) encode_batch_kernel(const __grid_constant
         const int c = (int)(local / M.slices), slice = (int)(local % M.slices);
         if (c < *M.n_chunks)
             encode_chunk_x2_body<4, -1, false>(M.pts, M.chunks[c], c, slice, M.nu, M.D,
-                                               M.nu_max_x, M.nu_max_y, tab.poly_warps, M.pt,
+                                               M.nu_max_x, M.nu_max_y, M.poly_warps, M.pt,
                                                M.out, sp, s_bound);
         __syncthreads();  // the staging buffers are reused by the next item
     }
@@ -708,9 +708,7 @@ cudaError_t launch_packed(const vsaogm_map *m, const PatchDev &pt, int np, const
                           bool atomic, cudaStream_t st)
 {
     const int npoly = std::min(m->encode_poly_pairs, np);
-    // every point inside the map lies within half a patch of its patch centre
-    const bool near = m->tile_w / (2.0 * pt.nx) * m->nu_max[0] < 4.0 &&
-                      m->tile_h / (2.0 * pt.ny) * m->nu_max[1] < 4.0;
+    const bool near = patches_near(m, pt);
     const int pw = m->encode_poly_warps >= 0
                        ? m->encode_poly_warps
                        : (np == 4 ? (near ? kAutoPolyWarps4Near : kAutoPolyWarps4) : kAutoPolyWarps2);
@@ -881,11 +879,17 @@ int batch_sort(vsaogm_map *m, Scratch &ws, const PatchDev &pt, const float *xy,
     return sort_stage(m, ws, pt, xy, lab, n, chunk, true, st, max_chunks);
 }
 
-const PatchDev &choose_patches(const vsaogm_map *m, int64_t n)
+const PatchDev &choose_patches(const vsaogm_map *m, int64_t n, int min_per_segment)
 {
     const PatchDev &fine = m->patches[1], &coarse = m->patches[0];
     if (fine.n == coarse.n) return coarse;
-    return n >= (int64_t)512 * m->S * fine.n ? fine : coarse;
+    return n >= (int64_t)min_per_segment * m->S * fine.n ? fine : coarse;
+}
+
+bool patches_near(const vsaogm_map *m, const PatchDev &pt)
+{
+    return m->tile_w / (2.0 * pt.nx) * m->nu_max[0] < 4.0 &&
+           m->tile_h / (2.0 * pt.ny) * m->nu_max[1] < 4.0;
 }
 
 void batch_encode_entry(const vsaogm_map *m, const Scratch &ws, const PatchDev &pt,

@@ -92,6 +92,7 @@ struct BatchEncodeMap {
     int D, slices;
     float nu_max_x, nu_max_y;
     PatchDev pt;
+    int poly_warps;         // this map's warps with one polynomial frequency pair
 };
 struct BatchEncodeTable {
     int n_maps, poly_warps;
@@ -280,7 +281,10 @@ int add_memories(float2 *dst, const float2 *src, int64_t count, cudaStream_t st)
 
 // The patching for a call of n points: the fine one when its segments hold
 // enough points each to pay for their fixed costs, else the coarse one.
-const PatchDev &choose_patches(const vsaogm_map *m, int64_t n);
+const PatchDev &choose_patches(const vsaogm_map *m, int64_t n, int min_per_segment = 512);
+// Whether every point inside the map lies within 4 turns of its patch centre
+// under patching pt (the encode's cheapest phase path).
+bool patches_near(const vsaogm_map *m, const PatchDev &pt);
 
 // batched (many-map) stages, used by batch.cu; `ws` is scratch the batch owns
 // (not the map's), so per-map calls never move memory a captured step uses
