@@ -380,4 +380,6 @@ int add_memories(float2 *dst, const float2 *src, int64_t count, cudaStream_t st)
     return e == cudaSuccess ? VSAOGM_OK : cuda_error(e, "fuse");
 }
 
+VSAOGM_CHECK_TU(decode)
+
 }  // namespace vsaogm_impl

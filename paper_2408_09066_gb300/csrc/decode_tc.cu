@@ -264,7 +264,8 @@ __device__ __forceinline__ void decode_tc_body(
         for (int q = 0; q < kQ; ++q) {
             const int m = warp + kWarps * q;
             dy[q] = m < nj ? row_off[b.j0 + m] : 0.f;
-            tl[q] = m < nj ? min(max(row_tile[b.j0 + m] - by0, 0), nt - 1) : 0;
+            const int t = m < nj ? row_tile[b.j0 + m] - by0 : 0;
+            tl[q] = VSAOGM_IN_BOUNDS(t >= 0 && t < nt) ? t : 0;  // staged memories exist for [0, nt)
             dx[q] = m < ni ? col_off[b.i0 + m] : 0.f;
         }
         const uint32_t soff = (uint32_t)(warp * kRowBytes +
@@ -447,7 +448,9 @@ __device__ __forceinline__ void decode_tc_body(
             for (int cc = ch0; cc < ch1; ++cc) {
                 float v[16];
                 tmem_ld_32x32b_x16(tmem + ((uint32_t)lane_base << 16) + 128u * c + cc * 16, v);
-                if (m < nj) {
+                if (m < nj &&
+                    VSAOGM_IN_BOUNDS(b.j0 + m - og.oy >= 0 && b.j0 + m - og.oy < og.OH &&
+                                     b.i0 - og.ox >= 0 && b.i0 - og.ox + ni <= og.OW)) {
                     float *row = out + (size_t)(b.j0 + m - og.oy) * og.OW + (b.i0 - og.ox);
 #pragma unroll
                     for (int x = 0; x < 16; ++x)
@@ -514,6 +517,8 @@ cudaError_t set_smem_attributes()
 }  // namespace
 
 int tc_stage_freqs(int decode_prec) { return stage_freqs(prec_of(decode_prec)); }
+
+VSAOGM_CHECK_TU(decode_tc)
 
 // Blocks of at most 128 x 128 cells covering region r for the tensor-core
 // decode: columns inside one tile column, rows across at most kMaxBlockTiles

@@ -272,7 +272,7 @@ __global__ void __launch_bounds__(256) seg_scatter_kernel(const float2 *__restri
             const double cy = pt.n > 1 ? (double)pt.cy[patch / pt.nx] : 0.0;
             float dx = (float)((double)p.x - ax.centre[bx] - cx);
             float dy = (float)((double)p.y - ay.centre[by] - cy);
-            sorted[dst] = make_float2(dx, dy);
+            if (VSAOGM_IN_BOUNDS(dst >= 0 && dst < n)) sorted[dst] = make_float2(dx, dy);
         }
     }
 }
@@ -340,7 +340,8 @@ __global__ void __launch_bounds__(256) encode_chunk_kernel(const float2 *__restr
     const int c = blockIdx.x;
     if (c >= *n_chunks) return;
     const int4 ch = chunks[c];
-    const int len = ch.z - ch.y;
+    // a chunk holds at most kMaxChunk points (the staging buffer's size)
+    const int len = VSAOGM_IN_BOUNDS(ch.z >= ch.y && ch.z - ch.y <= kMaxChunk) ? ch.z - ch.y : 0;
     const int kbase = blockIdx.y * (256 * KPT) + threadIdx.x;
     float nx[KPT], ny[KPT], ar[KPT], ai[KPT];
 #pragma unroll
@@ -500,7 +501,8 @@ __device__ __forceinline__ void encode_chunk_x2_body(const float2 *__restrict__ 
                                                      unsigned *s_bound)
 {
     using namespace sm100;
-    const int len = ch.z - ch.y;
+    // a chunk holds at most kMaxChunk points (the staging buffer's size)
+    const int len = VSAOGM_IN_BOUNDS(ch.z >= ch.y && ch.z - ch.y <= kMaxChunk) ? ch.z - ch.y : 0;
     const int kbase = slice * (512 * NP) + threadIdx.x;
     f32x2 nx[NP], ny[NP], ac[NP], as[NP];
 #pragma unroll
@@ -645,7 +647,7 @@ __global__ void __launch_bounds__(256) reduce_batch_kernel(const __grid_constant
     const int k = blockIdx.y * blockDim.x + threadIdx.x;
     if (k >= M.D) return;
     const int c0 = M.cbeg[s * M.patches], c1 = M.cbeg[(s + 1) * M.patches];
-    if (c0 == c1) return;
+    if (c0 == c1 || !VSAOGM_IN_BOUNDS(c0 >= 0 && c1 > c0)) return;
     float sr = 0.f, si = 0.f;
     for (int c = c0; c < c1; ++c) {
         float2 v = M.partial[(size_t)c * M.D + k];
@@ -667,7 +669,7 @@ __global__ void __launch_bounds__(256) reduce_partials_kernel(const float2 *__re
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= D) return;
     const int c0 = cbeg[s * patches], c1 = cbeg[(s + 1) * patches];
-    if (c0 == c1) return;
+    if (c0 == c1 || !VSAOGM_IN_BOUNDS(c0 >= 0 && c1 > c0)) return;
     float sr = 0.f, si = 0.f;
     for (int c = c0; c < c1; ++c) {
         float2 v = partial[(size_t)c * D + k];
@@ -1103,6 +1105,8 @@ static int encode_bundle_noalloc(vsaogm_map *m, const float *xy_f, const uint8_t
     if (e != cudaSuccess) return cuda_error(e, "encode_noalloc");
     return VSAOGM_OK;
 }
+
+VSAOGM_CHECK_TU(encode)
 
 }  // namespace vsaogm_impl
 

@@ -146,6 +146,7 @@ __device__ __forceinline__ void entropy_body(const float *__restrict__ heat, int
         float pr1 = __fdividef(1.0f, 1.0f + __expf(Hc[0] - Hc[1]));
         float pr0 = __fdividef(1.0f, 1.0f + __expf(Hc[1] - Hc[0]));
         size_t o = (size_t)y * ww + x;
+        if (!VSAOGM_IN_BOUNDS(o < (size_t)ww * wh)) continue;
         occ[o] = pr1;
         float d = pr1 - pr0;
         if (ogm) ogm[o] = d;
@@ -272,6 +273,7 @@ __device__ __forceinline__ void entropy_fixed_body(const float *__restrict__ hea
         const float pr1 = __fdividef(1.0f, 1.0f + __expf(Hc[0] - Hc[1]));
         const float pr0 = __fdividef(1.0f, 1.0f + __expf(Hc[1] - Hc[0]));
         const size_t o = (size_t)y * ww + x;
+        if (!VSAOGM_IN_BOUNDS(o < (size_t)ww * wh)) continue;
         occ[o] = pr1;
         const float d = pr1 - pr0;
         if (ogm) ogm[o] = d;
@@ -431,5 +433,7 @@ int entropy(vsaogm_map *m, const float *heat, Region r, Region win, bool raw_inp
     sc.end(1);
     return VSAOGM_OK;
 }
+
+VSAOGM_CHECK_TU(entropy)
 
 }  // namespace vsaogm_impl

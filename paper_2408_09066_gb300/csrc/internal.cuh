@@ -13,6 +13,40 @@
 
 namespace vsaogm_impl {
 
+// Bounds checks of the checked build (compiled with -DVSAOGM_CHECK): an access
+// whose index is out of range is skipped, and the first offending source line
+// is recorded in a device flag of its translation unit, which vsaogm_status
+// reports as VSAOGM_E_DATA.  Guards only ever skip an access, never a barrier,
+// so a failed check cannot stall a CTA.  In the normal build they vanish.
+#ifdef VSAOGM_CHECK
+static __device__ int g_check_line;
+__device__ __forceinline__ bool check_bounds(bool ok, int line)
+{
+    if (!ok) atomicCAS(&g_check_line, 0, line);
+    return ok;
+}
+#define VSAOGM_IN_BOUNDS(cond) (::vsaogm_impl::check_bounds((cond), __LINE__))
+#define VSAOGM_CHECK_TU(name)                                                       \
+    int take_check_line_##name()                                                    \
+    {                                                                               \
+        int line = 0, zero = 0;                                                     \
+        if (cudaMemcpyFromSymbol(&line, g_check_line, sizeof(int)) != cudaSuccess) \
+            return -1;                                                              \
+        if (line) cudaMemcpyToSymbol(g_check_line, &zero, sizeof(int));             \
+        return line;                                                                \
+    }
+#else
+#define VSAOGM_IN_BOUNDS(cond) true
+#define VSAOGM_CHECK_TU(name) \
+    int take_check_line_##name() { return 0; }
+#endif
+// first out-of-range source line recorded by each translation unit since the
+// last call (0: none; always 0 in the normal build)
+int take_check_line_encode();
+int take_check_line_decode();
+int take_check_line_decode_tc();
+int take_check_line_entropy();
+
 constexpr int kMaxTiles = 1024;      // tiles_x * tiles_y
 constexpr int kMaxRadius = 16;       // disk radius in cells
 constexpr int kSortBlock = 2048;     // points per block of the counting sort

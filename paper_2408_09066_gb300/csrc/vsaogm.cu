@@ -593,8 +593,22 @@ int vsaogm_status(vsaogm_map *m, void *stream)
     VSA_CUDA(cudaStreamSynchronize(st), "status");
     if (code != 0) {
         VSA_CUDA(cudaMemset(m->status, 0, sizeof(int)), "status");
+        if (code == VSAOGM_E_INVAL)
+            return set_error(code, "the tensor-core decode refused an ill-formed block");
         return set_error(code, "a kernel gave up on a bounded wait (tensor-core decode)");
     }
+    // the checked build's bounds records (always 0 in the normal build)
+    const struct {
+        const char *tu;
+        int line;
+    } checks[] = {{"encode.cu", take_check_line_encode()},
+                  {"decode.cu", take_check_line_decode()},
+                  {"decode_tc.cu", take_check_line_decode_tc()},
+                  {"entropy.cu", take_check_line_entropy()}};
+    for (const auto &c : checks)
+        if (c.line != 0)
+            return set_error(VSAOGM_E_DATA, "checked build: index out of range at %s:%d (access skipped)",
+                             c.tu, c.line);
     return VSAOGM_OK;
 }
 

@@ -13,7 +13,9 @@ import threading
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libvsaogm.so")
+# VSAOGM_CHECKED=1 loads the bounds-checked build (build.py --checked) instead
+LIB_PATH = os.path.join(_HERE, "libvsaogm_checked.so" if os.environ.get("VSAOGM_CHECKED") == "1"
+                        else "libvsaogm.so")
 
 STAGES = ("sort", "encode", "reduce", "norms", "decode", "nonlinear", "entropy")
 OK, E_INVAL, E_NOMEM, E_CUDA, E_TIMEOUT, E_DATA = 0, -1, -2, -3, -4, -5

@@ -64,6 +64,9 @@ def run_gpu(cfg: V.Config, xy: np.ndarray, labels: np.ndarray, calls: int = 1):
         out = dict(omega=omega.cpu().numpy(), P=heat_raw.cpu().numpy(), Phat=heat.cpu().numpy(),
                    occ=occ.cpu().numpy(), occ_query=occ_q.cpu().numpy(), ogm=ogm.cpu().numpy(),
                    cls=cls.cpu().numpy(), nu=nu, rejected=m.rejected())
+        # NaN / Inf scan of every floating output
+        for k in ("omega", "P", "Phat", "occ", "occ_query", "ogm"):
+            assert np.all(np.isfinite(out[k])), f"non-finite values in {k}"
     finally:
         m.close()
     return out

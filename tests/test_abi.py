@@ -104,3 +104,12 @@ def test_batch_create_rejects_bad_arguments_before_touching_the_gpu(L):
     assert not h.value
     assert L.vsaogm_batch_destroy(None) == V.OK
     assert L.vsaogm_batch_replay(None, None) == V.E_INVAL
+
+
+def test_bounds_checked_build_compiles_and_exports_the_same_symbols():
+    """The checked variant (the library's sanitizer stand-in) builds for sm_103a
+    and exports every declared entry point."""
+    lib = build_mod.build(checked=True)
+    L2 = ctypes.CDLL(lib)
+    missing = [n for n in _declared_functions() if not hasattr(L2, n)]
+    assert not missing, missing

@@ -67,9 +67,13 @@ class _Run:
         import torch
         torch.cuda.synchronize()
         self.batch.status()
-        return [dict(omega=m.get_memory().cpu().numpy(), P=h.cpu().numpy(), occ=o.cpu().numpy(),
-                     ogm=g.cpu().numpy())
-                for m, h, o, g in zip(self.maps, self.heat, self.occ, self.ogm)]
+        out = [dict(omega=m.get_memory().cpu().numpy(), P=h.cpu().numpy(), occ=o.cpu().numpy(),
+                    ogm=g.cpu().numpy())
+               for m, h, o, g in zip(self.maps, self.heat, self.occ, self.ogm)]
+        for d in out:  # NaN / Inf scan
+            for k, v in d.items():
+                assert np.all(np.isfinite(v)), f"non-finite values in {k}"
+        return out
 
     def close(self):
         self.batch.close()
