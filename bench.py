@@ -570,8 +570,8 @@ def batch_config(wls, tune=None) -> dict:
             "grid_range": [min(w.W for w in wls), max(w.W for w in wls)],
             "D_values": sorted({w.D for w in wls}),
             "tiles_total": sum(w.tiles_x * w.tiles_y for w in wls), "decode": "bf16x3",
-            "launch": "one CUDA graph per step: per-map sorts on 8 streams, then one launch "
-                      "per stage for all maps", "autotuned": tune,
+            "launch": "one CUDA graph per step: one launch per stage (four for the sort) "
+                      "for all maps", "autotuned": tune,
             "l2": "flushed between timed steps (256 MB device write outside the step events)",
             "parallelism": "one independent 64-map batch per GPU"}
 

@@ -287,8 +287,8 @@ int vsaogm_stage_times(vsaogm_map *map, double *ms, int64_t *launches, int reset
 typedef struct vsaogm_batch vsaogm_batch;
 
 /* Creates a batch over maps[0..count-1] (1 <= count <= VSAOGM_MAX_BATCH,
- * distinct maps).  Allocates a few small device buffers and 8 streams used
- * for the per-map sorts.                                                   */
+ * distinct maps).  Allocates a few small device buffers; per-map scratch
+ * grows on the first step.                                                 */
 int vsaogm_batch_create(vsaogm_map *const *maps, int32_t count, vsaogm_batch **out);
 
 /* Frees the batch (synchronises the device); the maps stay.  NULL is a no-op. */

@@ -4,8 +4,8 @@
 //
 // Stages of a step:
 //   reset (optional)  : memset of each map's memories
-//   sort              : per map, on parallel branches (aux streams): tile
-//                       assignment + counting sort (4 small kernels per map)
+//   sort              : tile assignment + counting sort of every map, four
+//                       launches (count, scan, chunk table, scatter)
 //   encode            : ONE persistent launch over every map's (chunk,
 //                       frequency slice) items, claimed from an atomic counter
 //   reduce            : ONE launch, fixed-order chunk sums of every segment
@@ -28,7 +28,6 @@ static_assert(vsaogm_impl::kMaxBatchMaps == VSAOGM_MAX_BATCH, "batch size limit"
 using namespace vsaogm_impl;
 
 namespace {
-constexpr int kAuxStreams = 8;
 
 struct Tuning {
     int poly_warps = 8;       // warps (of 8) evaluating one frequency pair by polynomial,
@@ -50,8 +49,6 @@ struct vsaogm_batch {
     int n_items = 0, items_cap = 0;
     int decode_waves_built = -1;
     std::vector<int> splits;                    // decode slices per map
-    cudaStream_t aux[kAuxStreams] = {};
-    cudaEvent_t fork = nullptr, join[kAuxStreams] = {};
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     long long graph_launches[VSAOGM_N_STAGES] = {};  // kernels of the captured step
@@ -162,27 +159,30 @@ int enqueue_step(vsaogm_batch *b, const float *const *xy, const uint8_t *const *
             if ((e = cudaMemsetAsync(m->omega, 0, sizeof(float2) * (size_t)m->S * m->cfg.D, st)) !=
                 cudaSuccess)
                 return cuda_error(e, "batch reset");
-    // ---- encode: per-map sorts on parallel branches, then one launch
+    // ---- encode: the sorts of every map (four launches), then one launch
     const int chunk = batch_chunk(b, n);
-    if ((e = cudaEventRecord(b->fork, st)) != cudaSuccess) return cuda_error(e, "batch fork");
-    for (int a = 0; a < kAuxStreams; ++a)
-        if ((e = cudaStreamWaitEvent(b->aux[a], b->fork, 0)) != cudaSuccess)
-            return cuda_error(e, "batch fork");
+    BatchSortTable sot;
+    memset(&sot, 0, sizeof(sot));
     BatchEncodeTable et;
     memset(&et, 0, sizeof(et));
     BatchReduceTable rt;
     memset(&rt, 0, sizeof(rt));
     long long items = 0;
-    int segs = 0, d_max = 0;
+    int segs = 0, d_max = 0, sort_blocks = 0, sort_segs = 0, max_s1 = 0;
     for (int i = 0; i < M; ++i) {
         vsaogm_map *m = b->maps[i];
         int max_chunks = 0;
         const PatchDev &pt = choose_patches(m, n[i], b->tune.fine_min);
         if (n[i] > 0) {
-            if ((rc = batch_sort(m, b->ws[i], pt, xy[i], lab[i], (int)n[i], chunk,
-                                 b->aux[i % kAuxStreams], &max_chunks)))
+            BatchSortMap &sm = sot.m[sot.n_maps++];
+            if ((rc = batch_sort_entry(m, b->ws[i], pt, xy[i], lab[i], (int)n[i], chunk, &sm,
+                                       &max_chunks)))
                 return rc;
-            counted[VSAOGM_STAGE_SORT] += 4;
+            sm.blk_begin = sort_blocks;
+            sm.seg_begin = sort_segs;
+            sort_blocks += sm.nb;
+            sort_segs += sm.S + 1;
+            max_s1 = std::max(max_s1, sm.S + 1);
         }
         BatchEncodeMap &em = et.m[i];
         batch_encode_entry(m, b->ws[i], pt, &em);
@@ -196,11 +196,9 @@ int enqueue_step(vsaogm_batch *b, const float *const *xy, const uint8_t *const *
         segs += n[i] > 0 ? m->S : 0;
         d_max = std::max(d_max, m->cfg.D);
     }
-    for (int a = 0; a < kAuxStreams; ++a) {
-        if ((e = cudaEventRecord(b->join[a], b->aux[a])) != cudaSuccess)
-            return cuda_error(e, "batch join");
-        if ((e = cudaStreamWaitEvent(st, b->join[a], 0)) != cudaSuccess)
-            return cuda_error(e, "batch join");
+    if (sot.n_maps > 0) {
+        if ((rc = launch_sort_batch(sot, sort_blocks, sort_segs, max_s1, st))) return rc;
+        counted[VSAOGM_STAGE_SORT] = 4;
     }
     mark();
     et.n_maps = M;
@@ -365,11 +363,6 @@ int vsaogm_batch_create(vsaogm_map *const *maps, int32_t count, vsaogm_batch **o
     b->decode_prec = maps[0]->cfg.decode_prec;
     b->enc_ctas = encode_batch_ctas();
     cudaError_t e = cudaMalloc((void **)&b->counter, sizeof(unsigned long long));
-    for (int a = 0; a < kAuxStreams && e == cudaSuccess; ++a) {
-        e = cudaStreamCreateWithFlags(&b->aux[a], cudaStreamNonBlocking);
-        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->join[a], cudaEventDisableTiming);
-    }
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
     if (e != cudaSuccess) {
         int rc = cuda_error(e, "batch create");
         vsaogm_batch_destroy(b);
@@ -387,11 +380,6 @@ int vsaogm_batch_destroy(vsaogm_batch *b)
     if (b->counter) cudaFree(b->counter);
     if (b->items) cudaFree(b->items);
     for (Scratch &w : b->ws) free_scratch(w);
-    for (int a = 0; a < kAuxStreams; ++a) {
-        if (b->aux[a]) cudaStreamDestroy(b->aux[a]);
-        if (b->join[a]) cudaEventDestroy(b->join[a]);
-    }
-    if (b->fork) cudaEventDestroy(b->fork);
     for (cudaEvent_t e : b->free_events) cudaEventDestroy(e);
     for (auto &p : b->pending)
         for (cudaEvent_t e : p) cudaEventDestroy(e);

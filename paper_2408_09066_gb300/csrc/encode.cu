@@ -120,18 +120,18 @@ __device__ int block_exclusive_scan(int v, int *total)
     return before;
 }
 
-// 1. Per-block histogram over segments 0..S (S = rejected).
-__global__ void __launch_bounds__(256) seg_count_kernel(const float2 *__restrict__ xy,
-                                                        const uint8_t *__restrict__ lab, int n,
-                                                        AxisDev ax, AxisDev ay, PatchDev pt,
-                                                        int S, int *__restrict__ hist)
+// 1. Per-block histogram over segments 0..S (S = rejected) of sort block blk.
+__device__ __forceinline__ void seg_count_body(const float2 *__restrict__ xy,
+                                               const uint8_t *__restrict__ lab, int n,
+                                               const AxisDev &ax, const AxisDev &ay,
+                                               const PatchDev &pt, int S, int *__restrict__ hist,
+                                               int blk, int *cnt)
 {
-    extern __shared__ int cnt[];  // [S + 1]
     const int S1 = S + 1;
     for (int s = threadIdx.x; s < S1; s += blockDim.x) cnt[s] = 0;
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int base = blockIdx.x * kSortBlock + warp * (kSortBlock / kSortWarps);
+    const int base = blk * kSortBlock + warp * (kSortBlock / kSortWarps);
     for (int r = 0; r < kSortBlock / kSortWarps / 32; ++r) {
         int i = base + r * 32 + lane;
         int seg = -1;
@@ -143,15 +143,23 @@ __global__ void __launch_bounds__(256) seg_count_kernel(const float2 *__restrict
         if (seg >= 0 && lane == __ffs(peers) - 1) atomicAdd(&cnt[seg], __popc(peers));
     }
     __syncthreads();
-    for (int s = threadIdx.x; s < S1; s += blockDim.x) hist[(size_t)blockIdx.x * S1 + s] = cnt[s];
+    for (int s = threadIdx.x; s < S1; s += blockDim.x) hist[(size_t)blk * S1 + s] = cnt[s];
+}
+
+__global__ void __launch_bounds__(256) seg_count_kernel(const float2 *__restrict__ xy,
+                                                        const uint8_t *__restrict__ lab, int n,
+                                                        AxisDev ax, AxisDev ay, PatchDev pt,
+                                                        int S, int *__restrict__ hist)
+{
+    extern __shared__ int cnt[];  // [S + 1]
+    seg_count_body(xy, lab, n, ax, ay, pt, S, hist, blockIdx.x, cnt);
 }
 
 // 2. Column s of hist [nb][S1] -> exclusive prefix over blocks (in place);
 //    total[s] = column sum.
-__global__ void __launch_bounds__(kScanThreads) seg_scan_kernel(int *__restrict__ hist, int nb,
-                                                                int S1, int *__restrict__ total)
+__device__ __forceinline__ void seg_scan_body(int *__restrict__ hist, int nb, int S1,
+                                              int *__restrict__ total, int s)
 {
-    const int s = blockIdx.x;
     int carry = 0;
     for (int b0 = 0; b0 < nb; b0 += kScanThreads) {
         int b = b0 + threadIdx.x;
@@ -164,12 +172,17 @@ __global__ void __launch_bounds__(kScanThreads) seg_scan_kernel(int *__restrict_
     if (threadIdx.x == 0) total[s] = carry;
 }
 
+__global__ void __launch_bounds__(kScanThreads) seg_scan_kernel(int *__restrict__ hist, int nb,
+                                                                int S1, int *__restrict__ total)
+{
+    seg_scan_body(hist, nb, S1, total, blockIdx.x);
+}
+
 // 3. Segment bases, chunk table, rejected count.  One CTA.
 //    meta layout: total[S1] | base[S1 + 1] | chunk_begin[S + 1] | n_chunks[1]
-__global__ void __launch_bounds__(kScanThreads) seg_meta_kernel(int *__restrict__ meta, int S,
-                                                                int chunk,
-                                                                int4 *__restrict__ chunks,
-                                                                unsigned long long *rejected)
+__device__ __forceinline__ void seg_meta_body(int *__restrict__ meta, int S, int chunk,
+                                              int4 *__restrict__ chunks,
+                                              unsigned long long *rejected)
 {
     const int S1 = S + 1;
     int *total = meta, *base = meta + S1, *cbeg = base + S1 + 1, *nch_out = cbeg + S + 1;
@@ -207,21 +220,30 @@ __global__ void __launch_bounds__(kScanThreads) seg_meta_kernel(int *__restrict_
     }
 }
 
-// 4. Stable scatter into segment order, tile-centred coordinates.
-__global__ void __launch_bounds__(256) seg_scatter_kernel(const float2 *__restrict__ xy,
-                                                          const uint8_t *__restrict__ lab, int n,
-                                                          AxisDev ax, AxisDev ay, PatchDev pt,
-                                                          int S, const int *__restrict__ blk_off,
-                                                          const int *__restrict__ meta,
-                                                          float2 *__restrict__ sorted)
+__global__ void __launch_bounds__(kScanThreads) seg_meta_kernel(int *__restrict__ meta, int S,
+                                                                int chunk,
+                                                                int4 *__restrict__ chunks,
+                                                                unsigned long long *rejected)
 {
-    extern __shared__ int wcnt[];  // [kSortWarps][S1]: counts, then running cursors
+    seg_meta_body(meta, S, chunk, chunks, rejected);
+}
+
+// 4. Stable scatter into segment order, tile-centred coordinates.
+__device__ __forceinline__ void seg_scatter_body(const float2 *__restrict__ xy,
+                                                 const uint8_t *__restrict__ lab, int n,
+                                                 const AxisDev &ax, const AxisDev &ay,
+                                                 const PatchDev &pt, int S,
+                                                 const int *__restrict__ blk_off,
+                                                 const int *__restrict__ meta,
+                                                 float2 *__restrict__ sorted, int blk, int *wcnt)
+{
+    // wcnt: [kSortWarps][S1]: counts, then running cursors
     const int S1 = S + 1;
     const int *seg_base = meta + S1;
     for (int s = threadIdx.x; s < kSortWarps * S1; s += blockDim.x) wcnt[s] = 0;
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int base = blockIdx.x * kSortBlock + warp * (kSortBlock / kSortWarps);
+    const int base = blk * kSortBlock + warp * (kSortBlock / kSortWarps);
     const int rounds = kSortBlock / kSortWarps / 32;
     int *mine = wcnt + warp * S1;
     // pass 1: per-warp counts (only this warp touches its row)
@@ -239,7 +261,7 @@ __global__ void __launch_bounds__(256) seg_scatter_kernel(const float2 *__restri
     __syncthreads();
     // cursors: global position of each warp's first point of each segment
     for (int s = threadIdx.x; s < S1; s += blockDim.x) {
-        int run = seg_base[s] + blk_off[(size_t)blockIdx.x * S1 + s];
+        int run = seg_base[s] + blk_off[(size_t)blk * S1 + s];
         for (int w = 0; w < kSortWarps; ++w) {
             int c = wcnt[w * S1 + s];
             wcnt[w * S1 + s] = run;
@@ -275,6 +297,58 @@ __global__ void __launch_bounds__(256) seg_scatter_kernel(const float2 *__restri
             if (VSAOGM_IN_BOUNDS(dst >= 0 && dst < n)) sorted[dst] = make_float2(dx, dy);
         }
     }
+}
+
+__global__ void __launch_bounds__(256) seg_scatter_kernel(const float2 *__restrict__ xy,
+                                                          const uint8_t *__restrict__ lab, int n,
+                                                          AxisDev ax, AxisDev ay, PatchDev pt,
+                                                          int S, const int *__restrict__ blk_off,
+                                                          const int *__restrict__ meta,
+                                                          float2 *__restrict__ sorted)
+{
+    extern __shared__ int wcnt[];
+    seg_scatter_body(xy, lab, n, ax, ay, pt, S, blk_off, meta, sorted, blockIdx.x, wcnt);
+}
+
+// 1'-4'. The four sort kernels over every map of a batch, one launch each:
+//        CTA q finds its map by binary search over each map's first CTA.
+__device__ __forceinline__ int batch_sort_map(const BatchSortTable &tab, int q, bool by_segment)
+{
+    int lo = 0, hi = tab.n_maps - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        const int first = by_segment ? tab.m[mid].seg_begin : tab.m[mid].blk_begin;
+        if (first <= q) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+__global__ void __launch_bounds__(256) batch_seg_count_kernel(const __grid_constant__ BatchSortTable tab)
+{
+    extern __shared__ int cnt[];
+    const BatchSortMap &M = tab.m[batch_sort_map(tab, blockIdx.x, false)];
+    seg_count_body(M.xy, M.lab, M.n, M.ax, M.ay, M.pt, M.S, M.hist, blockIdx.x - M.blk_begin,
+                   cnt);
+}
+
+__global__ void __launch_bounds__(kScanThreads) batch_seg_scan_kernel(const __grid_constant__ BatchSortTable tab)
+{
+    const BatchSortMap &M = tab.m[batch_sort_map(tab, blockIdx.x, true)];
+    seg_scan_body(M.hist, M.nb, M.S + 1, M.meta, blockIdx.x - M.seg_begin);
+}
+
+__global__ void __launch_bounds__(kScanThreads) batch_seg_meta_kernel(const __grid_constant__ BatchSortTable tab)
+{
+    const BatchSortMap &M = tab.m[blockIdx.x];
+    seg_meta_body(M.meta, M.S, M.chunk, M.chunks, M.rejected);
+}
+
+__global__ void __launch_bounds__(256) batch_seg_scatter_kernel(const __grid_constant__ BatchSortTable tab)
+{
+    extern __shared__ int wcnt[];
+    const BatchSortMap &M = tab.m[batch_sort_map(tab, blockIdx.x, false)];
+    seg_scatter_body(M.xy, M.lab, M.n, M.ax, M.ay, M.pt, M.S, M.hist, M.meta, M.sorted,
+                     blockIdx.x - M.blk_begin, wcnt);
 }
 
 // 5. Encode + bundle one chunk of one segment over a slice of 256*KPT
@@ -875,10 +949,52 @@ static int sort_stage(vsaogm_map *m, Scratch &ws, const PatchDev &pt, const floa
     return VSAOGM_OK;
 }
 
-int batch_sort(vsaogm_map *m, Scratch &ws, const PatchDev &pt, const float *xy,
-               const uint8_t *lab, int n, int chunk, cudaStream_t st, int *max_chunks)
+int batch_sort_entry(vsaogm_map *m, Scratch &ws, const PatchDev &pt, const float *xy,
+                     const uint8_t *lab, int n, int chunk, BatchSortMap *e, int *max_chunks)
 {
-    return sort_stage(m, ws, pt, xy, lab, n, chunk, true, st, max_chunks);
+    const int S = m->S * pt.n, S1 = S + 1, D = m->cfg.D;
+    const int nb = (n + kSortBlock - 1) / kSortBlock;
+    *max_chunks = (n + chunk - 1) / chunk + S;
+    int rc;
+    if ((rc = ensure(ws.blk_hist, sizeof(int) * (size_t)nb * S1))) return rc;
+    if ((rc = ensure(ws.seg_meta, sizeof(int) * (size_t)(3 * S1 + 2)))) return rc;
+    if ((rc = ensure(ws.chunks, sizeof(int4) * (size_t)*max_chunks))) return rc;
+    if ((rc = ensure(ws.sorted, sizeof(float2) * (size_t)n))) return rc;
+    if ((rc = ensure(ws.partial, sizeof(float2) * (size_t)*max_chunks * D))) return rc;
+    e->xy = (const float2 *)xy;
+    e->lab = lab;
+    e->n = n;
+    e->S = S;
+    e->chunk = chunk;
+    e->ax = axis_x(m);
+    e->ay = axis_y(m);
+    e->pt = pt;
+    e->hist = (int *)ws.blk_hist.ptr;
+    e->meta = (int *)ws.seg_meta.ptr;
+    e->chunks = (int4 *)ws.chunks.ptr;
+    e->sorted = (float2 *)ws.sorted.ptr;
+    e->rejected = m->rejected;
+    e->nb = nb;
+    return VSAOGM_OK;
+}
+
+int launch_sort_batch(const BatchSortTable &tab, int blocks, int segs, int max_s1,
+                      cudaStream_t st)
+{
+    if (tab.n_maps <= 0 || blocks <= 0) return VSAOGM_OK;
+    const size_t smem_count = sizeof(int) * max_s1;
+    const size_t smem_scatter = sizeof(int) * kSortWarps * max_s1;
+    cudaError_t e;
+    if ((e = cudaFuncSetAttribute(batch_seg_scatter_kernel,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)smem_scatter)) != cudaSuccess)
+        return cuda_error(e, "batch sort: shared memory");
+    batch_seg_count_kernel<<<blocks, 256, smem_count, st>>>(tab);
+    batch_seg_scan_kernel<<<segs, kScanThreads, 0, st>>>(tab);
+    batch_seg_meta_kernel<<<tab.n_maps, kScanThreads, 0, st>>>(tab);
+    batch_seg_scatter_kernel<<<blocks, 256, smem_scatter, st>>>(tab);
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_error(e, "batch sort");
+    return VSAOGM_OK;
 }
 
 const PatchDev &choose_patches(const vsaogm_map *m, int64_t n, int min_per_segment)

@@ -116,6 +116,24 @@ struct OutGeom {
 
 // Tables of the batched (many-map) kernels, passed as __grid_constant__ params.
 constexpr int kMaxBatchMaps = 64;
+struct BatchSortMap {
+    const float2 *xy;       // points of this map's step
+    const uint8_t *lab;
+    int n, S, chunk;        // points, segments (memories x patches), chunk length
+    AxisDev ax, ay;
+    PatchDev pt;
+    int *hist;              // [nb][S + 1]
+    int *meta;              // seg_meta layout of Scratch
+    int4 *chunks;
+    float2 *sorted;
+    unsigned long long *rejected;
+    int nb, blk_begin;      // sort blocks of this map, its first in the launch
+    int seg_begin;          // first scan CTA (segment column) of this map
+};
+struct BatchSortTable {
+    int n_maps;
+    BatchSortMap m[kMaxBatchMaps];
+};
 struct BatchEncodeMap {
     const float2 *pts;      // sorted tile-centred points
     const int4 *chunks;     // chunk table
@@ -322,8 +340,14 @@ bool patches_near(const vsaogm_map *m, const PatchDev &pt);
 
 // batched (many-map) stages, used by batch.cu; `ws` is scratch the batch owns
 // (not the map's), so per-map calls never move memory a captured step uses
-int batch_sort(vsaogm_map *m, Scratch &ws, const PatchDev &pt, const float *xy,
-               const uint8_t *lab, int n, int chunk, cudaStream_t st, int *max_chunks);
+// sizes map m's sort scratch in ws for n points and fills its sort entry
+// (blk_begin and seg_begin are left to the caller)
+int batch_sort_entry(vsaogm_map *m, Scratch &ws, const PatchDev &pt, const float *xy,
+                     const uint8_t *lab, int n, int chunk, BatchSortMap *e, int *max_chunks);
+// the four sort kernels over every entry, one launch each; blocks = sum of nb,
+// segs = sum of S + 1, max_s1 = the largest S + 1
+int launch_sort_batch(const BatchSortTable &tab, int blocks, int segs, int max_s1,
+                      cudaStream_t st);
 void batch_encode_entry(const vsaogm_map *m, const Scratch &ws, const PatchDev &pt,
                         BatchEncodeMap *e);
 void batch_reduce_entry(const vsaogm_map *m, const Scratch &ws, const PatchDev &pt,
