@@ -249,9 +249,9 @@ int enqueue_step(vsaogm_batch *b, const float *const *xy, const uint8_t *const *
         const int kps = ((D + s - 1) / s + KS - 1) / KS * KS;
         const float u = tc_u_scale(m);
         dt.m[i] = BatchDecodeMap{m->omega, m->inv_norm, m->nu, m->col_off, m->row_off,
-                                 m->row_tile, (float *)b->ws[i].dec_partial.ptr, m->status, D,
-                                 kps, m->cfg.grid_w, m->cfg.grid_h, m->cfg.tiles_x, u,
-                                 m->cfg.resolution};
+                                 m->tc_rot, m->row_tile, (float *)b->ws[i].dec_partial.ptr,
+                                 m->status, D, kps, m->cfg.grid_w, m->cfg.grid_h,
+                                 m->cfg.tiles_x, u};
         BatchMapOut &o = ot.m[i];
         o.partial = (const float *)b->ws[i].dec_partial.ptr;
         o.heat = heat[i];

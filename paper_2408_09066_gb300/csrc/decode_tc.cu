@@ -174,8 +174,8 @@ __device__ __forceinline__ void decode_tc_body(
     const DecodeBlock b, const int split, const float2 *__restrict__ omega,
     const float *__restrict__ inv_norm, const float *__restrict__ nu, int D, int tiles_x,
     const int *__restrict__ row_tile, OutGeom og, const float *__restrict__ col_off,
-    const float *__restrict__ row_off, float res, int k_per_split, int N, float u_scale,
-    float *__restrict__ partial, int *__restrict__ status)
+    const float *__restrict__ row_off, const float2 *__restrict__ rot, int k_per_split, int N,
+    float u_scale, float *__restrict__ partial, int *__restrict__ status)
 {
     constexpr int KS = stage_freqs(P);       // frequencies per stage
     constexpr int FPL = KS / 32;             // frequencies per producer lane
@@ -285,6 +285,7 @@ __device__ __forceinline__ void decode_tc_body(
         }
         // prefetch registers: this lane's frequencies and staged memory entries
         float pnx[FPL], pny[FPL];
+        float2 prx[FPL], pry[FPL];  // the 16-cell step phasors along x and y
         float2 pw[kWPerThread];
         auto prefetch = [&](int s) {
 #pragma unroll
@@ -292,6 +293,8 @@ __device__ __forceinline__ void decode_tc_body(
                 const int k = k_begin + s * KS + FPL * lane + j;
                 pnx[j] = k < k_end ? nu[k] : 0.f;
                 pny[j] = k < k_end ? nu[D + k] : 0.f;
+                prx[j] = k < k_end ? rot[k] : make_float2(1.f, 0.f);
+                pry[j] = k < k_end ? rot[D + k] : make_float2(1.f, 0.f);
             }
 #pragma unroll
             for (int r = 0; r < kWPerThread; ++r) {
@@ -311,20 +314,25 @@ __device__ __forceinline__ void decode_tc_body(
                         make_float2(pw[r].x * w_scale[r], pw[r].y * w_scale[r]);
         };
 #pragma unroll
-        for (int j = 0; j < FPL; ++j) pnx[j] = pny[j] = 0.f;
+        for (int j = 0; j < FPL; ++j) {
+            pnx[j] = pny[j] = 0.f;
+            prx[j] = pry[j] = make_float2(1.f, 0.f);
+        }
         if (n_stages > 0) {
             prefetch(0);
             stage_w(0);
         }
         float nux[FPL], nuy[FPL];
+        float2 rsx[FPL], rsy[FPL];
 #pragma unroll
         for (int j = 0; j < FPL; ++j) {
             nux[j] = pnx[j];
             nuy[j] = pny[j];
+            rsx[j] = prx[j];
+            rsy[j] = pry[j];
         }
         named_bar_sync(1, kProducers);
         uint32_t phase_bits = 0u;  // bit b: parity to wait for on empty_bar[b]
-        const float step_d = kWarps * res;  // offset between a thread's consecutive rows / columns
 
         for (int s = 0; s < n_stages; ++s) {
             const int buf = s & 1;
@@ -347,7 +355,7 @@ __device__ __forceinline__ void decode_tc_body(
                 float2 rot[FPL], a[FPL];
 #pragma unroll
                 for (int j = 0; j < FPL; ++j) {
-                    rot[j] = phasor(nux[j], step_d);
+                    rot[j] = rsx[j];
                     a[j] = phasor(nux[j], dx[0]);
                 }
 #pragma unroll
@@ -385,7 +393,7 @@ __device__ __forceinline__ void decode_tc_body(
                     }
                 };
 #pragma unroll
-                for (int j = 0; j < FPL; ++j) rot[j] = phasor(nuy[j], step_d);
+                for (int j = 0; j < FPL; ++j) rot[j] = rsy[j];
                 start_row(0);
 #pragma unroll
                 for (int q = 0; q < kQ; ++q) {
@@ -428,14 +436,18 @@ __device__ __forceinline__ void decode_tc_body(
                 for (int j = 0; j < FPL; ++j) {
                     nux[j] = pnx[j];
                     nuy[j] = pny[j];
+                    rsx[j] = prx[j];
+                    rsy[j] = pry[j];
                 }
             }
             named_bar_sync(1, kProducers);
         }
     }
     // epilogue (producers): warp w reads TMEM lanes 32 (w & 3) .. + 31 (its lane
-    // quarter), class (w >> 2) & 1, and one half of the 16-column chunks (w >> 3);
-    // always drain (bounded), even after a time-out: tensor memory is freed below
+    // quarter), class (w >> 2) & 1, and one half of the 16-column chunks (w >> 3),
+    // one row per lane; the rows go through shared memory (free once every MMA
+    // has finished) so that each store writes 32 consecutive cells of a row.
+    // Always drain (bounded), even after a time-out: tensor memory is freed below.
     if (!mbar_wait(&done_bar, 0u, kWaitNs)) atomicExch(&abort_s, 1);
     tc_fence_after_sync();
     __syncthreads();
@@ -445,16 +457,23 @@ __device__ __forceinline__ void decode_tc_body(
         const int nch = N / 16, ch0 = half ? (nch + 1) / 2 : 0, ch1 = half ? nch : (nch + 1) / 2;
         float *out = partial + (((size_t)split * 2 + c) * og.OH) * og.OW;
         if (!abort_s && n_stages > 0) {
+            constexpr int kPitch = kM / 2 + 1;  // floats per staged row (half the columns + 1)
+            float *tile = reinterpret_cast<float *>(smem) + (size_t)warp * 32 * kPitch;
             for (int cc = ch0; cc < ch1; ++cc) {
                 float v[16];
                 tmem_ld_32x32b_x16(tmem + ((uint32_t)lane_base << 16) + 128u * c + cc * 16, v);
-                if (m < nj &&
-                    VSAOGM_IN_BOUNDS(b.j0 + m - og.oy >= 0 && b.j0 + m - og.oy < og.OH &&
-                                     b.i0 - og.ox >= 0 && b.i0 - og.ox + ni <= og.OW)) {
-                    float *row = out + (size_t)(b.j0 + m - og.oy) * og.OW + (b.i0 - og.ox);
 #pragma unroll
-                    for (int x = 0; x < 16; ++x)
-                        if (cc * 16 + x < ni) row[cc * 16 + x] = v[x];
+                for (int x = 0; x < 16; ++x) tile[lane * kPitch + (cc - ch0) * 16 + x] = v[x];
+            }
+            __syncwarp();
+            const int x0 = ch0 * 16, cols = min(ni, ch1 * 16) - x0;
+            for (int r = 0; r < 32; ++r) {
+                const int mr = lane_base + r;
+                if (mr >= nj) break;
+                if (VSAOGM_IN_BOUNDS(b.j0 + mr - og.oy >= 0 && b.j0 + mr - og.oy < og.OH &&
+                                     b.i0 - og.ox >= 0 && b.i0 - og.ox + ni <= og.OW)) {
+                    float *row = out + (size_t)(b.j0 + mr - og.oy) * og.OW + (b.i0 - og.ox) + x0;
+                    for (int x = lane; x < cols; x += 32) row[x] = tile[r * kPitch + x];
                 }
             }
         } else if (!abort_s && n_stages == 0) {
@@ -474,11 +493,12 @@ template <int P>
 __global__ void __launch_bounds__(kThreads, 1) decode_tc_kernel(
     const BlockBatch blocks, const float2 *__restrict__ omega, const float *__restrict__ inv_norm,
     const float *__restrict__ nu, int D, int tiles_x, const int *__restrict__ row_tile, OutGeom og,
-    const float *__restrict__ col_off, const float *__restrict__ row_off, float res,
-    int k_per_split, int N, float u_scale, float *__restrict__ partial, int *__restrict__ status)
+    const float *__restrict__ col_off, const float *__restrict__ row_off,
+    const float2 *__restrict__ rot, int k_per_split, int N, float u_scale,
+    float *__restrict__ partial, int *__restrict__ status)
 {
     decode_tc_body<P>(blocks.b[blockIdx.x], blockIdx.y, omega, inv_norm, nu, D, tiles_x, row_tile,
-                      og, col_off, row_off, res, k_per_split, N, u_scale, partial, status);
+                      og, col_off, row_off, rot, k_per_split, N, u_scale, partial, status);
 }
 
 // Many maps in one launch: CTA q decodes item q of a device list of
@@ -491,8 +511,27 @@ __global__ void __launch_bounds__(kThreads, 1) decode_tc_batch_kernel(
     const BatchDecodeMap &M = tab.m[it.map];
     const int N = ((it.b.i1 - it.b.i0) + 15) / 16 * 16;
     decode_tc_body<P>(it.b, it.split, M.omega, M.inv_norm, M.nu, M.D, M.tiles_x, M.row_tile,
-                      OutGeom{0, 0, M.W, M.H}, M.col_off, M.row_off, M.res, M.k_per_split, N,
+                      OutGeom{0, 0, M.W, M.H}, M.col_off, M.row_off, M.rot, M.k_per_split, N,
                       M.u_scale, M.partial, M.status);
+}
+
+// rot[k] = exp(i 2 pi nu[k] step) for the x frequencies, then the y ones: the
+// phasor of one step of a thread's columns / rows (16 cells).  The phase is
+// reduced exactly and sin / cos taken of the reduced turn (sincospi).
+__global__ void __launch_bounds__(256) tc_rot_kernel(const float *__restrict__ nu, int n,
+                                                     float step, float2 *__restrict__ rot)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const float kMagic = 12582912.0f;
+    const float v = nu[k];
+    float p = __fmul_rn(v, step);
+    float e = fmaf(v, step, -p);
+    float r = __fsub_rn(__fadd_rn(p, kMagic), kMagic);
+    float f = __fadd_rn(__fsub_rn(p, r), e);
+    float sn, cs;
+    sincospif(2.f * f, &sn, &cs);
+    rot[k] = make_float2(cs, sn);
 }
 
 int prec_of(int decode_prec)
@@ -578,6 +617,19 @@ float tc_u_scale(const vsaogm_map *m)
     return u;
 }
 
+int build_tc_tables(vsaogm_map *m)
+{
+    const int D = m->cfg.D;
+    cudaError_t e = cudaMalloc((void **)&m->tc_rot, sizeof(float2) * 2 * (size_t)D);
+    if (e != cudaSuccess) return cuda_error(e, "decode tables");
+    // the same float step as the kernel's rows and columns: kWarps cells
+    tc_rot_kernel<<<(2 * D + 255) / 256, 256>>>(m->nu, 2 * D, (float)kWarps * m->cfg.resolution,
+                                                m->tc_rot);
+    if ((e = cudaGetLastError()) != cudaSuccess || (e = cudaDeviceSynchronize()) != cudaSuccess)
+        return cuda_error(e, "decode tables");
+    return VSAOGM_OK;
+}
+
 int decode_tensor_cores(vsaogm_map *m, Region r, float *heat, cudaStream_t st)
 {
     const int D = m->cfg.D;
@@ -618,7 +670,7 @@ int decode_tensor_cores(vsaogm_map *m, Region r, float *heat, cudaStream_t st)
 #define VSAOGM_LAUNCH_TC(PP)                                                                   \
     decode_tc_kernel<PP><<<grid, kThreads, smem, st>>>(                                        \
         batch, m->omega, m->inv_norm, m->nu, D, m->cfg.tiles_x, m->row_tile, og, m->col_off,    \
-        m->row_off, m->cfg.resolution, kps, N, u_scale, part, m->status)
+        m->row_off, m->tc_rot, kps, N, u_scale, part, m->status)
         if (P == kPrecFP8)
             VSAOGM_LAUNCH_TC(kPrecFP8);
         else if (P == kPrecFP16)

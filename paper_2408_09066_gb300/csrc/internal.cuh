@@ -166,11 +166,12 @@ struct BatchReduceTable {
 struct BatchDecodeMap {
     const float2 *omega;
     const float *inv_norm, *nu, *col_off, *row_off;
+    const float2 *rot;      // [2][D]: x then y phasor of a 16-cell step
     const int *row_tile;    // tile row of each cell row
     float *partial;         // [slices][2][H][W]
     int *status;
     int D, k_per_split, W, H, tiles_x;
-    float u_scale, res;
+    float u_scale;
 };
 struct BatchDecodeTable {
     int n_maps;
@@ -259,6 +260,7 @@ struct vsaogm_map {
     double *centre_x, *centre_y; // [tiles]
     int *col_tile, *row_tile;    // [W], [H]
     float *col_off, *row_off;    // [W], [H]
+    float2 *tc_rot;              // tensor-core decode: [2][D] phasors of a 16-cell step
     // bundling patches: [0] coarse (phases below 32 turns), [1] fine (below 4
     // turns); device tables of patch centres below
     vsaogm_impl::PatchDev patches[2];
@@ -320,6 +322,8 @@ int sum_slices(vsaogm_map *m, const float *partial, int splits, size_t cells, fl
 int decode_tensor_cores(vsaogm_map *m, Region r, float *heat, cudaStream_t st);
 // the tensor-core decode's blocks of region r (rows across tile rows)
 void tc_blocks(const vsaogm_map *m, Region r, std::vector<DecodeBlock> &out);
+// builds m's tensor-core decode tables (at creation, for a tensor-core decode_prec)
+int build_tc_tables(vsaogm_map *m);
 
 // entropy.cu
 // heat holds the class maps of region r ([2][r.h()][r.w()]); the outputs cover

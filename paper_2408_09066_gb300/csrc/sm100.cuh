@@ -1,7 +1,7 @@
 // Inline-PTX helpers for the 5th-generation tensor cores (tcgen05) on sm_103a:
 // mbarriers with bounded waits, tensor-memory allocation and loads, shared
-// memory matrix descriptors and the kind::f16 MMA.  Written from the public
-// PTX ISA description of these instructions.
+// memory matrix descriptors and the kind::f16 / kind::f8f6f4 MMAs.  Written
+// from the public PTX ISA description of these instructions.
 #pragma once
 
 #include <cuda_runtime.h>

@@ -142,7 +142,7 @@ void free_map(vsaogm_map *m)
     void *ptrs[] = {m->nu, m->omega, m->inv_norm, m->maxima, m->rejected, m->bnd_x_lo,
                     m->bnd_y_lo, m->centre_x, m->centre_y, m->col_tile, m->row_tile,
                     m->col_off, m->row_off, m->status, m->patch_cx[0], m->patch_cy[0],
-                    m->patch_cx[1], m->patch_cy[1]};
+                    m->patch_cx[1], m->patch_cy[1], m->tc_rot};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     free_scratch(m->ws);
@@ -387,6 +387,7 @@ int vsaogm_create(const vsaogm_config *cfg, vsaogm_map **out)
             rc = cuda_error(e, "map allocation");
             break;
         }
+        if (cfg->decode_prec != VSAOGM_DECODE_FP32 && (rc = build_tc_tables(m))) break;
     } while (0);
     if (rc != VSAOGM_OK) {
         free_map(m);
