@@ -324,12 +324,18 @@ __device__ __forceinline__ void decode_tc_body(
         }
         float nux[FPL], nuy[FPL];
         float2 rsx[FPL], rsy[FPL];
+        // the phasors of the thread's first column and first row at the
+        // stage's frequencies, taken as soon as the frequencies are in (the
+        // end of the previous stage), off the next stage's dependency chain
+        float2 ax0[FPL], ey0[FPL];
 #pragma unroll
         for (int j = 0; j < FPL; ++j) {
             nux[j] = pnx[j];
             nuy[j] = pny[j];
             rsx[j] = prx[j];
             rsy[j] = pry[j];
+            ax0[j] = phasor(nux[j], dx[0]);
+            ey0[j] = phasor(nuy[j], dy[0]);
         }
         named_bar_sync(1, kProducers);
         uint32_t phase_bits = 0u;  // bit b: parity to wait for on empty_bar[b]
@@ -351,17 +357,18 @@ __device__ __forceinline__ void decode_tc_body(
             // B operand: x phasors of the N columns.  Column warp + 16 (q + 1)
             // is 16 cells right of column warp + 16 q in the same tile, so its
             // phasor is the previous one times exp(i 2 pi nu_x 16 res).
+            // (Straight-line: every thread computes all kQ columns and stores
+            // those below N, so the compiler can interleave the B and A chains.)
             {
                 float2 rot[FPL], a[FPL];
 #pragma unroll
                 for (int j = 0; j < FPL; ++j) {
                     rot[j] = rsx[j];
-                    a[j] = phasor(nux[j], dx[0]);
+                    a[j] = ax0[j];
                 }
 #pragma unroll
                 for (int q = 0; q < kQ; ++q) {
                     const int n = warp + kWarps * q;
-                    if (n >= N) break;
 #pragma unroll
                     for (int j = 0; j < FPL; ++j)
                         if (q > 0) a[j] = cmul(a[j], rot[j]);
@@ -370,8 +377,10 @@ __device__ __forceinline__ void decode_tc_body(
                         split_pair<P>(a[0].x, a[0].y, hi, lo);
                     else
                         split_quad_e4m3(a[0].x, a[0].y, a[FPL - 1].x, a[FPL - 1].y, hi, lo);
-                    *reinterpret_cast<uint32_t *>(bh + q * kWarps * kRowBytes + soff) = hi;
-                    *reinterpret_cast<uint32_t *>(bl + q * kWarps * kRowBytes + soff) = lo;
+                    if (n < N) {
+                        *reinterpret_cast<uint32_t *>(bh + q * kWarps * kRowBytes + soff) = hi;
+                        *reinterpret_cast<uint32_t *>(bl + q * kWarps * kRowBytes + soff) = lo;
+                    }
                 }
             }
             // A operands: U_psi = conj(w_hat_psi) * y phasor, stored as
@@ -385,7 +394,7 @@ __device__ __forceinline__ void decode_tc_body(
                 auto start_row = [&](int q) {
 #pragma unroll
                     for (int j = 0; j < FPL; ++j) {
-                        const float2 e = phasor(nuy[j], dy[q]);
+                        const float2 e = q == 0 ? ey0[j] : phasor(nuy[j], dy[q]);
                         const float2 w0 = sw[(2 * tl[q]) * KS + FPL * lane + j];
                         const float2 w1 = sw[(2 * tl[q] + 1) * KS + FPL * lane + j];
                         u0[j] = make_float2(w0.x * e.x + w0.y * e.y, w0.x * e.y - w0.y * e.x);
@@ -438,6 +447,8 @@ __device__ __forceinline__ void decode_tc_body(
                     nuy[j] = pny[j];
                     rsx[j] = prx[j];
                     rsy[j] = pry[j];
+                    ax0[j] = phasor(nux[j], dx[0]);
+                    ey0[j] = phasor(nuy[j], dy[0]);
                 }
             }
             named_bar_sync(1, kProducers);
