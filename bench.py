@@ -295,9 +295,9 @@ DATA = ("synthetic: seeded 100-scan lidar trajectory in a walled 40 m world with
         "obstacles (1080 beams, 30 m range, sigma 0.03 m, 20 empty samples per beam)")
 
 # DRAM traffic of one encode launch on this workload from an ncu capture
-# (dram__bytes_read.sum + dram__bytes_write.sum = 25.79 MB + 115.97 MB), valid
+# (dram__bytes_read.sum + dram__bytes_write.sum = 23.99 MB + 114.25 MB), valid
 # only for the kernel source it was taken on (sha1 of csrc/encode.cu).
-ENCODE_TRAFFIC = {"sha1": "09dba0c7855709f518bd11b78f9653f1f9e004b8", "bytes": 141765632}
+ENCODE_TRAFFIC = {"sha1": "c77598dce4e607ef4ac241a2a4e043b8b370d754", "bytes": 138240256}
 
 
 def workload_config(wl, decode: str) -> dict:
