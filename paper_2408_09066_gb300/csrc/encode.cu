@@ -66,8 +66,8 @@ __device__ __forceinline__ int point_segment(float x, float y, unsigned lab, con
     int by = tile_along(ay.bnd_lo, ay.n_tiles - 1, y);
     const int mem = 2 * (by * ax.n_tiles + bx) + (int)lab;
     if (pt.n == 1) return mem;
-    const float ux = (x - (float)ax.centre[bx] + pt.hw_x) * pt.inv_pw_x;
-    const float uy = (y - (float)ay.centre[by] + pt.hw_y) * pt.inv_pw_y;
+    const float ux = (x - ax.centre[bx].x + pt.hw_x) * pt.inv_pw_x;
+    const float uy = (y - ay.centre[by].x + pt.hw_y) * pt.inv_pw_y;
     const int px = (int)floorf(fminf(fmaxf(ux, 0.f), (float)(pt.nx - 1)));
     const int py = (int)floorf(fminf(fmaxf(uy, 0.f), (float)(pt.ny - 1)));
     return mem * pt.n + py * pt.nx + px;
@@ -229,6 +229,27 @@ __global__ void __launch_bounds__(kScanThreads) seg_meta_kernel(int *__restrict_
 }
 
 // 4. Stable scatter into segment order, tile-centred coordinates.
+// a + b as the rounded sum s and its exact error e (a + b = s + e exactly).
+__device__ __forceinline__ float two_sum(float a, float b, float &e)
+{
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return s;
+}
+
+// x - (c.x + c.y) - d for a float x, a centre given as the float pair c and a
+// float d: two exact differences and the rounded sum of their errors, within an
+// ulp of the correctly rounded value (no FP64, which this GPU runs at a small
+// fraction of the FP32 rate).
+__device__ __forceinline__ float offset_from(float x, float2 c, float d)
+{
+    float e1, e2;
+    const float s = two_sum(x, -c.x, e1);
+    const float r = two_sum(s, -d, e2);
+    return __fadd_rn(r, __fsub_rn(__fadd_rn(e1, e2), c.y));
+}
+
 __device__ __forceinline__ void seg_scatter_body(const float2 *__restrict__ xy,
                                                  const uint8_t *__restrict__ lab, int n,
                                                  const AxisDev &ax, const AxisDev &ay,
@@ -244,18 +265,23 @@ __device__ __forceinline__ void seg_scatter_body(const float2 *__restrict__ xy,
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int base = blk * kSortBlock + warp * (kSortBlock / kSortWarps);
-    const int rounds = kSortBlock / kSortWarps / 32;
+    constexpr int kRounds = kSortBlock / kSortWarps / 32;
     int *mine = wcnt + warp * S1;
-    // pass 1: per-warp counts (only this warp touches its row)
-    for (int r = 0; r < rounds; ++r) {
-        int i = base + r * 32 + lane;
-        int seg = -1;
+    // pass 1: per-warp counts (only this warp touches its row); the points and
+    // their segments stay in registers for pass 2
+    float2 p[kRounds];
+    int seg[kRounds];
+#pragma unroll
+    for (int r = 0; r < kRounds; ++r) {
+        const int i = base + r * 32 + lane;
+        seg[r] = -1;
+        p[r] = make_float2(0.f, 0.f);
         if (i < n) {
-            float2 p = xy[i];
-            seg = point_segment(p.x, p.y, lab[i], ax, ay, pt, S);
+            p[r] = xy[i];
+            seg[r] = point_segment(p[r].x, p[r].y, lab[i], ax, ay, pt, S);
         }
-        unsigned peers = __match_any_sync(0xffffffffu, seg);
-        if (seg >= 0 && lane == __ffs(peers) - 1) mine[seg] += __popc(peers);
+        const unsigned peers = __match_any_sync(0xffffffffu, seg[r]);
+        if (seg[r] >= 0 && lane == __ffs(peers) - 1) mine[seg[r]] += __popc(peers);
         __syncwarp();
     }
     __syncthreads();
@@ -269,31 +295,25 @@ __device__ __forceinline__ void seg_scatter_body(const float2 *__restrict__ xy,
         }
     }
     __syncthreads();
-    // pass 2: ranks in original order, write tile-centred coordinates
+    // pass 2: ranks in original order, write offsets from the tile (or patch)
+    // centre
     const unsigned lt = (1u << lane) - 1u;
-    for (int r = 0; r < rounds; ++r) {
-        int i = base + r * 32 + lane;
-        int seg = -1;
-        float2 p = make_float2(0.f, 0.f);
-        if (i < n) {
-            p = xy[i];
-            seg = point_segment(p.x, p.y, lab[i], ax, ay, pt, S);
-        }
-        unsigned peers = __match_any_sync(0xffffffffu, seg);
+#pragma unroll
+    for (int r = 0; r < kRounds; ++r) {
+        const unsigned peers = __match_any_sync(0xffffffffu, seg[r]);
         int dst = 0;
-        if (seg >= 0) dst = mine[seg] + __popc(peers & lt);
+        if (seg[r] >= 0) dst = mine[seg[r]] + __popc(peers & lt);
         __syncwarp();
-        if (seg >= 0 && lane == __ffs(peers) - 1) mine[seg] += __popc(peers);
+        if (seg[r] >= 0 && lane == __ffs(peers) - 1) mine[seg[r]] += __popc(peers);
         __syncwarp();
-        if (seg >= 0 && seg < S) {
-            const int mem = seg / pt.n, patch = seg - mem * pt.n;
+        if (seg[r] >= 0 && seg[r] < S) {
+            const int mem = seg[r] / pt.n, patch = seg[r] - mem * pt.n;
             const int beta = mem >> 1;
             const int bx = beta % ax.n_tiles, by = beta / ax.n_tiles;
-            // FP64 once per point: the offset from the tile (or patch) centre, then f32.
-            const double cx = pt.n > 1 ? (double)pt.cx[patch % pt.nx] : 0.0;
-            const double cy = pt.n > 1 ? (double)pt.cy[patch / pt.nx] : 0.0;
-            float dx = (float)((double)p.x - ax.centre[bx] - cx);
-            float dy = (float)((double)p.y - ay.centre[by] - cy);
+            const float cx = pt.n > 1 ? pt.cx[patch % pt.nx] : 0.f;
+            const float cy = pt.n > 1 ? pt.cy[patch / pt.nx] : 0.f;
+            const float dx = offset_from(p[r].x, ax.centre[bx], cx);
+            const float dy = offset_from(p[r].y, ay.centre[by], cy);
             if (VSAOGM_IN_BOUNDS(dst >= 0 && dst < n)) sorted[dst] = make_float2(dx, dy);
         }
     }

@@ -58,7 +58,7 @@ constexpr int64_t kMaxBatch = 1 << 26;  // points per internal encode batch
 struct AxisDev {
     int n_tiles;
     const float *bnd_lo;    // [n_tiles - 1]: largest float <= x_min + a * tile_w, a = 1..
-    const double *centre;   // [n_tiles]: tile centres, FP64
+    const float2 *centre;   // [n_tiles]: tile centres as hi + lo (hi = f32(c), lo = f32(c - hi))
 };
 
 // Patches: for bundling only, a tile too wide for the fast phase reduction is
@@ -257,7 +257,7 @@ struct vsaogm_map {
     unsigned *maxima;            // [2]: order-preserving encoding of max P per class
     unsigned long long *rejected;  // [1]: points rejected by encode since reset
     float *bnd_x_lo, *bnd_y_lo;  // [tiles - 1]
-    double *centre_x, *centre_y; // [tiles]
+    float2 *centre_x, *centre_y; // [tiles]: tile centres as float pairs hi + lo
     int *col_tile, *row_tile;    // [W], [H]
     float *col_off, *row_off;    // [W], [H]
     float2 *tc_rot;              // tensor-core decode: [2][D] phasors of a 16-cell step

@@ -194,6 +194,18 @@ struct AxisHost {
     std::vector<int> first, last;  // per tile: first cell and one past the last
 };
 
+// FP64 values as float pairs hi + lo, hi = f32(v), lo = f32(v - hi): about 48
+// significant bits, for the sort's offsets from tile centres without FP64.
+std::vector<float2> centre_pairs(const std::vector<double> &v)
+{
+    std::vector<float2> out;
+    for (double c : v) {
+        const float hi = (float)c;
+        out.push_back(make_float2(hi, (float)(c - (double)hi)));
+    }
+    return out;
+}
+
 AxisHost build_axis(int cells, int tiles, double res, double lo)
 {
     AxisHost a;
@@ -332,7 +344,8 @@ int vsaogm_create(const vsaogm_config *cfg, vsaogm_map **out)
         m->tile_w = (double)cfg->grid_w * (double)cfg->resolution / cfg->tiles_x;
         m->tile_h = (double)cfg->grid_h * (double)cfg->resolution / cfg->tiles_y;
         if ((rc = upload(&m->bnd_x_lo, ax.bnd_lo)) || (rc = upload(&m->bnd_y_lo, ay.bnd_lo)) ||
-            (rc = upload(&m->centre_x, ax.centre)) || (rc = upload(&m->centre_y, ay.centre)) ||
+            (rc = upload(&m->centre_x, centre_pairs(ax.centre))) ||
+            (rc = upload(&m->centre_y, centre_pairs(ay.centre))) ||
             (rc = upload(&m->col_tile, ax.cell_tile)) || (rc = upload(&m->row_tile, ay.cell_tile)) ||
             (rc = upload(&m->col_off, ax.cell_off)) || (rc = upload(&m->row_off, ay.cell_off)))
             break;
