@@ -8,7 +8,8 @@
 //   3. seg_meta     : segment bases and the chunk table (chunks of at most
 //                     `chunk` points that never straddle a segment).
 //   4. seg_scatter  : stable scatter of the points into segment order, in the
-//                     tile-centred frame (offsets computed in FP64 per point).
+//                     tile-centred frame (offsets from float-pair centres with
+//                     compensated FP32 differences, within an ulp).
 //   5. encode_chunk : one CTA per (chunk, slice of k); each thread keeps KPT
 //                     frequencies in registers, walks the chunk's points from
 //                     shared memory and accumulates exp(i 2 pi nu . p) with
