@@ -7,8 +7,9 @@
 //   sort              : tile assignment + counting sort of every map, four
 //                       launches (count, scan, chunk table, scatter)
 //   encode            : ONE persistent launch over every map's (chunk,
-//                       frequency slice) items, claimed from an atomic counter
-//   reduce            : ONE launch, fixed-order chunk sums of every segment
+//                       frequency slice) items, claimed from an atomic counter;
+//                       the last CTA of each (memory, slice) adds the memory's
+//                       chunk partials in chunk order (fixed-order sums)
 //   norms             : ONE launch over every memory
 //   decode            : ONE tensor-core launch over every map's (block, slice)
 //   slice sums + max  : ONE launch (plus one tiny launch zeroing the maxima)
@@ -53,7 +54,8 @@ struct vsaogm_batch {
     cudaGraphExec_t exec = nullptr;
     long long graph_launches[VSAOGM_N_STAGES] = {};  // kernels of the captured step
     // stage timing: 7 events per timed step bound the stages sort (with the
-    // reset), encode, reduce, norms, decode (with the slice sums) and entropy
+    // reset), encode (with the chunk sums), reduce (empty: fused into the
+    // encode), norms, decode (with the slice sums) and entropy
     bool timing = false;
     std::vector<cudaEvent_t> free_events;
     std::vector<std::array<cudaEvent_t, 7>> pending;
@@ -165,10 +167,8 @@ int enqueue_step(vsaogm_batch *b, const float *const *xy, const uint8_t *const *
     memset(&sot, 0, sizeof(sot));
     BatchEncodeTable et;
     memset(&et, 0, sizeof(et));
-    BatchReduceTable rt;
-    memset(&rt, 0, sizeof(rt));
     long long items = 0;
-    int segs = 0, d_max = 0, sort_blocks = 0, sort_segs = 0, max_s1 = 0;
+    int sort_blocks = 0, sort_segs = 0, max_s1 = 0;
     for (int i = 0; i < M; ++i) {
         vsaogm_map *m = b->maps[i];
         int max_chunks = 0;
@@ -191,10 +191,6 @@ int enqueue_step(vsaogm_batch *b, const float *const *xy, const uint8_t *const *
         em.item_begin = items;
         items += (long long)max_chunks * em.slices;
         if (n[i] == 0) em.slices = 1;  // no items: max_chunks = 0
-        batch_reduce_entry(m, b->ws[i], pt, &rt.m[i]);
-        rt.m[i].seg_begin = segs;
-        segs += n[i] > 0 ? m->S : 0;
-        d_max = std::max(d_max, m->cfg.D);
     }
     if (sot.n_maps > 0) {
         if ((rc = launch_sort_batch(sot, sort_blocks, sort_segs, max_s1, st))) return rc;
@@ -209,20 +205,7 @@ int enqueue_step(vsaogm_batch *b, const float *const *xy, const uint8_t *const *
         counted[VSAOGM_STAGE_ENCODE] = 1;
     }
     mark();
-    // maps without points take part in nothing of the reduction
-    {
-        BatchReduceTable rr;
-        memset(&rr, 0, sizeof(rr));
-        int k = 0;
-        for (int i = 0; i < M; ++i)
-            if (n[i] > 0) rr.m[k++] = rt.m[i];
-        rr.n_maps = k;
-        rr.total_segs = segs;
-        if (k > 0) {
-            if ((rc = launch_reduce_batch(rr, d_max, st))) return rc;
-            counted[VSAOGM_STAGE_REDUCE] = 1;
-        }
-    }
+    // (the chunk sums of Eq. bundling run inside the encode launch)
     mark();
     // ---- query: norms, decode, slice sums + maxima, entropy
     BatchNormTable nt;

@@ -586,14 +586,15 @@ __device__ __forceinline__ void encode_points_x2(const float2 *sp, int len,
 // threads; contains __syncthreads).  sp and s_bound are the CTA's shared
 // staging buffers; out receives the chunk's partial memory (or, with ATOMIC,
 // is the map's memories).
-template <int NP, int NPOLY, bool ATOMIC>
+template <int NP, int NPOLY, bool ATOMIC, bool FUSED>
 __device__ __forceinline__ void encode_chunk_x2_body(const float2 *__restrict__ pts, int4 ch,
                                                      int c, int slice,
                                                      const float *__restrict__ nu, int D,
                                                      float nu_max_x, float nu_max_y,
                                                      int poly_warps, const PatchDev &pt,
-                                                     float2 *__restrict__ out, float2 *sp,
-                                                     unsigned *s_bound)
+                                                     float2 *__restrict__ out,
+                                                     const TailSum &tail, float2 *sp,
+                                                     unsigned *s_bound, int *s_tail)
 {
     using namespace sm100;
     // a chunk holds at most kMaxChunk points (the staging buffer's size)
@@ -675,6 +676,53 @@ __device__ __forceinline__ void encode_chunk_x2_body(const float2 *__restrict__ 
             }
         }
     }
+    if (!ATOMIC && FUSED) {
+        // The bundling's sum (Eq. bundling) over this memory's chunks, fused:
+        // every CTA publishes its partial and counts itself in; the last one
+        // for this (memory, slice) adds the memory's partials for the slice in
+        // chunk order (the order of a separate reduction kernel, so the result
+        // does not depend on which CTA is last) and clears the counter.
+        __threadfence();
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            const int c0 = tail.cbeg[mem * pt.n], c1 = tail.cbeg[(mem + 1) * pt.n];
+            unsigned *cnt = tail.cnt + (size_t)mem * tail.n_slices + slice;
+            const bool last = atomicAdd(cnt, 1u) + 1u == (unsigned)(c1 - c0);
+            if (last) *cnt = 0u;
+            s_tail[0] = last ? 1 : 0;
+            s_tail[1] = c0;
+            s_tail[2] = c1;
+        }
+        __syncthreads();
+        if (s_tail[0]) {
+            __threadfence();
+            const int c0 = s_tail[1], c1 = s_tail[2];
+            float sr[2 * NP], si[2 * NP];
+#pragma unroll
+            for (int q = 0; q < 2 * NP; ++q) sr[q] = si[q] = 0.f;
+            if (VSAOGM_IN_BOUNDS(c0 >= 0 && c1 >= c0))
+                for (int cc = c0; cc < c1; ++cc) {
+#pragma unroll
+                    for (int q = 0; q < 2 * NP; ++q) {
+                        const int k = kbase + q * 256;
+                        if (k < D) {
+                            const float2 v = __ldcg(out + (size_t)cc * D + k);
+                            sr[q] += v.x;
+                            si[q] += v.y;
+                        }
+                    }
+                }
+#pragma unroll
+            for (int q = 0; q < 2 * NP; ++q) {
+                const int k = kbase + q * 256;
+                if (k < D) {
+                    float2 *w = tail.omega + (size_t)mem * D + k;
+                    const float2 o = *w;
+                    *w = make_float2(o.x + sr[q], o.y + si[q]);
+                }
+            }
+        }
+    }
 }
 
 template <int NP, int NPOLY, bool ATOMIC>
@@ -688,10 +736,12 @@ __global__ void __launch_bounds__(256) encode_chunk_x2_kernel(const float2 *__re
 {
     __shared__ float2 sp[kMaxChunk];
     __shared__ unsigned s_bound[2];
+    __shared__ int s_tail[3];
     const int c = blockIdx.x;
     if (c >= *n_chunks) return;
-    encode_chunk_x2_body<NP, NPOLY, ATOMIC>(pts, chunks[c], c, blockIdx.y, nu, D, nu_max_x,
-                                            nu_max_y, poly_warps, pt, out, sp, s_bound);
+    encode_chunk_x2_body<NP, NPOLY, ATOMIC, false>(pts, chunks[c], c, blockIdx.y, nu, D,
+                                                   nu_max_x, nu_max_y, poly_warps, pt, out,
+                                                   TailSum{}, sp, s_bound, s_tail);
 }
 
 // 5''. Many maps in one persistent launch.  Work items are (map, chunk,
@@ -704,6 +754,7 @@ __global__ void __launch_bounds__(256) encode_batch_kernel(const __grid_constant
 {
     __shared__ float2 sp[kMaxChunk];
     __shared__ unsigned s_bound[2];
+    __shared__ int s_tail[3];
     __shared__ long long s_item;
     for (;;) {
         if (threadIdx.x == 0) s_item = (long long)atomicAdd(counter, 1ull);
@@ -719,38 +770,11 @@ __global__ void __launch_bounds__(256) encode_batch_kernel(const __grid_constant
         const long long local = it - M.item_begin;
         const int c = (int)(local / M.slices), slice = (int)(local % M.slices);
         if (c < *M.n_chunks)
-            encode_chunk_x2_body<4, -1, false>(M.pts, M.chunks[c], c, slice, M.nu, M.D,
-                                               M.nu_max_x, M.nu_max_y, M.poly_warps, M.pt,
-                                               M.out, sp, s_bound);
+            encode_chunk_x2_body<4, -1, false, true>(M.pts, M.chunks[c], c, slice, M.nu, M.D,
+                                                     M.nu_max_x, M.nu_max_y, M.poly_warps,
+                                                     M.pt, M.out, M.tail, sp, s_bound, s_tail);
         __syncthreads();  // the staging buffers are reused by the next item
     }
-}
-
-// 6'. The fixed-order partial sums of many maps in one launch: blockIdx.x is a
-//     global segment (maps' segments numbered one after the other; up to
-//     64 x 2048 of them, beyond the 65535 limit of a grid's y extent).
-__global__ void __launch_bounds__(256) reduce_batch_kernel(const __grid_constant__ BatchReduceTable tab)
-{
-    const int gs = blockIdx.x;
-    int lo = 0, hi = tab.n_maps - 1;
-    while (lo < hi) {
-        int mid = (lo + hi + 1) >> 1;
-        if (tab.m[mid].seg_begin <= gs) lo = mid; else hi = mid - 1;
-    }
-    const BatchReduceMap &M = tab.m[lo];
-    const int s = gs - M.seg_begin;  // memory of this map; its patches' chunks are contiguous
-    const int k = blockIdx.y * blockDim.x + threadIdx.x;
-    if (k >= M.D) return;
-    const int c0 = M.cbeg[s * M.patches], c1 = M.cbeg[(s + 1) * M.patches];
-    if (c0 == c1 || !VSAOGM_IN_BOUNDS(c0 >= 0 && c1 > c0)) return;
-    float sr = 0.f, si = 0.f;
-    for (int c = c0; c < c1; ++c) {
-        float2 v = M.partial[(size_t)c * M.D + k];
-        sr += v.x;
-        si += v.y;
-    }
-    float2 w = M.omega[(size_t)s * M.D + k];
-    M.omega[(size_t)s * M.D + k] = make_float2(w.x + sr, w.y + si);
 }
 
 // 6. omega[s][k] += sum of the partial memories of memory s (the chunks of its
@@ -1046,18 +1070,7 @@ void batch_encode_entry(const vsaogm_map *m, const Scratch &ws, const PatchDev &
     e->nu_max_x = m->nu_max[0];
     e->nu_max_y = m->nu_max[1];
     e->pt = pt;
-}
-
-void batch_reduce_entry(const vsaogm_map *m, const Scratch &ws, const PatchDev &pt,
-                        BatchReduceMap *e)
-{
-    const int S1 = m->S * pt.n + 1;
-    const int *meta = (const int *)ws.seg_meta.ptr;
-    e->partial = (const float2 *)ws.partial.ptr;
-    e->cbeg = meta + 2 * S1 + 1;
-    e->omega = m->omega;
-    e->D = m->cfg.D;
-    e->patches = pt.n;
+    e->tail = TailSum{meta + 2 * S1 + 1, m->enc_cnt, m->omega, e->slices};
 }
 
 int encode_batch_ctas()
@@ -1081,12 +1094,6 @@ int launch_encode_batch(const BatchEncodeTable &tab, unsigned long long *counter
     return e == cudaSuccess ? VSAOGM_OK : cuda_error(e, "batch encode");
 }
 
-int launch_reduce_batch(const BatchReduceTable &tab, int d_max, cudaStream_t st)
-{
-    reduce_batch_kernel<<<dim3(tab.total_segs, (d_max + 255) / 256), 256, 0, st>>>(tab);
-    cudaError_t e = cudaGetLastError();
-    return e == cudaSuccess ? VSAOGM_OK : cuda_error(e, "batch reduce");
-}
 
 int encode_bundle(vsaogm_map *m, const float *xy_f, const uint8_t *lab, int64_t n64,
                   cudaStream_t st)

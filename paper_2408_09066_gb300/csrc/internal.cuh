@@ -134,6 +134,15 @@ struct BatchSortTable {
     int n_maps;
     BatchSortMap m[kMaxBatchMaps];
 };
+// The bundling's fixed-order chunk sums, fused into the encode: the last CTA
+// to finish a (memory, frequency slice) adds that memory's chunk partials for
+// the slice to the memory, in chunk order.
+struct TailSum {
+    const int *cbeg;        // first chunk of each segment [S patches + 1]
+    unsigned *cnt;          // [memories][n_slices] finished chunks (zero between calls)
+    float2 *omega;          // the map's memories
+    int n_slices;
+};
 struct BatchEncodeMap {
     const float2 *pts;      // sorted tile-centred points
     const int4 *chunks;     // chunk table
@@ -145,22 +154,12 @@ struct BatchEncodeMap {
     float nu_max_x, nu_max_y;
     PatchDev pt;
     int poly_warps;         // this map's warps with one polynomial frequency pair
+    TailSum tail;
 };
 struct BatchEncodeTable {
     int n_maps, poly_warps;
     long long total;        // work items over all maps
     BatchEncodeMap m[kMaxBatchMaps];
-};
-struct BatchReduceMap {
-    const float2 *partial;
-    const int *cbeg;        // chunk range of each segment [S patches + 1]
-    float2 *omega;
-    int D, seg_begin;       // first global memory of this map
-    int patches;            // segments (patches) per memory
-};
-struct BatchReduceTable {
-    int n_maps, total_segs;
-    BatchReduceMap m[kMaxBatchMaps];
 };
 
 struct BatchDecodeMap {
@@ -260,6 +259,7 @@ struct vsaogm_map {
     float2 *centre_x, *centre_y; // [tiles]: tile centres as float pairs hi + lo
     int *col_tile, *row_tile;    // [W], [H]
     float *col_off, *row_off;    // [W], [H]
+    unsigned *enc_cnt;           // [S][ceil(D / 512)]: the encode's finished-chunk counters
     float2 *tc_rot;              // tensor-core decode: [2][D] phasors of a 16-cell step
     // bundling patches: [0] coarse (phases below 32 turns), [1] fine (below 4
     // turns); device tables of patch centres below
@@ -354,12 +354,9 @@ int launch_sort_batch(const BatchSortTable &tab, int blocks, int segs, int max_s
                       cudaStream_t st);
 void batch_encode_entry(const vsaogm_map *m, const Scratch &ws, const PatchDev &pt,
                         BatchEncodeMap *e);
-void batch_reduce_entry(const vsaogm_map *m, const Scratch &ws, const PatchDev &pt,
-                        BatchReduceMap *e);
 int encode_batch_ctas();
 int launch_encode_batch(const BatchEncodeTable &tab, unsigned long long *counter, int ctas,
                         cudaStream_t st);
-int launch_reduce_batch(const BatchReduceTable &tab, int d_max, cudaStream_t st);
 int launch_norms_batch(const BatchNormTable &tab, int total_memories, cudaStream_t st);
 int launch_sums_batch(const BatchOutTable &tab, size_t max_cells, cudaStream_t st);
 int launch_decode_tc_batch(const BatchDecodeTable &tab, const BatchDecodeItem *items,

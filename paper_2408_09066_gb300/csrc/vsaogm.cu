@@ -139,7 +139,7 @@ float round_down_f32(double v)
 void free_map(vsaogm_map *m)
 {
     if (!m) return;
-    void *ptrs[] = {m->nu, m->omega, m->inv_norm, m->maxima, m->rejected, m->bnd_x_lo,
+    void *ptrs[] = {m->nu, m->omega, m->inv_norm, m->maxima, m->rejected, m->enc_cnt, m->bnd_x_lo,
                     m->bnd_y_lo, m->centre_x, m->centre_y, m->col_tile, m->row_tile,
                     m->col_off, m->row_off, m->status, m->patch_cx[0], m->patch_cy[0],
                     m->patch_cx[1], m->patch_cy[1], m->tc_rot};
@@ -395,6 +395,11 @@ int vsaogm_create(const vsaogm_config *cfg, vsaogm_map **out)
         if (e == cudaSuccess) e = cudaMalloc((void **)&m->rejected, sizeof(unsigned long long));
         if (e == cudaSuccess) e = cudaMemset(m->omega, 0, sizeof(float2) * (size_t)m->S * D);
         if (e == cudaSuccess) e = cudaMemset(m->rejected, 0, sizeof(unsigned long long));
+        // the encode's finished-chunk counters: one per memory and slice of at
+        // least 512 frequencies; each is back at zero when a launch ends
+        const size_t n_cnt = (size_t)m->S * ((D + 511) / 512);
+        if (e == cudaSuccess) e = cudaMalloc((void **)&m->enc_cnt, sizeof(unsigned) * n_cnt);
+        if (e == cudaSuccess) e = cudaMemset(m->enc_cnt, 0, sizeof(unsigned) * n_cnt);
         if (e == cudaSuccess) e = cudaDeviceSynchronize();
         if (e != cudaSuccess) {
             rc = cuda_error(e, "map allocation");
