@@ -8,8 +8,10 @@
 //                       launches (count, scan, chunk table, scatter)
 //   encode            : ONE persistent launch over every map's (chunk,
 //                       frequency slice) items, claimed from an atomic counter;
-//                       the last CTA of each (memory, slice) adds the memory's
-//                       chunk partials in chunk order (fixed-order sums)
+//                       for maps with few chunks per memory the last CTA of
+//                       each (memory, slice) adds the memory's chunk partials
+//                       in chunk order (fixed-order sums)
+//   reduce            : ONE launch, the same sums for the other maps
 //   norms             : ONE launch over every memory
 //   decode            : ONE tensor-core launch over every map's (block, slice)
 //   slice sums + max  : ONE launch (plus one tiny launch zeroing the maxima)
@@ -25,6 +27,11 @@
 #include "internal.cuh"
 
 static_assert(vsaogm_impl::kMaxBatchMaps == VSAOGM_MAX_BATCH, "batch size limit");
+
+// Average chunks per memory up to which a map's chunk sums run inside the
+// batched encode (above it one CTA walking a memory's chunks at the end of
+// the launch costs more than the separate reduction).
+constexpr int kFusedChunksPerMemory = 16;
 
 using namespace vsaogm_impl;
 
@@ -54,8 +61,8 @@ struct vsaogm_batch {
     cudaGraphExec_t exec = nullptr;
     long long graph_launches[VSAOGM_N_STAGES] = {};  // kernels of the captured step
     // stage timing: 7 events per timed step bound the stages sort (with the
-    // reset), encode (with the chunk sums), reduce (empty: fused into the
-    // encode), norms, decode (with the slice sums) and entropy
+    // reset), encode (with fused chunk sums), reduce (the other maps' chunk
+    // sums), norms, decode (with the slice sums) and entropy
     bool timing = false;
     std::vector<cudaEvent_t> free_events;
     std::vector<std::array<cudaEvent_t, 7>> pending;
@@ -167,8 +174,10 @@ int enqueue_step(vsaogm_batch *b, const float *const *xy, const uint8_t *const *
     memset(&sot, 0, sizeof(sot));
     BatchEncodeTable et;
     memset(&et, 0, sizeof(et));
+    BatchReduceTable rt;
+    memset(&rt, 0, sizeof(rt));
     long long items = 0;
-    int sort_blocks = 0, sort_segs = 0, max_s1 = 0;
+    int sort_blocks = 0, sort_segs = 0, max_s1 = 0, red_segs = 0, d_max = 0;
     for (int i = 0; i < M; ++i) {
         vsaogm_map *m = b->maps[i];
         int max_chunks = 0;
@@ -191,6 +200,17 @@ int enqueue_step(vsaogm_batch *b, const float *const *xy, const uint8_t *const *
         em.item_begin = items;
         items += (long long)max_chunks * em.slices;
         if (n[i] == 0) em.slices = 1;  // no items: max_chunks = 0
+        // Maps whose memories hold few chunks each sum them inside the encode
+        // launch (the last CTA of a memory walks its chunks); maps with many
+        // chunks per memory leave that to the separate reduction launch.
+        if (n[i] > 0 && (n[i] + chunk - 1) / chunk > (int64_t)kFusedChunksPerMemory * m->S) {
+            em.tail.cnt = nullptr;
+            BatchReduceMap &rm = rt.m[rt.n_maps++];
+            batch_reduce_entry(m, b->ws[i], pt, &rm);
+            rm.seg_begin = red_segs;
+            red_segs += m->S;
+            d_max = std::max(d_max, m->cfg.D);
+        }
     }
     if (sot.n_maps > 0) {
         if ((rc = launch_sort_batch(sot, sort_blocks, sort_segs, max_s1, st))) return rc;
@@ -205,7 +225,11 @@ int enqueue_step(vsaogm_batch *b, const float *const *xy, const uint8_t *const *
         counted[VSAOGM_STAGE_ENCODE] = 1;
     }
     mark();
-    // (the chunk sums of Eq. bundling run inside the encode launch)
+    rt.total_segs = red_segs;
+    if (rt.n_maps > 0) {
+        if ((rc = launch_reduce_batch(rt, d_max, st))) return rc;
+        counted[VSAOGM_STAGE_REDUCE] = 1;
+    }
     mark();
     // ---- query: norms, decode, slice sums + maxima, entropy
     BatchNormTable nt;

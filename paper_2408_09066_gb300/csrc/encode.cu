@@ -676,7 +676,7 @@ __device__ __forceinline__ void encode_chunk_x2_body(const float2 *__restrict__ 
             }
         }
     }
-    if (!ATOMIC && FUSED) {
+    if (!ATOMIC && FUSED && tail.cnt) {
         // The bundling's sum (Eq. bundling) over this memory's chunks, fused:
         // every CTA publishes its partial and counts itself in; the last one
         // for this (memory, slice) adds the memory's partials for the slice in
@@ -775,6 +775,34 @@ __global__ void __launch_bounds__(256) encode_batch_kernel(const __grid_constant
                                                      M.pt, M.out, M.tail, sp, s_bound, s_tail);
         __syncthreads();  // the staging buffers are reused by the next item
     }
+}
+
+// 6'. The fixed-order partial sums of many maps in one launch (maps whose
+//     memories hold many chunks each): blockIdx.x is a global memory (maps'
+//     memories numbered one after the other; beyond the 65535 limit of a
+//     grid's y extent).
+__global__ void __launch_bounds__(256) reduce_batch_kernel(const __grid_constant__ BatchReduceTable tab)
+{
+    const int gs = blockIdx.x;
+    int lo = 0, hi = tab.n_maps - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (tab.m[mid].seg_begin <= gs) lo = mid; else hi = mid - 1;
+    }
+    const BatchReduceMap &M = tab.m[lo];
+    const int s = gs - M.seg_begin;  // memory of this map; its patches' chunks are contiguous
+    const int k = blockIdx.y * blockDim.x + threadIdx.x;
+    if (k >= M.D) return;
+    const int c0 = M.cbeg[s * M.patches], c1 = M.cbeg[(s + 1) * M.patches];
+    if (c0 == c1 || !VSAOGM_IN_BOUNDS(c0 >= 0 && c1 > c0)) return;
+    float sr = 0.f, si = 0.f;
+    for (int c = c0; c < c1; ++c) {
+        float2 v = M.partial[(size_t)c * M.D + k];
+        sr += v.x;
+        si += v.y;
+    }
+    float2 w = M.omega[(size_t)s * M.D + k];
+    M.omega[(size_t)s * M.D + k] = make_float2(w.x + sr, w.y + si);
 }
 
 // 6. omega[s][k] += sum of the partial memories of memory s (the chunks of its
@@ -1071,6 +1099,25 @@ void batch_encode_entry(const vsaogm_map *m, const Scratch &ws, const PatchDev &
     e->nu_max_y = m->nu_max[1];
     e->pt = pt;
     e->tail = TailSum{meta + 2 * S1 + 1, m->enc_cnt, m->omega, e->slices};
+}
+
+void batch_reduce_entry(const vsaogm_map *m, const Scratch &ws, const PatchDev &pt,
+                        BatchReduceMap *e)
+{
+    const int S1 = m->S * pt.n + 1;
+    const int *meta = (const int *)ws.seg_meta.ptr;
+    e->partial = (const float2 *)ws.partial.ptr;
+    e->cbeg = meta + 2 * S1 + 1;
+    e->omega = m->omega;
+    e->D = m->cfg.D;
+    e->patches = pt.n;
+}
+
+int launch_reduce_batch(const BatchReduceTable &tab, int d_max, cudaStream_t st)
+{
+    reduce_batch_kernel<<<dim3(tab.total_segs, (d_max + 255) / 256), 256, 0, st>>>(tab);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? VSAOGM_OK : cuda_error(e, "batch reduce");
 }
 
 int encode_batch_ctas()

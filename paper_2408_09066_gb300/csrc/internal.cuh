@@ -139,7 +139,8 @@ struct BatchSortTable {
 // the slice to the memory, in chunk order.
 struct TailSum {
     const int *cbeg;        // first chunk of each segment [S patches + 1]
-    unsigned *cnt;          // [memories][n_slices] finished chunks (zero between calls)
+    unsigned *cnt;          // [memories][n_slices] finished chunks (zero between calls);
+                            // null: the map's chunks are summed by reduce_batch_kernel
     float2 *omega;          // the map's memories
     int n_slices;
 };
@@ -160,6 +161,18 @@ struct BatchEncodeTable {
     int n_maps, poly_warps;
     long long total;        // work items over all maps
     BatchEncodeMap m[kMaxBatchMaps];
+};
+
+struct BatchReduceMap {
+    const float2 *partial;
+    const int *cbeg;        // chunk range of each segment [S patches + 1]
+    float2 *omega;
+    int D, seg_begin;       // first global memory of this map
+    int patches;            // segments (patches) per memory
+};
+struct BatchReduceTable {
+    int n_maps, total_segs;
+    BatchReduceMap m[kMaxBatchMaps];
 };
 
 struct BatchDecodeMap {
@@ -357,6 +370,10 @@ void batch_encode_entry(const vsaogm_map *m, const Scratch &ws, const PatchDev &
 int encode_batch_ctas();
 int launch_encode_batch(const BatchEncodeTable &tab, unsigned long long *counter, int ctas,
                         cudaStream_t st);
+// the fixed-order chunk sums of the maps whose encode entry has no fused sums
+void batch_reduce_entry(const vsaogm_map *m, const Scratch &ws, const PatchDev &pt,
+                        BatchReduceMap *e);
+int launch_reduce_batch(const BatchReduceTable &tab, int d_max, cudaStream_t st);
 int launch_norms_batch(const BatchNormTable &tab, int total_memories, cudaStream_t st);
 int launch_sums_batch(const BatchOutTable &tab, size_t max_cells, cudaStream_t st);
 int launch_decode_tc_batch(const BatchDecodeTable &tab, const BatchDecodeItem *items,
