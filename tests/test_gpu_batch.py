@@ -113,6 +113,36 @@ def test_batch_matches_oracle(prec):
         r.close()
 
 
+def test_batch_mixes_fused_and_separate_chunk_sums():
+    """A batch holding a one-tile map with many points (its memories hold many
+    chunks: their sums run in the separate reduction launch) beside many-tile
+    maps with few points (their sums run inside the encode launch), checked
+    against the oracle; a second step on reset maps gives bit-identical
+    memories (both fixed-order paths are deterministic)."""
+    import dataclasses
+    wls = _maps(n_maps=3, seed=41, min_cells=64, max_cells=96, min_points=2000,
+                max_points=4000, max_tiles=4, dims=(1000, 2048))
+    dense = synth.batch_maps(n_maps=1, seed=43, min_cells=64, max_cells=64, min_points=60000,
+                             max_points=60000, max_tiles=1, dims=(1000,))[0]
+    wls = ([dataclasses.replace(dense, tiles_x=1, tiles_y=1)] +
+           [dataclasses.replace(w, tiles_x=4, tiles_y=4) for w in wls])
+    r = _Run(wls, V.DECODE_BF16X3)
+    try:
+        r.batch.set_timing(True)
+        r.batch.step(r.xy, r.lab, r.heat, r.occ, r.ogm)
+        got = r.host()
+        st = r.batch.stage_times(reset=True)
+        assert st["reduce"][1] == 1  # the dense map's sums
+        for w, cfg, g in zip(r.wls, r.cfgs, got):
+            _check(g, _oracle(cfg, w.xy, w.labels), w.name)
+        r.batch.step(r.xy, r.lab, r.heat, r.occ, r.ogm, reset=True)
+        again = r.host()
+        for a, b in zip(got, again):
+            assert np.array_equal(a["omega"], b["omega"])
+    finally:
+        r.close()
+
+
 def test_batch_equals_single_maps():
     """The batch gives each map what vsaogm_encode_bundle + vsaogm_query give
     it alone, up to the summation order inside the memories."""
