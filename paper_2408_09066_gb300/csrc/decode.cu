@@ -23,24 +23,45 @@ namespace {
 constexpr int kBI = 64, kBJ = 64, kKC = 32;  // cells per block (x, y), k per stage
 
 // ||w|| per memory -> 1/||w|| (0 for an all-zero memory).
-__global__ void __launch_bounds__(256) norms_kernel(const float2 *__restrict__ omega, int D,
-                                                    float *__restrict__ inv_norm)
+// ||w_s||^2 by one CTA of kNormThreads threads: each thread keeps four running
+// sums (frequencies k = t + j kNormThreads, j mod 4) so that four loads are in
+// flight, then a fixed-order tree over the warps (the same order on every call).
+constexpr int kNormThreads = 1024;
+
+__device__ __forceinline__ float norm2_row(const float2 *__restrict__ w, int D)
 {
-    const int s = blockIdx.x;
-    float acc = 0.f;
-    for (int k = threadIdx.x; k < D; k += blockDim.x) {
-        float2 w = omega[(size_t)s * D + k];
-        acc = fmaf(w.x, w.x, fmaf(w.y, w.y, acc));
+    float a[4] = {0.f, 0.f, 0.f, 0.f};
+    int k = threadIdx.x;
+    for (; k + 3 * kNormThreads < D; k += 4 * kNormThreads) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const float2 v = w[k + j * kNormThreads];
+            a[j] = fmaf(v.x, v.x, fmaf(v.y, v.y, a[j]));
+        }
     }
-    __shared__ float red[8];
+    for (int j = 0; k < D; k += kNormThreads, ++j) {
+        const float2 v = w[k];
+        a[j & 3] = fmaf(v.x, v.x, fmaf(v.y, v.y, a[j & 3]));
+    }
+    float acc = (a[0] + a[1]) + (a[2] + a[3]);
+    __shared__ float red[kNormThreads / 32];
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
     __syncthreads();
-    if (threadIdx.x == 0) {
-        float t = 0.f;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
-        inv_norm[s] = t > 0.f ? rsqrtf(t) : 0.f;
+    float t = 0.f;
+    if (threadIdx.x < 32) {
+        t = red[threadIdx.x];
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
     }
+    return t;  // valid in thread 0
+}
+
+__global__ void __launch_bounds__(kNormThreads) norms_kernel(const float2 *__restrict__ omega,
+                                                             int D, float *__restrict__ inv_norm)
+{
+    const int s = blockIdx.x;
+    const float t = norm2_row(omega + (size_t)s * D, D);
+    if (threadIdx.x == 0) inv_norm[s] = t > 0.f ? rsqrtf(t) : 0.f;
 }
 
 // exp(i 2 pi nu d) with the phase reduced exactly to [-1/2, 1/2] turns:
@@ -184,7 +205,7 @@ __global__ void nonlinear_kernel(float *__restrict__ heat, size_t cells,
 }
 
 // ---- batched forms (many maps per launch) ----
-__global__ void __launch_bounds__(256) norms_batch_kernel(const __grid_constant__ BatchNormTable tab)
+__global__ void __launch_bounds__(kNormThreads) norms_batch_kernel(const __grid_constant__ BatchNormTable tab)
 {
     const int gs = blockIdx.x;
     int lo = 0, hi = tab.n_maps - 1;
@@ -194,20 +215,8 @@ __global__ void __launch_bounds__(256) norms_batch_kernel(const __grid_constant_
     }
     const BatchNormMap &M = tab.m[lo];
     const int s = gs - M.mem_begin;
-    float acc = 0.f;
-    for (int k = threadIdx.x; k < M.D; k += blockDim.x) {
-        float2 w = M.omega[(size_t)s * M.D + k];
-        acc = fmaf(w.x, w.x, fmaf(w.y, w.y, acc));
-    }
-    __shared__ float red[8];
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        float t = 0.f;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
-        M.inv_norm[s] = t > 0.f ? rsqrtf(t) : 0.f;
-    }
+    const float t = norm2_row(M.omega + (size_t)s * M.D, M.D);
+    if (threadIdx.x == 0) M.inv_norm[s] = t > 0.f ? rsqrtf(t) : 0.f;
 }
 
 __global__ void zero_maxima_batch_kernel(const __grid_constant__ BatchOutTable tab)
@@ -255,7 +264,7 @@ __global__ void add_kernel(float2 *__restrict__ dst, const float2 *__restrict__ 
 int memory_norms(vsaogm_map *m, cudaStream_t st)
 {
     StageScope sc(m, VSAOGM_STAGE_NORMS, st);
-    norms_kernel<<<m->S, 256, 0, st>>>(m->omega, m->cfg.D, m->inv_norm);
+    norms_kernel<<<m->S, kNormThreads, 0, st>>>(m->omega, m->cfg.D, m->inv_norm);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_error(e, "decode: norms");
     sc.end(1);
@@ -358,7 +367,7 @@ int apply_nonlinearity(vsaogm_map *m, float *heat, cudaStream_t st)
 
 int launch_norms_batch(const BatchNormTable &tab, int total_memories, cudaStream_t st)
 {
-    norms_batch_kernel<<<total_memories, 256, 0, st>>>(tab);
+    norms_batch_kernel<<<total_memories, kNormThreads, 0, st>>>(tab);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? VSAOGM_OK : cuda_error(e, "batch norms");
 }
