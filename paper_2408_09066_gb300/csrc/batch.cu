@@ -248,8 +248,7 @@ int enqueue_step(vsaogm_batch *b, const float *const *xy, const uint8_t *const *
     memset(&dt, 0, sizeof(dt));
     BatchOutTable ot;
     memset(&ot, 0, sizeof(ot));
-    size_t max_cells = 0;
-    int ent_blocks = 0;
+    int ent_blocks = 0, sum_blocks = 0;
     for (int i = 0; i < M; ++i) {
         vsaogm_map *m = b->maps[i];
         const int D = m->cfg.D, s = b->splits[i], KS = tc_stage_freqs(b->decode_prec);
@@ -275,11 +274,12 @@ int enqueue_step(vsaogm_batch *b, const float *const *xy, const uint8_t *const *
         o.mode = m->cfg.decode_mode;
         o.blk_begin = ent_blocks;
         ent_blocks += ((o.W + 31) / 32) * ((o.H + 31) / 32);
-        max_cells = std::max(max_cells, (size_t)o.W * o.H);
+        o.sum_begin = sum_blocks;
+        sum_blocks += (int)((2 * (size_t)o.W * o.H + kSumBlockOutputs - 1) / kSumBlockOutputs);
     }
     dt.n_maps = ot.n_maps = M;
     if ((rc = launch_decode_tc_batch(dt, b->items, b->n_items, b->decode_prec, st))) return rc;
-    if ((rc = launch_sums_batch(ot, max_cells, st))) return rc;
+    if ((rc = launch_sums_batch(ot, sum_blocks, st))) return rc;
     counted[VSAOGM_STAGE_DECODE] = 3;
     mark();
     if ((rc = launch_entropy_batch(ot, st))) return rc;

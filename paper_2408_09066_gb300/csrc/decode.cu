@@ -229,13 +229,22 @@ __global__ void zero_maxima_batch_kernel(const __grid_constant__ BatchOutTable t
 }
 
 // blockIdx.y is the map: its slices summed in order, scaled, and the maxima.
+// One block of kSumBlockOutputs outputs of one map per CTA (maps' blocks
+// numbered one after the other, so large and small maps share the GPU evenly).
 __global__ void __launch_bounds__(256) reduce_slices_batch_kernel(const __grid_constant__ BatchOutTable tab)
 {
-    const BatchMapOut &M = tab.m[blockIdx.y];
+    const int qb = blockIdx.x;
+    int lo = 0, hi = tab.n_maps - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (tab.m[mid].sum_begin <= qb) lo = mid; else hi = mid - 1;
+    }
+    const BatchMapOut &M = tab.m[lo];
     const size_t cells = (size_t)M.W * M.H;
+    const size_t q0 = (size_t)(qb - M.sum_begin) * kSumBlockOutputs;
+    const size_t q1 = min(2 * cells, q0 + kSumBlockOutputs);
     float mx[2] = {-INFINITY, -INFINITY};
-    for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < 2 * cells;
-         q += (size_t)gridDim.x * blockDim.x) {
+    for (size_t q = q0 + threadIdx.x; q < q1; q += blockDim.x) {
         float s = 0.f;
         for (int sp = 0; sp < M.splits; ++sp) s += M.partial[(size_t)sp * 2 * cells + q];
         s *= M.inv_scale;
@@ -372,11 +381,10 @@ int launch_norms_batch(const BatchNormTable &tab, int total_memories, cudaStream
     return e == cudaSuccess ? VSAOGM_OK : cuda_error(e, "batch norms");
 }
 
-int launch_sums_batch(const BatchOutTable &tab, size_t max_cells, cudaStream_t st)
+int launch_sums_batch(const BatchOutTable &tab, int total_blocks, cudaStream_t st)
 {
     zero_maxima_batch_kernel<<<1, kMaxBatchMaps, 0, st>>>(tab);
-    const int bx = (int)std::max<size_t>(1, std::min<size_t>((2 * max_cells + 255) / 256, 64));
-    reduce_slices_batch_kernel<<<dim3(bx, tab.n_maps), 256, 0, st>>>(tab);
+    if (total_blocks > 0) reduce_slices_batch_kernel<<<total_blocks, 256, 0, st>>>(tab);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? VSAOGM_OK : cuda_error(e, "batch slice sums");
 }

@@ -213,6 +213,7 @@ struct BatchMapOut {
     int r[2];               // disk radius of class 0 (empty) and 1 (occupied)
     unsigned mode;
     int blk_begin;          // first 32 x 32 entropy block of this map in the batch
+    int sum_begin;          // first slice-sum block of this map in the batch
 };
 struct BatchOutTable {
     int n_maps;
@@ -375,7 +376,10 @@ void batch_reduce_entry(const vsaogm_map *m, const Scratch &ws, const PatchDev &
                         BatchReduceMap *e);
 int launch_reduce_batch(const BatchReduceTable &tab, int d_max, cudaStream_t st);
 int launch_norms_batch(const BatchNormTable &tab, int total_memories, cudaStream_t st);
-int launch_sums_batch(const BatchOutTable &tab, size_t max_cells, cudaStream_t st);
+// slice sums + maxima of every map; sum_begin numbers kSumBlockOutputs-output
+// blocks over the maps, total_blocks of them
+constexpr int kSumBlockOutputs = 2048;
+int launch_sums_batch(const BatchOutTable &tab, int total_blocks, cudaStream_t st);
 int launch_decode_tc_batch(const BatchDecodeTable &tab, const BatchDecodeItem *items,
                            int n_items, int decode_prec, cudaStream_t st);
 // frequencies per tensor-core stage for a decode_prec (slices are multiples of it)
