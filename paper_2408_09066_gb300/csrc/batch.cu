@@ -190,7 +190,7 @@ int enqueue_step(vsaogm_batch *b, const float *const *xy, const uint8_t *const *
             sm.blk_begin = sort_blocks;
             sm.seg_begin = sort_segs;
             sort_blocks += sm.nb;
-            sort_segs += sm.S + 1;
+            sort_segs += sort_scan_ctas(sm.S + 1);
             max_s1 = std::max(max_s1, sm.S + 1);
         }
         BatchEncodeMap &em = et.m[i];

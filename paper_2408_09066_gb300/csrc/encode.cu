@@ -158,23 +158,42 @@ __global__ void __launch_bounds__(256) seg_count_kernel(const float2 *__restrict
 
 // 2. Column s of hist [nb][S1] -> exclusive prefix over blocks (in place);
 //    total[s] = column sum.
+// Columns cg * kScanCols .. + kScanCols - 1 of hist [nb][S1] by one CTA of
+// kScanWarps warps: lane = column (coalesced rows), warp w = a contiguous run
+// of block rows.  Pass 1 sums each warp's run, the runs' sums are scanned
+// across warps, and pass 2 rewrites the run in place as exclusive prefixes.
+constexpr int kScanCols = 32;
+constexpr int kScanWarps = 32;
 __device__ __forceinline__ void seg_scan_body(int *__restrict__ hist, int nb, int S1,
-                                              int *__restrict__ total, int s)
+                                              int *__restrict__ total, int cg)
 {
+    __shared__ int wsum[kScanWarps][kScanCols + 1];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int s = cg * kScanCols + lane;
+    const bool col = s < S1;
+    const int per = (nb + kScanWarps - 1) / kScanWarps;
+    const int b0 = min(nb, warp * per), b1 = min(nb, b0 + per);
+    int sum = 0;
+    if (col)
+        for (int b = b0; b < b1; ++b) sum += hist[(size_t)b * S1 + s];
+    wsum[warp][lane] = sum;
+    __syncthreads();
     int carry = 0;
-    for (int b0 = 0; b0 < nb; b0 += kScanThreads) {
-        int b = b0 + threadIdx.x;
-        int v = b < nb ? hist[(size_t)b * S1 + s] : 0;
-        int tot;
-        int pre = block_exclusive_scan(v, &tot);
-        if (b < nb) hist[(size_t)b * S1 + s] = carry + pre;
-        carry += tot;
+    for (int w = 0; w < warp; ++w) carry += wsum[w][lane];
+    if (col) {
+        for (int b = b0; b < b1; ++b) {
+            const size_t i = (size_t)b * S1 + s;
+            const int v = hist[i];
+            hist[i] = carry;
+            carry += v;
+        }
+        if (warp == kScanWarps - 1) total[s] = carry;  // the last run ends at the column sum
     }
-    if (threadIdx.x == 0) total[s] = carry;
 }
 
-__global__ void __launch_bounds__(kScanThreads) seg_scan_kernel(int *__restrict__ hist, int nb,
-                                                                int S1, int *__restrict__ total)
+__global__ void __launch_bounds__(32 * kScanWarps) seg_scan_kernel(int *__restrict__ hist, int nb,
+                                                                   int S1,
+                                                                   int *__restrict__ total)
 {
     seg_scan_body(hist, nb, S1, total, blockIdx.x);
 }
@@ -352,7 +371,7 @@ __global__ void __launch_bounds__(256) batch_seg_count_kernel(const __grid_const
                    cnt);
 }
 
-__global__ void __launch_bounds__(kScanThreads) batch_seg_scan_kernel(const __grid_constant__ BatchSortTable tab)
+__global__ void __launch_bounds__(32 * kScanWarps) batch_seg_scan_kernel(const __grid_constant__ BatchSortTable tab)
 {
     const BatchSortMap &M = tab.m[batch_sort_map(tab, blockIdx.x, true)];
     seg_scan_body(M.hist, M.nb, M.S + 1, M.meta, blockIdx.x - M.seg_begin);
@@ -1013,7 +1032,8 @@ static int sort_stage(vsaogm_map *m, Scratch &ws, const PatchDev &pt, const floa
         return cuda_error(e, "encode: shared memory");
     StageScope sc(m, VSAOGM_STAGE_SORT, st);
     seg_count_kernel<<<nb, 256, smem_count, st>>>(xy, lab, n, ax, ay, pt, S, hist);
-    seg_scan_kernel<<<S1, kScanThreads, 0, st>>>(hist, nb, S1, meta);
+    seg_scan_kernel<<<(S1 + kScanCols - 1) / kScanCols, 32 * kScanWarps, 0, st>>>(hist, nb,
+                                                                                 S1, meta);
     seg_meta_kernel<<<1, kScanThreads, 0, st>>>(meta, S, chunk, chunks, m->rejected);
     seg_scatter_kernel<<<nb, 256, smem_scatter, st>>>(xy, lab, n, ax, ay, pt, S, hist, meta,
                                                       sorted);
@@ -1051,6 +1071,8 @@ int batch_sort_entry(vsaogm_map *m, Scratch &ws, const PatchDev &pt, const float
     return VSAOGM_OK;
 }
 
+int sort_scan_ctas(int S1) { return (S1 + kScanCols - 1) / kScanCols; }
+
 int launch_sort_batch(const BatchSortTable &tab, int blocks, int segs, int max_s1,
                       cudaStream_t st)
 {
@@ -1063,7 +1085,7 @@ int launch_sort_batch(const BatchSortTable &tab, int blocks, int segs, int max_s
                                   (int)smem_scatter)) != cudaSuccess)
         return cuda_error(e, "batch sort: shared memory");
     batch_seg_count_kernel<<<blocks, 256, smem_count, st>>>(tab);
-    batch_seg_scan_kernel<<<segs, kScanThreads, 0, st>>>(tab);
+    batch_seg_scan_kernel<<<segs, 32 * kScanWarps, 0, st>>>(tab);
     batch_seg_meta_kernel<<<tab.n_maps, kScanThreads, 0, st>>>(tab);
     batch_seg_scatter_kernel<<<blocks, 256, smem_scatter, st>>>(tab);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_error(e, "batch sort");
@@ -1175,7 +1197,8 @@ int encode_bundle(vsaogm_map *m, const float *xy_f, const uint8_t *lab, int64_t 
     {
         StageScope sc(m, VSAOGM_STAGE_SORT, st);
         seg_count_kernel<<<nb, 256, smem_count, st>>>(xy, lab, n, ax, ay, pt, S, hist);
-        seg_scan_kernel<<<S1, kScanThreads, 0, st>>>(hist, nb, S1, meta);
+        seg_scan_kernel<<<(S1 + kScanCols - 1) / kScanCols, 32 * kScanWarps, 0, st>>>(
+            hist, nb, S1, meta);
         seg_meta_kernel<<<1, kScanThreads, 0, st>>>(meta, S, chunk, chunks, m->rejected);
         seg_scatter_kernel<<<nb, 256, smem_scatter, st>>>(xy, lab, n, ax, ay, pt, S, hist, meta,
                                                           sorted);
@@ -1278,7 +1301,8 @@ static int encode_bundle_noalloc(vsaogm_map *m, const float *xy_f, const uint8_t
     // (histograms, offsets, chunk table, sorted points), so nothing has to be
     // cleared; bundling adds straight into the map's memories with atomics.
     seg_count_kernel<<<nb, 256, sizeof(int) * S1, st>>>(xy, lab, n, ax, ay, pt, S, hist);
-    seg_scan_kernel<<<S1, kScanThreads, 0, st>>>(hist, nb, S1, meta);
+    seg_scan_kernel<<<(S1 + kScanCols - 1) / kScanCols, 32 * kScanWarps, 0, st>>>(hist, nb,
+                                                                                 S1, meta);
     seg_meta_kernel<<<1, kScanThreads, 0, st>>>(meta, S, chunk, chunks, m->rejected);
     seg_scatter_kernel<<<nb, 256, smem_scatter, st>>>(xy, lab, n, ax, ay, pt, S, hist, meta,
                                                       sorted);

@@ -128,7 +128,7 @@ struct BatchSortMap {
     float2 *sorted;
     unsigned long long *rejected;
     int nb, blk_begin;      // sort blocks of this map, its first in the launch
-    int seg_begin;          // first scan CTA (segment column) of this map
+    int seg_begin;          // first scan CTA (group of segment columns) of this map
 };
 struct BatchSortTable {
     int n_maps;
@@ -363,9 +363,11 @@ bool patches_near(const vsaogm_map *m, const PatchDev &pt);
 int batch_sort_entry(vsaogm_map *m, Scratch &ws, const PatchDev &pt, const float *xy,
                      const uint8_t *lab, int n, int chunk, BatchSortMap *e, int *max_chunks);
 // the four sort kernels over every entry, one launch each; blocks = sum of nb,
-// segs = sum of S + 1, max_s1 = the largest S + 1
+// segs = sum of sort_scan_ctas(S + 1), max_s1 = the largest S + 1
 int launch_sort_batch(const BatchSortTable &tab, int blocks, int segs, int max_s1,
                       cudaStream_t st);
+// CTAs of the segment scan for S1 segment columns
+int sort_scan_ctas(int S1);
 void batch_encode_entry(const vsaogm_map *m, const Scratch &ws, const PatchDev &pt,
                         BatchEncodeMap *e);
 int encode_batch_ctas();
