@@ -496,7 +496,7 @@ int vsaogm_batch_autotune(vsaogm_batch *b, const float *const *xy, const uint8_t
     Tuning best = b->tune;
     float best_ms = 1e30f;
     // encode shape first (decode fixed), then the decode slicing
-    const int pws[] = {6, 7, 8}, ipcs[] = {4, 8, 16};
+    const int pws[] = {6, 7, 8}, ipcs[] = {8, 16, 32};
     for (int pw : pws)
         for (int ipc : ipcs) {
             if (rc) break;
