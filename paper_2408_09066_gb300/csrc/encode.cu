@@ -391,6 +391,83 @@ __global__ void __launch_bounds__(256) batch_seg_scatter_kernel(const __grid_con
                      blockIdx.x - M.blk_begin, wcnt);
 }
 
+// 1-4 in one CTA for a small call (n <= kSmallSortPoints points, S + 1 <=
+// kSmallSortSegs segments): the same stable counting sort with the 32 warps of
+// one CTA in place of the sort blocks (warp w takes points w * PW .. + PW - 1,
+// in order), so a small update costs one launch instead of four.
+constexpr int kSmallSortWarps = 32;
+constexpr int kSmallSortPoints = 32768;
+constexpr int kSmallSortSegs = 1536;  // 32 x 1536 counters: 192 KB of shared memory
+__global__ void __launch_bounds__(32 * kSmallSortWarps) seg_sort_small_kernel(
+    const float2 *__restrict__ xy, const uint8_t *__restrict__ lab, int n, AxisDev ax,
+    AxisDev ay, PatchDev pt, int S, int chunk, int *__restrict__ meta, int4 *__restrict__ chunks,
+    unsigned long long *rejected, float2 *__restrict__ sorted)
+{
+    extern __shared__ int wcnt[];  // [kSmallSortWarps][S1]: counts, then cursors
+    const int S1 = S + 1;
+    for (int i = threadIdx.x; i < kSmallSortWarps * S1; i += blockDim.x) wcnt[i] = 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int pw = (n + kSmallSortWarps * 32 - 1) / (kSmallSortWarps * 32) * 32;  // points a warp
+    const int base = warp * pw;
+    int *mine = wcnt + warp * S1;
+    for (int r = 0; r < pw; r += 32) {
+        const int i = base + r + lane;
+        int seg = -1;
+        if (i < n) {
+            const float2 p = xy[i];
+            seg = point_segment(p.x, p.y, lab[i], ax, ay, pt, S);
+        }
+        const unsigned peers = __match_any_sync(0xffffffffu, seg);
+        if (seg >= 0 && lane == __ffs(peers) - 1) mine[seg] += __popc(peers);
+        __syncwarp();
+    }
+    __syncthreads();
+    // per segment: the warps' exclusive offsets and the segment's total
+    for (int s = threadIdx.x; s < S1; s += blockDim.x) {
+        int run = 0;
+        for (int w = 0; w < kSmallSortWarps; ++w) {
+            const int c = wcnt[w * S1 + s];
+            wcnt[w * S1 + s] = run;
+            run += c;
+        }
+        meta[s] = run;
+    }
+    __syncthreads();
+    seg_meta_body(meta, S, chunk, chunks, rejected);
+    __syncthreads();
+    const int *seg_base = meta + S1;
+    for (int s = threadIdx.x; s < kSmallSortWarps * S1; s += blockDim.x)
+        wcnt[s] += seg_base[s % S1];
+    __syncthreads();
+    const unsigned lt = (1u << lane) - 1u;
+    for (int r = 0; r < pw; r += 32) {
+        const int i = base + r + lane;
+        int seg = -1;
+        float2 p = make_float2(0.f, 0.f);
+        if (i < n) {
+            p = xy[i];
+            seg = point_segment(p.x, p.y, lab[i], ax, ay, pt, S);
+        }
+        const unsigned peers = __match_any_sync(0xffffffffu, seg);
+        int dst = 0;
+        if (seg >= 0) dst = mine[seg] + __popc(peers & lt);
+        __syncwarp();
+        if (seg >= 0 && lane == __ffs(peers) - 1) mine[seg] += __popc(peers);
+        __syncwarp();
+        if (seg >= 0 && seg < S) {
+            const int mem = seg / pt.n, patch = seg - mem * pt.n;
+            const int beta = mem >> 1;
+            const int bx = beta % ax.n_tiles, by = beta / ax.n_tiles;
+            const float cx = pt.n > 1 ? pt.cx[patch % pt.nx] : 0.f;
+            const float cy = pt.n > 1 ? pt.cy[patch / pt.nx] : 0.f;
+            const float dx = offset_from(p.x, ax.centre[bx], cx);
+            const float dy = offset_from(p.y, ay.centre[by], cy);
+            if (VSAOGM_IN_BOUNDS(dst >= 0 && dst < n)) sorted[dst] = make_float2(dx, dy);
+        }
+    }
+}
+
 // 5. Encode + bundle one chunk of one segment over a slice of 256*KPT
 //    frequencies.  The phase in turns t = nu_x dx + nu_y dy is reduced to
 //    f = t - rint(t) in [-1/2, 1/2] and then one MUFU sin and one MUFU cos of
@@ -1000,46 +1077,41 @@ int reserve_encode(vsaogm_map *m, int64_t n64)
     return VSAOGM_OK;
 }
 
-// Stage 1 of encode + bundle for one map: tile assignment and the stable
-// counting sort into segment order with chunks of at most `chunk` points, in
-// the map's scratch (grown if needed).  Returns the chunk-table bound.
-static int sort_stage(vsaogm_map *m, Scratch &ws, const PatchDev &pt, const float *xy_f,
-                      const uint8_t *lab, int n, int chunk, bool need_partial, cudaStream_t st,
-                      int *max_chunks_out)
+// The sort of one map's call (steps 1-4): one CTA for a small call, else the
+// four kernels.  hist needs nb x (S + 1) ints only for the latter.
+static cudaError_t launch_sort(const float2 *xy, const uint8_t *lab, int n, const AxisDev &ax,
+                               const AxisDev &ay, const PatchDev &pt, int S, int chunk, int *hist,
+                               int *meta, int4 *chunks, unsigned long long *rejected,
+                               float2 *sorted, cudaStream_t st, int *launches)
 {
-    const int S = m->S * pt.n, S1 = S + 1, D = m->cfg.D;
-    const int nb = (n + kSortBlock - 1) / kSortBlock;
-    const int max_chunks = (n + chunk - 1) / chunk + S;
-    *max_chunks_out = max_chunks;
-    int rc;
-    if ((rc = ensure(ws.blk_hist, sizeof(int) * (size_t)nb * S1))) return rc;
-    if ((rc = ensure(ws.seg_meta, sizeof(int) * (size_t)(3 * S1 + 2)))) return rc;
-    if ((rc = ensure(ws.chunks, sizeof(int4) * (size_t)max_chunks))) return rc;
-    if ((rc = ensure(ws.sorted, sizeof(float2) * (size_t)n))) return rc;
-    if (need_partial && (rc = ensure(ws.partial, sizeof(float2) * (size_t)max_chunks * D)))
-        return rc;
-    int *hist = (int *)ws.blk_hist.ptr, *meta = (int *)ws.seg_meta.ptr;
-    int4 *chunks = (int4 *)ws.chunks.ptr;
-    float2 *sorted = (float2 *)ws.sorted.ptr;
-    const float2 *xy = (const float2 *)xy_f;
-    AxisDev ax = axis_x(m), ay = axis_y(m);
+    const int S1 = S + 1;
     cudaError_t e;
+    if (n <= kSmallSortPoints && S1 <= kSmallSortSegs) {
+        const size_t smem = sizeof(int) * kSmallSortWarps * S1;
+        if ((e = cudaFuncSetAttribute(seg_sort_small_kernel,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
+            cudaSuccess)
+            return e;
+        seg_sort_small_kernel<<<1, 32 * kSmallSortWarps, smem, st>>>(
+            xy, lab, n, ax, ay, pt, S, chunk, meta, chunks, rejected, sorted);
+        *launches = 1;
+        return cudaGetLastError();
+    }
+    const int nb = (n + kSortBlock - 1) / kSortBlock;
     const size_t smem_count = sizeof(int) * S1;
     const size_t smem_scatter = sizeof(int) * kSortWarps * S1;
     // opt-in to more than 48 KB of dynamic shared memory (a per-device setting)
     if ((e = cudaFuncSetAttribute(seg_scatter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)smem_scatter)) != cudaSuccess)
-        return cuda_error(e, "encode: shared memory");
-    StageScope sc(m, VSAOGM_STAGE_SORT, st);
+        return e;
     seg_count_kernel<<<nb, 256, smem_count, st>>>(xy, lab, n, ax, ay, pt, S, hist);
-    seg_scan_kernel<<<(S1 + kScanCols - 1) / kScanCols, 32 * kScanWarps, 0, st>>>(hist, nb,
-                                                                                 S1, meta);
-    seg_meta_kernel<<<1, kScanThreads, 0, st>>>(meta, S, chunk, chunks, m->rejected);
+    seg_scan_kernel<<<(S1 + kScanCols - 1) / kScanCols, 32 * kScanWarps, 0, st>>>(hist, nb, S1,
+                                                                                 meta);
+    seg_meta_kernel<<<1, kScanThreads, 0, st>>>(meta, S, chunk, chunks, rejected);
     seg_scatter_kernel<<<nb, 256, smem_scatter, st>>>(xy, lab, n, ax, ay, pt, S, hist, meta,
                                                       sorted);
-    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_error(e, "encode: sort");
-    sc.end(4);
-    return VSAOGM_OK;
+    *launches = 4;
+    return cudaGetLastError();
 }
 
 int batch_sort_entry(vsaogm_map *m, Scratch &ws, const PatchDev &pt, const float *xy,
@@ -1163,7 +1235,6 @@ int launch_encode_batch(const BatchEncodeTable &tab, unsigned long long *counter
     return e == cudaSuccess ? VSAOGM_OK : cuda_error(e, "batch encode");
 }
 
-
 int encode_bundle(vsaogm_map *m, const float *xy_f, const uint8_t *lab, int64_t n64,
                   cudaStream_t st)
 {
@@ -1188,22 +1259,13 @@ int encode_bundle(vsaogm_map *m, const float *xy_f, const uint8_t *lab, int64_t 
     AxisDev ax = axis_x(m), ay = axis_y(m);
     cudaError_t e;
 
-    size_t smem_count = sizeof(int) * S1;
-    size_t smem_scatter = sizeof(int) * kSortWarps * S1;
-    // opt-in to more than 48 KB of dynamic shared memory (a per-device setting)
-    if ((e = cudaFuncSetAttribute(seg_scatter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)smem_scatter)) != cudaSuccess)
-        return cuda_error(e, "encode: shared memory");
     {
         StageScope sc(m, VSAOGM_STAGE_SORT, st);
-        seg_count_kernel<<<nb, 256, smem_count, st>>>(xy, lab, n, ax, ay, pt, S, hist);
-        seg_scan_kernel<<<(S1 + kScanCols - 1) / kScanCols, 32 * kScanWarps, 0, st>>>(
-            hist, nb, S1, meta);
-        seg_meta_kernel<<<1, kScanThreads, 0, st>>>(meta, S, chunk, chunks, m->rejected);
-        seg_scatter_kernel<<<nb, 256, smem_scatter, st>>>(xy, lab, n, ax, ay, pt, S, hist, meta,
-                                                          sorted);
-        if ((e = cudaGetLastError()) != cudaSuccess) return cuda_error(e, "encode: sort");
-        sc.end(4);
+        int launches = 0;
+        if ((e = launch_sort(xy, lab, n, ax, ay, pt, S, chunk, hist, meta, chunks, m->rejected,
+                             sorted, st, &launches)) != cudaSuccess)
+            return cuda_error(e, "encode: sort");
+        sc.end(launches);
     }
     const int *cbeg = meta + S1 + S1 + 1;
     const int *n_chunks = cbeg + S + 1;
@@ -1293,19 +1355,13 @@ static int encode_bundle_noalloc(vsaogm_map *m, const float *xy_f, const uint8_t
     float2 *sorted = (float2 *)(base + b_hist + b_meta + b_chunks);
     const float2 *xy = (const float2 *)xy_f;
     AxisDev ax = axis_x(m), ay = axis_y(m);
-    const size_t smem_scatter = sizeof(int) * kSortWarps * S1;
-    if ((e = cudaFuncSetAttribute(seg_scatter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)smem_scatter)) != cudaSuccess)
-        return cuda_error(e, "encode_noalloc: shared memory");
     // Every scratch word these kernels read is written earlier in the same call
     // (histograms, offsets, chunk table, sorted points), so nothing has to be
     // cleared; bundling adds straight into the map's memories with atomics.
-    seg_count_kernel<<<nb, 256, sizeof(int) * S1, st>>>(xy, lab, n, ax, ay, pt, S, hist);
-    seg_scan_kernel<<<(S1 + kScanCols - 1) / kScanCols, 32 * kScanWarps, 0, st>>>(hist, nb,
-                                                                                 S1, meta);
-    seg_meta_kernel<<<1, kScanThreads, 0, st>>>(meta, S, chunk, chunks, m->rejected);
-    seg_scatter_kernel<<<nb, 256, smem_scatter, st>>>(xy, lab, n, ax, ay, pt, S, hist, meta,
-                                                      sorted);
+    int launches = 0;
+    if ((e = launch_sort(xy, lab, n, ax, ay, pt, S, chunk, hist, meta, chunks, m->rejected,
+                         sorted, st, &launches)) != cudaSuccess)
+        return cuda_error(e, "encode_noalloc: sort");
     const int *n_chunks = meta + S1 + S1 + 1 + S + 1;
     if (m->encode_packed)
         e = launch_packed(m, pt, kpt / 2, sorted, chunks, n_chunks, m->omega, max_chunks, true,
