@@ -28,10 +28,6 @@
 
 static_assert(vsaogm_impl::kMaxBatchMaps == VSAOGM_MAX_BATCH, "batch size limit");
 
-// Average chunks per memory up to which a map's chunk sums run inside the
-// batched encode (above it one CTA walking a memory's chunks at the end of
-// the launch costs more than the separate reduction).
-constexpr int kFusedChunksPerMemory = 16;
 
 using namespace vsaogm_impl;
 

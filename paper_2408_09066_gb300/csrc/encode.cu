@@ -821,23 +821,24 @@ __device__ __forceinline__ void encode_chunk_x2_body(const float2 *__restrict__ 
     }
 }
 
-template <int NP, int NPOLY, bool ATOMIC>
+template <int NP, int NPOLY, bool ATOMIC, bool FUSED>
 __global__ void __launch_bounds__(256) encode_chunk_x2_kernel(const float2 *__restrict__ pts,
                                                               const int4 *__restrict__ chunks,
                                                               const int *__restrict__ n_chunks,
                                                               const float *__restrict__ nu, int D,
                                                               float nu_max_x, float nu_max_y,
                                                               int poly_warps, PatchDev pt,
-                                                              float2 *__restrict__ out)
+                                                              float2 *__restrict__ out,
+                                                              TailSum tail)
 {
     __shared__ float2 sp[kMaxChunk];
     __shared__ unsigned s_bound[2];
     __shared__ int s_tail[3];
     const int c = blockIdx.x;
     if (c >= *n_chunks) return;
-    encode_chunk_x2_body<NP, NPOLY, ATOMIC, false>(pts, chunks[c], c, blockIdx.y, nu, D,
-                                                   nu_max_x, nu_max_y, poly_warps, pt, out,
-                                                   TailSum{}, sp, s_bound, s_tail);
+    encode_chunk_x2_body<NP, NPOLY, ATOMIC, FUSED>(pts, chunks[c], c, blockIdx.y, nu, D,
+                                                   nu_max_x, nu_max_y, poly_warps, pt, out, tail,
+                                                   sp, s_bound, s_tail);
 }
 
 // 5''. Many maps in one persistent launch.  Work items are (map, chunk,
@@ -932,35 +933,48 @@ constexpr int kAutoPolyWarps4Near = 8;  // 4 pairs per thread, phases below 4 tu
 constexpr int kAutoPolyWarps4 = 6;      // 4 pairs per thread otherwise: 6/32
 constexpr int kAutoPolyWarps2 = 3;      // 2 pairs per thread: 3/16
 
+// cbeg non-null: the chunk sums run inside the launch (the last CTA of each
+// memory and slice adds the memory's chunks in order; see encode_chunk_x2_body)
 template <int NP, int NPOLY>
 cudaError_t launch_x2(const vsaogm_map *m, const PatchDev &pt, const float2 *pts,
                       const int4 *chunks, const int *n_chunks, float2 *out, int max_chunks,
-                      bool atomic, int pw, cudaStream_t st)
+                      bool atomic, int pw, cudaStream_t st, const int *cbeg = nullptr)
 {
     const int D = m->cfg.D;
     dim3 grid(max_chunks, (D + 512 * NP - 1) / (512 * NP));
+    const TailSum tail{cbeg, m->enc_cnt, m->omega, (int)grid.y};
     if (atomic)
-        encode_chunk_x2_kernel<NP, NPOLY, true><<<grid, 256, 0, st>>>(
-            pts, chunks, n_chunks, m->nu, D, m->nu_max[0], m->nu_max[1], pw, pt, out);
+        encode_chunk_x2_kernel<NP, NPOLY, true, false><<<grid, 256, 0, st>>>(
+            pts, chunks, n_chunks, m->nu, D, m->nu_max[0], m->nu_max[1], pw, pt, out, tail);
+    else if (cbeg && NPOLY < 0)
+        encode_chunk_x2_kernel<NP, NPOLY, false, NPOLY < 0><<<grid, 256, 0, st>>>(
+            pts, chunks, n_chunks, m->nu, D, m->nu_max[0], m->nu_max[1], pw, pt, out, tail);
     else
-        encode_chunk_x2_kernel<NP, NPOLY, false><<<grid, 256, 0, st>>>(
-            pts, chunks, n_chunks, m->nu, D, m->nu_max[0], m->nu_max[1], pw, pt, out);
+        encode_chunk_x2_kernel<NP, NPOLY, false, false><<<grid, 256, 0, st>>>(
+            pts, chunks, n_chunks, m->nu, D, m->nu_max[0], m->nu_max[1], pw, pt, out, tail);
     return cudaGetLastError();
 }
 
+// cbeg non-null asks for the fused chunk sums; returns in *fused whether the
+// launch does them (the mixed-polynomial kernels only), else the caller sums.
 cudaError_t launch_packed(const vsaogm_map *m, const PatchDev &pt, int np, const float2 *pts,
                           const int4 *chunks, const int *n_chunks, float2 *out, int max_chunks,
-                          bool atomic, cudaStream_t st)
+                          bool atomic, cudaStream_t st, const int *cbeg = nullptr,
+                          bool *fused = nullptr)
 {
+    if (fused) *fused = false;
     const int npoly = std::min(m->encode_poly_pairs, np);
     const bool near = patches_near(m, pt);
     const int pw = m->encode_poly_warps >= 0
                        ? m->encode_poly_warps
                        : (np == 4 ? (near ? kAutoPolyWarps4Near : kAutoPolyWarps4) : kAutoPolyWarps2);
     if (npoly == 0 && pw > 0) {  // mixed: some warps with one polynomial pair
+        if (fused) *fused = cbeg && !atomic;
         if (np == 4)
-            return launch_x2<4, -1>(m, pt, pts, chunks, n_chunks, out, max_chunks, atomic, pw, st);
-        return launch_x2<2, -1>(m, pt, pts, chunks, n_chunks, out, max_chunks, atomic, pw, st);
+            return launch_x2<4, -1>(m, pt, pts, chunks, n_chunks, out, max_chunks, atomic, pw, st,
+                                    cbeg);
+        return launch_x2<2, -1>(m, pt, pts, chunks, n_chunks, out, max_chunks, atomic, pw, st,
+                                cbeg);
     }
 #define VSA_X2(NPV, NPOLYV) \
     launch_x2<NPV, NPOLYV>(m, pt, pts, chunks, n_chunks, out, max_chunks, atomic, 0, st)
@@ -1270,11 +1284,16 @@ int encode_bundle(vsaogm_map *m, const float *xy_f, const uint8_t *lab, int64_t 
     const int *cbeg = meta + S1 + S1 + 1;
     const int *n_chunks = cbeg + S + 1;
     float2 *out = atomic ? m->omega : (float2 *)m->ws.partial.ptr;
+    bool fused = false;
     {
         StageScope sc(m, VSAOGM_STAGE_ENCODE, st);
+        // a call whose memories hold few chunks each sums them in the same
+        // launch (one launch less on small calls); many chunks per memory keep
+        // the separate reduction, which spreads each memory over many CTAs
+        const bool want_fused = (n + chunk - 1) / chunk <= kFusedChunksPerMemory * m->S;
         if (m->encode_packed)
             e = launch_packed(m, pt, kpt / 2, sorted, chunks, n_chunks, out, max_chunks, atomic,
-                              st);
+                              st, want_fused ? cbeg : nullptr, &fused);
         else if (kpt == 4)
             e = launch_encode<4>(m, pt, sorted, chunks, n_chunks, out, max_chunks, atomic, st);
         else if (kpt == 2)
@@ -1284,7 +1303,7 @@ int encode_bundle(vsaogm_map *m, const float *xy_f, const uint8_t *lab, int64_t 
         if (e != cudaSuccess) return cuda_error(e, "encode: bundle");
         sc.end(1);
     }
-    if (!atomic) {
+    if (!atomic && !fused) {
         StageScope sc(m, VSAOGM_STAGE_REDUCE, st);
         dim3 grid((D + 255) / 256, m->S);
         reduce_partials_kernel<<<grid, 256, 0, st>>>((const float2 *)m->ws.partial.ptr, cbeg, D,

@@ -134,6 +134,11 @@ struct BatchSortTable {
     int n_maps;
     BatchSortMap m[kMaxBatchMaps];
 };
+// Average chunks per memory up to which a call's chunk sums run inside the
+// encode launch (above it one CTA walking a memory's chunks at the end of the
+// launch costs more than the separate reduction).
+constexpr int kFusedChunksPerMemory = 16;
+
 // The bundling's fixed-order chunk sums, fused into the encode: the last CTA
 // to finish a (memory, frequency slice) adds that memory's chunk partials for
 // the slice to the memory, in chunk order.
