@@ -396,7 +396,7 @@ __global__ void __launch_bounds__(256) batch_seg_scatter_kernel(const __grid_con
 // one CTA in place of the sort blocks (warp w takes points w * PW .. + PW - 1,
 // in order), so a small update costs one launch instead of four.
 constexpr int kSmallSortWarps = 32;
-constexpr int kSmallSortPoints = 32768;
+constexpr int kSmallSortPoints = 8192;
 constexpr int kSmallSortSegs = 1536;  // 32 x 1536 counters: 192 KB of shared memory
 __global__ void __launch_bounds__(32 * kSmallSortWarps) seg_sort_small_kernel(
     const float2 *__restrict__ xy, const uint8_t *__restrict__ lab, int n, AxisDev ax,
