@@ -8,8 +8,10 @@
 // with A(i, k) = exp(i 2 pi nu_x[k] dx_i) and U_psi = conj(w_hat_psi[k]) *
 // exp(i 2 pi nu_y[k] dy_j): the sum over k' is Re sum_k U A, i.e. Eq. loc-query
 // in its separable form.  Both operands are generated in shared memory (sin/cos
-// after an exact phase reduction, then the complex product), never read from
-// HBM, in the 128-byte-swizzled K-major layout the tensor cores read.
+// after an exact phase reduction for a thread's first row or column, a complex
+// multiply by the map's 16-cell step phasor for the next ones, then the
+// complex product with the memories), never read from HBM, in the
+// 128-byte-swizzled K-major layout the tensor cores read.
 //
 // Precision: each operand is split x = hi + lo in BF16, FP16 or FP8 (e4m3) and
 // the product is hi*hi + hi*lo + lo*hi with FP32 accumulation in tensor memory:
@@ -29,8 +31,9 @@
 // x 4 K-steps of 32 bytes) and commits them to the buffer's mbarrier.  The
 // 128-byte swizzle puts 4-byte word kk of row m at byte
 // m * 128 + ((kk / 4) xor (m mod 8)) * 16 + (kk mod 4) * 4.  The epilogue reads
-// the two 128 x N FP32 accumulators from tensor memory and writes per-slice
-// partial maps; a second kernel sums the slices in a fixed order and folds the
+// the two 128 x N FP32 accumulators from tensor memory, stages each warp's rows
+// in shared memory and writes per-slice partial maps in whole row segments; a
+// second kernel sums the slices in a fixed order and folds the
 // per-class maxima (Eq. non-linearities needs the map maximum).  Every wait is
 // bounded: on time-out the CTA records VSAOGM_E_TIMEOUT, drains its MMAs, frees
 // its tensor memory and returns.
