@@ -328,3 +328,21 @@ def test_single_point_far_from_a_wide_tile_centre():
     got = run_gpu(cfg, pts, np.array([1], np.uint8))
     want = _oracle_all(cfg, pts, np.array([1], np.uint8))
     assert np.abs(got["omega"] - want["omega"]).max() <= TOL_OMEGA
+
+
+@pytest.mark.parametrize("n", [8192, 8193])
+def test_sort_paths_either_side_of_the_one_cta_bound(n):
+    """Up to 8192 points the four sort steps run in one CTA, above it as four
+    kernels; both give the oracle's memories and maps and are bitwise
+    reproducible (a stable counting sort either way)."""
+    import dataclasses
+    wl = synth.batch_maps(n_maps=1, seed=51, min_cells=80, max_cells=80, min_points=9000,
+                          max_points=9000, max_tiles=1, dims=(1024,))[0]
+    wl = dataclasses.replace(wl, xy=wl.xy[:n].copy(), labels=wl.labels[:n].copy(), tiles_x=4,
+                             tiles_y=4)
+    cfg = config_for(wl)
+    a = run_gpu(cfg, wl.xy, wl.labels)
+    _check_all(cfg, a, _oracle_all(cfg, wl.xy, wl.labels))
+    b = run_gpu(cfg, wl.xy, wl.labels)
+    for k in ("omega", "P", "occ"):
+        assert np.array_equal(a[k], b[k]), k
