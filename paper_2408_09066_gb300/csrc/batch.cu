@@ -498,7 +498,7 @@ int vsaogm_batch_autotune(vsaogm_batch *b, const float *const *xy, const uint8_t
             if (rc) break;
             b->tune.poly_warps = pw;
             b->tune.items_per_cta = ipc;
-            float ms;
+            float ms = 0.f;
             if ((rc = time_step(&ms))) break;
             if (ms < best_ms) {
                 best_ms = ms;
@@ -510,7 +510,7 @@ int vsaogm_batch_autotune(vsaogm_batch *b, const float *const *xy, const uint8_t
     for (int w : waves) {
         if (rc) break;
         b->tune.decode_waves = w;
-        float ms;
+        float ms = 0.f;
         if ((rc = time_step(&ms))) break;
         if (ms < best_ms) {
             best_ms = ms;
@@ -523,7 +523,7 @@ int vsaogm_batch_autotune(vsaogm_batch *b, const float *const *xy, const uint8_t
     for (int f : fines) {
         if (rc) break;
         b->tune.fine_min = f;
-        float ms;
+        float ms = 0.f;
         if ((rc = time_step(&ms))) break;
         if (ms < best_ms) {
             best_ms = ms;

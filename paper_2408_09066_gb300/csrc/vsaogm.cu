@@ -385,7 +385,8 @@ int vsaogm_create(const vsaogm_config *cfg, vsaogm_map **out)
         m->tile_last[0] = ax.last;
         m->tile_first[1] = ay.first;
         m->tile_last[1] = ay.last;
-        if ((rc = upload(&m->status, std::vector<int>(1, 0)))) break;
+        const std::vector<int> status0(1, 0);
+        if ((rc = upload(&m->status, status0))) break;
         disk_half_widths(cfg->r_emp, m->r_hw[0]);
         disk_half_widths(cfg->r_occ, m->r_hw[1]);
         // Memories and per-map device state.
