@@ -299,7 +299,7 @@ DATA = ("synthetic: seeded 100-scan lidar trajectory in a walled 40 m world with
 # DRAM traffic of one encode launch on this workload from an ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum = 24.55 MB + 114.55 MB), valid
 # only for the kernel source it was taken on (sha1 of csrc/encode.cu).
-ENCODE_TRAFFIC = {"sha1": "a4cf82ff28d87afa8e98dab86b1a4cf7a20d44c9", "bytes": 139100416}
+ENCODE_TRAFFIC = {"sha1": "872e55d45d44b2547ffe11644075195633022ab1", "bytes": 139104256}
 
 
 def workload_config(wl, decode: str) -> dict:

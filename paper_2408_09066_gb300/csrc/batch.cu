@@ -5,7 +5,8 @@
 // Stages of a step:
 //   reset (optional)  : memset of each map's memories
 //   sort              : tile assignment + counting sort of every map, four
-//                       launches (count, scan, chunk table, scatter)
+//                       launches (count, scan, chunk table, scatter), plus
+//                       one launch sorting each small map in one CTA
 //   encode            : ONE persistent launch over every map's (chunk,
 //                       frequency slice) items, claimed from an atomic counter;
 //                       for maps with few chunks per memory the last CTA of
@@ -166,8 +167,10 @@ int enqueue_step(vsaogm_batch *b, const float *const *xy, const uint8_t *const *
                 return cuda_error(e, "batch reset");
     // ---- encode: the sorts of every map (four launches), then one launch
     const int chunk = batch_chunk(b, n);
-    BatchSortTable sot;
+    BatchSortTable sot, sos;  // maps sorted by the four kernels / in one CTA each
     memset(&sot, 0, sizeof(sot));
+    memset(&sos, 0, sizeof(sos));
+    int small_s1 = 0;
     BatchEncodeTable et;
     memset(&et, 0, sizeof(et));
     BatchReduceTable rt;
@@ -179,15 +182,20 @@ int enqueue_step(vsaogm_batch *b, const float *const *xy, const uint8_t *const *
         int max_chunks = 0;
         const PatchDev &pt = choose_patches(m, n[i], b->tune.fine_min);
         if (n[i] > 0) {
-            BatchSortMap &sm = sot.m[sot.n_maps++];
+            const bool small = sort_small((int)n[i], m->S * pt.n + 1);
+            BatchSortMap &sm = small ? sos.m[sos.n_maps++] : sot.m[sot.n_maps++];
             if ((rc = batch_sort_entry(m, b->ws[i], pt, xy[i], lab[i], (int)n[i], chunk, &sm,
                                        &max_chunks)))
                 return rc;
-            sm.blk_begin = sort_blocks;
-            sm.seg_begin = sort_segs;
-            sort_blocks += sm.nb;
-            sort_segs += sort_scan_ctas(sm.S + 1);
-            max_s1 = std::max(max_s1, sm.S + 1);
+            if (small) {
+                small_s1 = std::max(small_s1, sm.S + 1);
+            } else {
+                sm.blk_begin = sort_blocks;
+                sm.seg_begin = sort_segs;
+                sort_blocks += sm.nb;
+                sort_segs += sort_scan_ctas(sm.S + 1);
+                max_s1 = std::max(max_s1, sm.S + 1);
+            }
         }
         BatchEncodeMap &em = et.m[i];
         batch_encode_entry(m, b->ws[i], pt, &em);
@@ -210,7 +218,11 @@ int enqueue_step(vsaogm_batch *b, const float *const *xy, const uint8_t *const *
     }
     if (sot.n_maps > 0) {
         if ((rc = launch_sort_batch(sot, sort_blocks, sort_segs, max_s1, st))) return rc;
-        counted[VSAOGM_STAGE_SORT] = 4;
+        counted[VSAOGM_STAGE_SORT] += 4;
+    }
+    if (sos.n_maps > 0) {
+        if ((rc = launch_sort_small_batch(sos, small_s1, st))) return rc;
+        counted[VSAOGM_STAGE_SORT] += 1;
     }
     mark();
     et.n_maps = M;

@@ -398,12 +398,13 @@ __global__ void __launch_bounds__(256) batch_seg_scatter_kernel(const __grid_con
 constexpr int kSmallSortWarps = 32;
 constexpr int kSmallSortPoints = 8192;
 constexpr int kSmallSortSegs = 1536;  // 32 x 1536 counters: 192 KB of shared memory
-__global__ void __launch_bounds__(32 * kSmallSortWarps) seg_sort_small_kernel(
-    const float2 *__restrict__ xy, const uint8_t *__restrict__ lab, int n, AxisDev ax,
-    AxisDev ay, PatchDev pt, int S, int chunk, int *__restrict__ meta, int4 *__restrict__ chunks,
-    unsigned long long *rejected, float2 *__restrict__ sorted)
+__device__ __forceinline__ void seg_sort_small_body(
+    const float2 *__restrict__ xy, const uint8_t *__restrict__ lab, int n, const AxisDev &ax,
+    const AxisDev &ay, const PatchDev &pt, int S, int chunk, int *__restrict__ meta,
+    int4 *__restrict__ chunks, unsigned long long *rejected, float2 *__restrict__ sorted,
+    int *wcnt)
 {
-    extern __shared__ int wcnt[];  // [kSmallSortWarps][S1]: counts, then cursors
+    // wcnt: [kSmallSortWarps][S1]: counts, then cursors
     const int S1 = S + 1;
     for (int i = threadIdx.x; i < kSmallSortWarps * S1; i += blockDim.x) wcnt[i] = 0;
     __syncthreads();
@@ -466,6 +467,25 @@ __global__ void __launch_bounds__(32 * kSmallSortWarps) seg_sort_small_kernel(
             if (VSAOGM_IN_BOUNDS(dst >= 0 && dst < n)) sorted[dst] = make_float2(dx, dy);
         }
     }
+}
+
+__global__ void __launch_bounds__(32 * kSmallSortWarps) seg_sort_small_kernel(
+    const float2 *__restrict__ xy, const uint8_t *__restrict__ lab, int n, AxisDev ax,
+    AxisDev ay, PatchDev pt, int S, int chunk, int *__restrict__ meta, int4 *__restrict__ chunks,
+    unsigned long long *rejected, float2 *__restrict__ sorted)
+{
+    extern __shared__ int wcnt[];
+    seg_sort_small_body(xy, lab, n, ax, ay, pt, S, chunk, meta, chunks, rejected, sorted, wcnt);
+}
+
+// The small maps of a batch: one CTA each.
+__global__ void __launch_bounds__(32 * kSmallSortWarps) batch_seg_sort_small_kernel(
+    const __grid_constant__ BatchSortTable tab)
+{
+    extern __shared__ int wcnt[];
+    const BatchSortMap &M = tab.m[blockIdx.x];
+    seg_sort_small_body(M.xy, M.lab, M.n, M.ax, M.ay, M.pt, M.S, M.chunk, M.meta, M.chunks,
+                        M.rejected, M.sorted, wcnt);
 }
 
 // 5. Encode + bundle one chunk of one segment over a slice of 256*KPT
@@ -1100,7 +1120,7 @@ static cudaError_t launch_sort(const float2 *xy, const uint8_t *lab, int n, cons
 {
     const int S1 = S + 1;
     cudaError_t e;
-    if (n <= kSmallSortPoints && S1 <= kSmallSortSegs) {
+    if (sort_small(n, S1)) {
         const size_t smem = sizeof(int) * kSmallSortWarps * S1;
         if ((e = cudaFuncSetAttribute(seg_sort_small_kernel,
                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
@@ -1158,6 +1178,20 @@ int batch_sort_entry(vsaogm_map *m, Scratch &ws, const PatchDev &pt, const float
 }
 
 int sort_scan_ctas(int S1) { return (S1 + kScanCols - 1) / kScanCols; }
+
+bool sort_small(int n, int S1) { return n <= kSmallSortPoints && S1 <= kSmallSortSegs; }
+
+int launch_sort_small_batch(const BatchSortTable &tab, int max_s1, cudaStream_t st)
+{
+    if (tab.n_maps <= 0) return VSAOGM_OK;
+    const size_t smem = sizeof(int) * kSmallSortWarps * max_s1;
+    cudaError_t e = cudaFuncSetAttribute(batch_seg_sort_small_kernel,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return cuda_error(e, "batch sort: shared memory");
+    batch_seg_sort_small_kernel<<<tab.n_maps, 32 * kSmallSortWarps, smem, st>>>(tab);
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_error(e, "batch sort");
+    return VSAOGM_OK;
+}
 
 int launch_sort_batch(const BatchSortTable &tab, int blocks, int segs, int max_s1,
                       cudaStream_t st)

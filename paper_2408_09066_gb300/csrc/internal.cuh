@@ -373,6 +373,10 @@ int launch_sort_batch(const BatchSortTable &tab, int blocks, int segs, int max_s
                       cudaStream_t st);
 // CTAs of the segment scan for S1 segment columns
 int sort_scan_ctas(int S1);
+// whether a call of n points over S1 - 1 segments sorts in one CTA, and that
+// sort for every entry of a table (one CTA each; max_s1 the largest S + 1)
+bool sort_small(int n, int S1);
+int launch_sort_small_batch(const BatchSortTable &tab, int max_s1, cudaStream_t st);
 void batch_encode_entry(const vsaogm_map *m, const Scratch &ws, const PatchDev &pt,
                         BatchEncodeMap *e);
 int encode_batch_ctas();

@@ -356,10 +356,12 @@ def test_stage_timing_and_launch_counts():
         st = r.batch.stage_times(reset=True)
         # maps with few chunks per memory sum them inside the encode launch;
         # the reduce launch runs only for the others
+        # small maps sort in one CTA each (one launch), the others in four
         launched = {k: v[1] for k, v in st.items()}
         assert launched["reduce"] in (0, 1)
-        per_step = {"sort": 4, "encode": 1, "reduce": launched["reduce"], "norms": 1,
-                    "decode": 3, "nonlinear": 0, "entropy": 1}
+        assert launched["sort"] in (1, 4, 5)
+        per_step = {"sort": launched["sort"], "encode": 1, "reduce": launched["reduce"],
+                    "norms": 1, "decode": 3, "nonlinear": 0, "entropy": 1}
         assert launched == per_step
         assert all(st[k][0] > 0 for k in ("sort", "encode", "norms", "decode",
                                           "entropy"))
