@@ -32,17 +32,23 @@ _lock = threading.Lock()
 _lib = None
 
 
+def compile_source(src: str, out: str) -> str:
+    """Compile the C source ``src`` into the shared library ``out`` with the
+    oracle's flags (gcc, OpenMP, no FP contraction)."""
+    tmp = out + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-fopenmp", "-ffp-contract=off", "-fPIC", "-shared",
+           "-o", tmp, src, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, out)
+    return out
+
+
 def build(force: bool = False) -> str:
-    """Compile ``oracle.c`` into ``liboracle.so`` with gcc (OpenMP, no FP contraction)."""
+    """Compile ``oracle.c`` into ``liboracle.so`` unless it is up to date."""
     if (not force and os.path.exists(_LIB)
             and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC)):
         return _LIB
-    tmp = _LIB + f".tmp{os.getpid()}"
-    cmd = ["gcc", "-O2", "-fopenmp", "-ffp-contract=off", "-fPIC", "-shared",
-           "-o", tmp, _SRC, "-lm"]
-    subprocess.run(cmd, check=True)
-    os.replace(tmp, _LIB)
-    return _LIB
+    return compile_source(_SRC, _LIB)
 
 
 class _Grid(ctypes.Structure):
@@ -71,51 +77,57 @@ class Grid:
         return _Grid(self.W, self.H, self.res, self.x_min, self.y_min, self.tiles_x, self.tiles_y)
 
 
+def bind(path: str):
+    """Load a library built from ``oracle.c`` (or a test's altered copy of it)
+    and declare the C signatures of its entry points."""
+    lib = ctypes.CDLL(path)
+    P = ctypes.POINTER
+    lib.orc_num_threads.restype = ctypes.c_int32
+    lib.orc_num_threads.argtypes = []
+    lib.orc_splitmix64_at.restype = ctypes.c_uint64
+    lib.orc_splitmix64_at.argtypes = [ctypes.c_uint64, ctypes.c_uint64]
+    lib.orc_draw_nu.argtypes = [ctypes.c_uint64, ctypes.c_int32, ctypes.c_double,
+                                ctypes.c_void_p, ctypes.c_void_p]
+    lib.orc_tile_of.restype = ctypes.c_int32
+    lib.orc_tile_of.argtypes = [P(_Grid), ctypes.c_double, ctypes.c_double]
+    lib.orc_tile_centre.argtypes = [P(_Grid), ctypes.c_int32, P(ctypes.c_double),
+                                    P(ctypes.c_double)]
+    lib.orc_assign.argtypes = [P(_Grid), ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]
+    lib.orc_memories.restype = ctypes.c_int32
+    lib.orc_memories.argtypes = [P(_Grid), ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
+                                 ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
+                                 ctypes.c_int32, ctypes.c_void_p, ctypes.c_int32,
+                                 ctypes.c_void_p, ctypes.c_void_p]
+    lib.orc_norms.argtypes = [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32,
+                              ctypes.c_void_p]
+    lib.orc_decode_cells.argtypes = [P(_Grid), ctypes.c_int32, ctypes.c_void_p,
+                                     ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
+                                     ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
+                                     ctypes.c_void_p]
+    lib.orc_decode_map.argtypes = [P(_Grid), ctypes.c_int32, ctypes.c_void_p,
+                                   ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
+                                   ctypes.c_void_p, ctypes.c_void_p]
+    lib.orc_direct_cells.argtypes = [P(_Grid), ctypes.c_int32, ctypes.c_void_p,
+                                     ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                     ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64,
+                                     ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+    lib.orc_nonlinear.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
+                                  ctypes.c_void_p]
+    lib.orc_entropy.argtypes = [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32,
+                                ctypes.c_int32, ctypes.c_void_p]
+    lib.orc_softmax_psd.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
+                                    ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+    lib.orc_classify_f32.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_float,
+                                     ctypes.c_void_p]
+    return lib
+
+
 def _load():
     global _lib
     with _lock:
         if _lib is None:
             build()
-            lib = ctypes.CDLL(_LIB)
-            P = ctypes.POINTER
-            lib.orc_num_threads.restype = ctypes.c_int32
-            lib.orc_num_threads.argtypes = []
-            lib.orc_splitmix64_at.restype = ctypes.c_uint64
-            lib.orc_splitmix64_at.argtypes = [ctypes.c_uint64, ctypes.c_uint64]
-            lib.orc_draw_nu.argtypes = [ctypes.c_uint64, ctypes.c_int32, ctypes.c_double,
-                                        ctypes.c_void_p, ctypes.c_void_p]
-            lib.orc_tile_of.restype = ctypes.c_int32
-            lib.orc_tile_of.argtypes = [P(_Grid), ctypes.c_double, ctypes.c_double]
-            lib.orc_tile_centre.argtypes = [P(_Grid), ctypes.c_int32, P(ctypes.c_double),
-                                            P(ctypes.c_double)]
-            lib.orc_assign.argtypes = [P(_Grid), ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]
-            lib.orc_memories.restype = ctypes.c_int32
-            lib.orc_memories.argtypes = [P(_Grid), ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
-                                         ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
-                                         ctypes.c_int32, ctypes.c_void_p, ctypes.c_int32,
-                                         ctypes.c_void_p, ctypes.c_void_p]
-            lib.orc_norms.argtypes = [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32,
-                                      ctypes.c_void_p]
-            lib.orc_decode_cells.argtypes = [P(_Grid), ctypes.c_int32, ctypes.c_void_p,
-                                             ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
-                                             ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
-                                             ctypes.c_void_p]
-            lib.orc_decode_map.argtypes = [P(_Grid), ctypes.c_int32, ctypes.c_void_p,
-                                           ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
-                                           ctypes.c_void_p, ctypes.c_void_p]
-            lib.orc_direct_cells.argtypes = [P(_Grid), ctypes.c_int32, ctypes.c_void_p,
-                                             ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
-                                             ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64,
-                                             ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
-            lib.orc_nonlinear.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
-                                          ctypes.c_void_p]
-            lib.orc_entropy.argtypes = [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32,
-                                        ctypes.c_int32, ctypes.c_void_p]
-            lib.orc_softmax_psd.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
-                                            ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
-            lib.orc_classify_f32.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_float,
-                                             ctypes.c_void_p]
-            _lib = lib
+            _lib = bind(_LIB)
     return _lib
 
 
