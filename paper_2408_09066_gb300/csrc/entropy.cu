@@ -173,26 +173,43 @@ __host__ __device__ constexpr int disk_hw(int r, int dy)
     return w;
 }
 
-// One disk row (offset DY) of a cell's disk sum as the difference of two
-// running sums; `base` points at the cell's column in its own row.  The row's
-// half-width is a template constant.
-template <int R, int DY, int PITCH>
-__device__ __forceinline__ float disk_row(const float *base)
+// Disk sums of four vertically adjacent output cells of one column, rows
+// ly0 .. ly0 + 3.  Staged row ly0 + T (T in [-R, R + 3]) enters output row Q at
+// offset dy = T - Q with the disk's half-width w at dy, as the difference of
+// two running sums; `base` points at the column of output row ly0.  Offsets
+// and half-widths are template constants, so a (row, half-width) difference
+// that several of the four outputs share is loaded once.
+template <int R, int PITCH, int T, int Q>
+__device__ __forceinline__ void disk_term(const float *base, float (&h)[4])
 {
-    constexpr int w = disk_hw(R, DY);
-    static_assert(w >= 0, "rows of the disk only");
-    return base[DY * PITCH + w + 1] - base[DY * PITCH - w];
+    constexpr int dy = T - Q;
+    if constexpr (dy >= -R && dy <= R) {
+        constexpr int w = disk_hw(R, dy);
+        static_assert(w >= 0, "rows of the disk only");
+        h[Q] += base[T * PITCH + w + 1] - base[T * PITCH - w];
+    }
+}
+template <int R, int PITCH, int T, int... Q>
+__device__ __forceinline__ void disk_row4(const float *base, float (&h)[4],
+                                          std::integer_sequence<int, Q...>)
+{
+    (disk_term<R, PITCH, T, Q>(base, h), ...);
 }
 template <int R, int PITCH, int... I>
-__device__ __forceinline__ float disk_sum(const float *base, std::integer_sequence<int, I...>)
+__device__ __forceinline__ void disk_sum4(const float *base, float (&h)[4],
+                                          std::integer_sequence<int, I...>)
 {
-    return (0.f + ... + disk_row<R, I - R, PITCH>(base));
+    (disk_row4<R, PITCH, I - R>(base, h, std::make_integer_sequence<int, 4>{}), ...);
 }
+
+constexpr int kEntThreads = 256;  // threads per entropy CTA (8 warps)
 
 // The entropy stencil for the common case of one disk radius R (<= 8) for
 // both classes: the same computation as entropy_body with every loop bound,
-// staged extent and disk half-width known at compile time, so no instruction
-// is spent on loop control or on staging rows that do not exist.
+// staged extent and disk half-width known at compile time.  Staging walks the
+// (32 + 2R)^2 staged cells of both classes as one flat range (no lane idles on
+// a row's ragged end), and each thread sums the disks of four vertically
+// adjacent cells of one column, so the disk rows they share are read once.
 template <int R>
 __device__ __forceinline__ void entropy_fixed_body(const float *__restrict__ heat, int W, int H,
                                                    int wx0, int wy0, int ww, int wh, int raw,
@@ -203,8 +220,9 @@ __device__ __forceinline__ void entropy_fixed_body(const float *__restrict__ hea
                                                    uint8_t *__restrict__ cls, int bx0, int by0,
                                                    float *sh)
 {
-    constexpr int E = kTB + 2 * R, PITCH = E + 1;
-    constexpr int ROWS = (E + 7) / 8, STRIPS = (E + 31) / 32;
+    constexpr int E = kTB + 2 * R, PITCH = E + 1, EE = E * E;
+    constexpr int SLOTS = (EE + kEntThreads - 1) / kEntThreads;
+    static_assert(kTB == 32 && kEntThreads == 256, "8 warps of 4 output rows each");
     const int x0 = wx0 + bx0, y0 = wy0 + by0;
     float inv[2] = {1.f, 1.f};
     const bool norm = raw && !(mode & VSAOGM_MODE_NO_NORM);
@@ -216,42 +234,43 @@ __device__ __forceinline__ void entropy_fixed_body(const float *__restrict__ hea
         }
     }
     const size_t cells = (size_t)W * H;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    float v[2][ROWS][STRIPS];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    // Stage: staged cell e = ly * E + lx of both classes; every load of the
+    // thread is issued before any is used.  Off-grid cells read as 0, whose
+    // summand is 0.
+    float v0[SLOTS], v1[SLOTS];
 #pragma unroll
-    for (int c = 0; c < 2; ++c)
+    for (int i = 0; i < SLOTS; ++i) {
+        const int e = tid + kEntThreads * i;
+        const int ly = e / E, lx = e - ly * E;
+        const int y = y0 - R + ly, x = x0 - R + lx;
+        const bool ok = e < EE && x >= 0 && x < W && y >= 0 && y < H;
+        const size_t g = (size_t)y * W + x;
+        v0[i] = ok ? __ldg(heat + g) : 0.f;
+        v1[i] = ok ? __ldg(heat + cells + g) : 0.f;
+    }
 #pragma unroll
-        for (int i = 0; i < ROWS; ++i)
-#pragma unroll
-            for (int q = 0; q < STRIPS; ++q) {
-                const int ly = warp + 8 * i, lx = lane + 32 * q;
-                const int y = y0 - R + ly, x = x0 - R + lx;
-                v[c][i][q] = (ly < E && lx < E && x >= 0 && x < W && y >= 0 && y < H)
-                                 ? __ldg(heat + c * cells + (size_t)y * W + x)
-                                 : 0.f;
+    for (int i = 0; i < SLOTS; ++i) {
+        const int e = tid + kEntThreads * i;
+        if (e < EE) {
+            const int ly = e / E, lx = e - ly * E;
+            float a = v0[i], b = v1[i];
+            if (norm) {
+                a *= inv[0];
+                b *= inv[1];
             }
-#pragma unroll
-    for (int c = 0; c < 2; ++c)
-#pragma unroll
-        for (int i = 0; i < ROWS; ++i) {
-            const int ly = warp + 8 * i;
-            if (ly >= E) continue;
-            float *row = sh + (c * E + ly) * PITCH;
-            if (lane == 0) row[0] = 0.f;
-#pragma unroll
-            for (int q = 0; q < STRIPS; ++q) {
-                const int lx = lane + 32 * q;
-                if (lx < E) {
-                    float x = v[c][i][q];
-                    if (norm) x *= inv[c];
-                    if (square) x = x * x;
-                    row[1 + lx] = x > 0.f ? -x * __logf(x) : 0.f;
-                }
+            if (square) {
+                a = a * a;
+                b = b * b;
             }
+            sh[ly * PITCH + 1 + lx] = a > 0.f ? -a * __logf(a) : 0.f;
+            sh[(E + ly) * PITCH + 1 + lx] = b > 0.f ? -b * __logf(b) : 0.f;
         }
+    }
+    if (tid < 2 * E) sh[tid * PITCH] = 0.f;
     __syncthreads();
-    if ((int)threadIdx.x < 2 * E) {
-        float *row = sh + threadIdx.x * PITCH + 1;
+    if (tid < 2 * E) {
+        float *row = sh + tid * PITCH + 1;
         float acc = 0.f;
 #pragma unroll
         for (int lx = 0; lx < E; ++lx) {
@@ -260,18 +279,19 @@ __device__ __forceinline__ void entropy_fixed_body(const float *__restrict__ hea
         }
     }
     __syncthreads();
+    const int ly0 = 4 * warp;
+    float Hc[2][4] = {};
 #pragma unroll
-    for (int q = 0; q < kTB / 8; ++q) {
-        const int ly = warp + 8 * q;
-        const int x = bx0 + lane, y = by0 + ly;
+    for (int c = 0; c < 2; ++c)
+        disk_sum4<R, PITCH>(sh + (c * E + R + ly0) * PITCH + R + lane, Hc[c],
+                            std::make_integer_sequence<int, 2 * R + 4>{});
+    const int x = bx0 + lane;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int y = by0 + ly0 + q;
         if (x >= ww || y >= wh) continue;
-        float Hc[2];
-#pragma unroll
-        for (int c = 0; c < 2; ++c)
-            Hc[c] = disk_sum<R, PITCH>(sh + (c * E + R + ly) * PITCH + R + lane,
-                                       std::make_integer_sequence<int, 2 * R + 1>{});
-        const float pr1 = __fdividef(1.0f, 1.0f + __expf(Hc[0] - Hc[1]));
-        const float pr0 = __fdividef(1.0f, 1.0f + __expf(Hc[1] - Hc[0]));
+        const float pr1 = __fdividef(1.0f, 1.0f + __expf(Hc[0][q] - Hc[1][q]));
+        const float pr0 = __fdividef(1.0f, 1.0f + __expf(Hc[1][q] - Hc[0][q]));
         const size_t o = (size_t)y * ww + x;
         if (!VSAOGM_IN_BOUNDS(o < (size_t)ww * wh)) continue;
         occ[o] = pr1;
@@ -290,7 +310,7 @@ __host__ inline int fixed_radius(unsigned mode, int r0, int r1)
 }
 
 template <int R>
-__global__ void __launch_bounds__(256) entropy_fixed_kernel(const float *__restrict__ heat, int W,
+__global__ void __launch_bounds__(kEntThreads) entropy_fixed_kernel(const float *__restrict__ heat, int W,
                                                             int H, int wx0, int wy0, int ww, int wh,
                                                             int raw,
                                                             const unsigned *__restrict__ maxima,
@@ -352,7 +372,7 @@ __global__ void __launch_bounds__(256) entropy_batch_kernel(const __grid_constan
 }
 
 template <int R>
-__global__ void __launch_bounds__(256) entropy_fixed_batch_kernel(const __grid_constant__ BatchOutTable tab)
+__global__ void __launch_bounds__(kEntThreads) entropy_fixed_batch_kernel(const __grid_constant__ BatchOutTable tab)
 {
     extern __shared__ float sh_dyn[];
     const int q = blockIdx.x;
@@ -385,7 +405,7 @@ int launch_entropy_batch(const BatchOutTable &tab, cudaStream_t st)
     const size_t smem = staged_floats(R) * sizeof(float);
     switch (fixed) {
 #define VSAOGM_FIXED_BATCH(RR) \
-    case RR: entropy_fixed_batch_kernel<RR><<<blocks, 256, smem, st>>>(tab); break;
+    case RR: entropy_fixed_batch_kernel<RR><<<blocks, kEntThreads, smem, st>>>(tab); break;
         VSAOGM_FIXED_BATCH(0) VSAOGM_FIXED_BATCH(1) VSAOGM_FIXED_BATCH(2) VSAOGM_FIXED_BATCH(3)
         VSAOGM_FIXED_BATCH(4) VSAOGM_FIXED_BATCH(5) VSAOGM_FIXED_BATCH(6) VSAOGM_FIXED_BATCH(7)
         VSAOGM_FIXED_BATCH(8)
@@ -413,7 +433,7 @@ int entropy(vsaogm_map *m, const float *heat, Region r, Region win, bool raw_inp
     switch (fixed) {
 #define VSAOGM_FIXED(RR)                                                                          \
     case RR:                                                                                      \
-        entropy_fixed_kernel<RR><<<grid, 256, smem, st>>>(heat, r.w(), r.h(), win.x0 - r.x0,      \
+        entropy_fixed_kernel<RR><<<grid, kEntThreads, smem, st>>>(heat, r.w(), r.h(), win.x0 - r.x0,      \
                                                           win.y0 - r.y0, win.w(), win.h(),        \
                                                           raw_input ? 1 : 0, m->maxima,           \
                                                           m->cfg.decode_mode, m->cfg.rho, occ,    \
