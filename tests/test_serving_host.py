@@ -1,0 +1,208 @@
+"""The serving loop's admission and ordering rules, on the CPU.
+
+``serving.Server.run`` is host logic: it admits requests to execution slots as
+they arrive and as slots free up, keeps each robot's requests in arrival order
+and never runs two requests of one robot at once (a map is used by one stream
+at a time).  Here the server's CUDA streams, events and maps are host fakes:
+a fake map applies an update or answers a query when it is launched and marks
+its robot busy until the slot's completion event, which completes after a
+random number of polls.  The rules are then checked on the record of launches
+and completions, with several robots and fewer slots than requests.
+"""
+import contextlib
+import time
+
+import numpy as np
+import pytest
+import torch
+
+from paper_2408_09066_gb300 import serving
+
+
+class World:
+    def __init__(self, seed):
+        self.rng = np.random.default_rng(seed)
+        self.busy = set()          # robots with work launched and not yet completed
+        self.launches = []         # (robot, kind, payload) in launch order
+        self.max_in_flight = 0
+        self.max_busy_robots = 0
+
+
+class FakeStream:
+    def __init__(self):
+        self.ops = []              # robots whose work was enqueued since the last event
+
+
+class FakeEvent:
+    def __init__(self, world):
+        self.world = world
+        self.t_rec = None
+        self.t_done = None
+        self.polls = 0
+        self.robots = []
+
+    def record(self, stream=None):
+        self.t_rec = time.perf_counter()
+        self.t_done = None
+        self.polls = int(self.world.rng.integers(0, 6))
+        self.robots = list(stream.ops) if stream is not None else []
+        if stream is not None:
+            stream.ops.clear()
+
+    def query(self):
+        if self.t_done is not None:
+            return True
+        if self.polls > 0:
+            self.polls -= 1
+            return False
+        self.t_done = time.perf_counter()
+        for r in self.robots:
+            self.world.busy.discard(r)
+        return True
+
+    def elapsed_time(self, other):
+        return (other.t_done - self.t_rec) * 1e3
+
+
+class FakeTorch:
+    class cuda:
+        @staticmethod
+        def stream(s):
+            return contextlib.nullcontext()
+
+        @staticmethod
+        def synchronize():
+            pass
+
+
+class FakeMap:
+    def __init__(self, world, robot, n_slots):
+        self.world, self.robot, self.n_slots = world, robot, n_slots
+        self.updates = 0
+
+    def _launch(self, stream, kind, payload):
+        w = self.world
+        assert self.robot not in w.busy, "two requests of one robot in flight"
+        w.busy.add(self.robot)
+        assert len(w.busy) <= self.n_slots
+        w.max_busy_robots = max(w.max_busy_robots, len(w.busy))
+        stream.ops.append(self.robot)
+        w.launches.append((self.robot, kind, payload))
+
+    def encode_bundle(self, xy, lab, stream=None):
+        self._launch(stream, "update", (len(lab), float(xy[:, 0].sum()), int(lab.sum())))
+        self.updates += 1
+
+    def query_window(self, x0, y0, w, h, heat, occ, stream=None):
+        self._launch(stream, "query", (x0, y0, w, h))
+        occ.fill_(float(self.updates))  # the answer: how many updates the map has seen
+
+
+class FakeSlot:
+    def __init__(self, world, max_points, max_cells):
+        self.stream = FakeStream()
+        self.xy = torch.empty((max_points, 2), dtype=torch.float32)
+        self.lab = torch.empty(max_points, dtype=torch.uint8)
+        self.heat = torch.empty(4 * max_cells, dtype=torch.float32)
+        self.occ = torch.empty(max_cells, dtype=torch.float32)
+        self.xy_h = torch.empty((max_points, 2), dtype=torch.float32)
+        self.lab_h = torch.empty(max_points, dtype=torch.uint8)
+        self.occ_h = torch.empty(max_cells, dtype=torch.float32)
+        self.done = FakeEvent(world)
+        self.req = None
+
+
+def make_server(world, n_robots, n_slots, max_points=64, max_window=8):
+    srv = serving.Server.__new__(serving.Server)
+    srv.torch = FakeTorch
+    srv.maps = [FakeMap(world, i, n_slots) for i in range(n_robots)]
+    srv.max_points, srv.max_window = max_points, max_window
+    srv.n_slots = n_slots
+    srv.slots = [FakeSlot(world, max_points, max_window * max_window) for _ in range(n_slots)]
+    srv.t0_event = FakeEvent(world)
+    return srv
+
+
+def make_requests(rng, n_robots, n, span):
+    reqs, t = [], 0.0
+    for _ in range(n):
+        t += rng.exponential(span / n)
+        rb = int(rng.integers(n_robots))
+        if rng.uniform() < 0.5:
+            w, h = (int(v) for v in rng.integers(1, 9, 2))
+            reqs.append(serving.Request("query", rb, t, window=(int(rng.integers(0, 4)), 0, w, h)))
+        else:
+            k = int(rng.integers(1, 65))
+            xy = rng.normal(size=(k, 2)).astype(np.float32)
+            lab = rng.integers(0, 2, k).astype(np.uint8)
+            reqs.append(serving.Request("update", rb, t, xy=xy, labels=lab))
+    return reqs
+
+
+@pytest.mark.parametrize("realtime", [False, True])
+@pytest.mark.parametrize("n_slots", [1, 3, 8])
+def test_admission_and_per_robot_order(realtime, n_slots):
+    world = World(seed=n_slots)
+    n_robots = 5
+    reqs = make_requests(np.random.default_rng(10 + n_slots), n_robots, 120, span=0.03)
+    srv = make_server(world, n_robots, n_slots)
+    done = srv.run(reqs, realtime=realtime)
+
+    # every request is served once
+    assert len(done) == len(reqs) and len({id(r) for r in done}) == len(reqs)
+    assert not world.busy
+    # each robot's requests were launched in arrival order, with their own data
+    for rb in range(n_robots):
+        mine = [r for r in reqs if r.robot == rb]
+        launched = [(k, p) for (r, k, p) in world.launches if r == rb]
+        want = []
+        for r in mine:
+            if r.kind == "update":
+                want.append(("update", (len(r.labels), float(r.xy[:, 0].sum()), int(r.labels.sum()))))
+            else:
+                want.append(("query", r.window))
+        assert len(launched) == len(want)
+        for (k, p), (wk, wp) in zip(launched, want):
+            assert k == wk
+            if k == "update":
+                assert p[0] == wp[0] and p[2] == wp[2] and abs(p[1] - wp[1]) < 1e-4
+            else:
+                assert p == wp
+        # a query answers with exactly the updates of its robot that arrived before it
+        seen = 0
+        for r in mine:
+            if r.kind == "update":
+                seen += 1
+            else:
+                x0, y0, w, h = r.window
+                assert r.result.shape == (h, w)
+                assert np.all(r.result == seen)
+    # timing fields are consistent; with realtime, nothing starts before it arrives
+    for r in done:
+        assert r.done >= r.start - 1e-3
+        if realtime:
+            assert r.start >= r.arrival
+    # with more than one slot, requests of different robots overlap
+    if n_slots > 1:
+        assert world.max_busy_robots > 1
+
+
+def test_update_larger_than_the_slot_buffers_is_refused():
+    world = World(seed=0)
+    srv = make_server(world, 1, 2, max_points=16)
+    big = serving.Request("update", 0, 0.0, xy=np.zeros((17, 2), np.float32),
+                          labels=np.zeros(17, np.uint8))
+    with pytest.raises(ValueError):
+        srv.run([big], realtime=False)
+
+
+def test_summary_percentiles_and_rate():
+    rs = []
+    for i, lat in enumerate([1.0, 2.0, 3.0, 4.0]):
+        r = serving.Request("update" if i % 2 == 0 else "query", 0, 0.0)
+        r.done = lat / 1e3
+        rs.append(r)
+    s = serving.summarize(rs, duration=1.0)
+    assert s["update"]["count"] == 2 and s["query"]["count"] == 2
+    assert s["update"]["p50_ms"] == pytest.approx(2.0) and s["query"]["max_ms"] == pytest.approx(4.0)
+    assert s["requests_per_s"] == pytest.approx(4.0)
