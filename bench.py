@@ -262,7 +262,8 @@ def run_reference(args):
     if int(os.environ.get("RANK", "0")) != 0:
         return 0
     oracle.build()
-    wl = make_workload(getattr(args, "workload", "paper"))
+    name = getattr(args, "workload", "paper")
+    wl = make_workload(name)
     rng = np.random.default_rng(11)
     n_pts, n_cells = calibrate_oracle(wl, 2.0, rng)
     for _ in range(args.warmup):
@@ -274,7 +275,7 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": value, "unit": "points/s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": mean_s * 1e3, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": DATA,
+        "vs_baseline": None, "dtype": "f64", "data": data_of(name, wl),
         "config": workload_config(wl, "fp64 oracle"),
         "cells_per_s": wl.W * wl.H / mean_s,
         "p50_ms": percentile(steps, 50) * 1e3, "p99_ms": percentile(steps, 99) * 1e3,
@@ -300,6 +301,14 @@ DATA = ("synthetic: seeded 100-scan lidar trajectory in a walled 40 m world with
 # (dram__bytes_read.sum + dram__bytes_write.sum = 24.58 MB + 114.52 MB), valid
 # only for the kernel source it was taken on (sha1 of csrc/encode.cu).
 ENCODE_TRAFFIC = {"sha1": "872e55d45d44b2547ffe11644075195633022ab1", "bytes": 139104256}
+
+
+def data_of(name: str, wl) -> str:
+    """The line's `data` field: which synthetic workload it ran and what it stands for."""
+    if name == "paper":
+        return DATA
+    return (f"synthetic: seeded lidar workload shaped like the paper's {name} dataset "
+            f"({wl.name}, {wl.n} points)")
 
 
 def workload_config(wl, decode: str) -> dict:
@@ -530,9 +539,7 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": "points/s", "n_gpus": d.world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-        "data": DATA if args.workload == "paper" else
-        (f"synthetic: seeded lidar workload shaped like the paper's {args.workload} dataset "
-         f"({wl.name}, {wl.n} points)"),
+        "data": data_of(args.workload, wl),
         "config": workload_config(wl, args.decode),
         "fp32_plain": plain,
         "cells_per_s": d.sum(float(cells * args.steps)) / total_s,
