@@ -5,6 +5,7 @@ saturates.  Prints one JSON line per rate with p50/p99 latency per request kind
 and the achieved throughput.
 
     python -m paper_2408_09066_gb300.serve_bench [--robots 32] [--duration 2]
+        [--deadline-ms T]   # drop requests not started T ms after arrival
 """
 from __future__ import annotations
 
@@ -23,6 +24,8 @@ def main():
     p.add_argument("--rates", type=str, default="250,500,1000,2000,4000,8000")
     p.add_argument("--query-frac", type=float, default=0.5)
     p.add_argument("--decode", choices=["bf16x3", "fp16x3", "fp32"], default="bf16x3")
+    p.add_argument("--deadline-ms", type=float, default=None,
+                   help="start deadline per request; later requests are dropped as expired")
     a = p.parse_args()
     prec = {"fp32": V.DECODE_FP32, "bf16x3": V.DECODE_BF16X3, "fp16x3": V.DECODE_FP16X3}[a.decode]
     fleet = synth.robot_fleet(a.robots)
@@ -35,11 +38,13 @@ def main():
         srv.run(serving.poisson_requests(fleet, 2000.0, 0.5, a.query_frac, seed=99),
                 realtime=False)
         for i, rate in enumerate(float(x) for x in a.rates.split(",")):
-            reqs = serving.poisson_requests(fleet, rate, a.duration, a.query_frac, seed=i)
+            deadline = None if a.deadline_ms is None else a.deadline_ms / 1e3
+            reqs = serving.poisson_requests(fleet, rate, a.duration, a.query_frac, seed=i,
+                                            deadline=deadline)
             done = srv.run(reqs, realtime=True)
             s = serving.summarize(done, a.duration)
             s.update({"offered_per_s": rate, "robots": a.robots, "slots": srv.n_slots,
-                      "decode": a.decode, "D": 8192,
+                      "decode": a.decode, "D": 8192, "deadline_ms": a.deadline_ms,
                       "saturated": s["requests_per_s"] < 0.9 * rate})
             print(json.dumps(s), flush=True)
     finally:

@@ -14,7 +14,10 @@ admits after the resident maps.  A request is started as soon as a slot is free
 and no earlier request of the same robot is still running (requests of one
 robot keep their arrival order; a map is used by one stream at a time).
 Requests of different robots run concurrently on different streams, so work
-that arrives while the GPU is busy joins it as slots free up.  Latency is
+that arrives while the GPU is busy joins it as slots free up.  A request may
+carry a deadline: if it has not started that many seconds after its arrival
+it is dropped (status "expired") and never launched, which bounds the queue
+under overload; the robot's later requests keep their order.  Latency is
 measured from arrival to the completion event of the request's last GPU
 operation (for queries, the copy of the occupancy window to pinned host
 memory).
@@ -38,7 +41,9 @@ class Request:
     xy: np.ndarray | None = None       # update: float32 [n][2]
     labels: np.ndarray | None = None   # update: uint8 [n]
     window: tuple | None = None        # query: (x0, y0, w, h)
+    deadline: float | None = None      # seconds after arrival by which it must start
     # filled in by the server
+    status: str = "pending"            # "done", or "expired" if it could not start in time
     start: float = float("nan")
     done: float = float("nan")
     result: np.ndarray | None = None   # query: Pr(psi = 1) of the window, float32 [h][w]
@@ -121,6 +126,7 @@ class Server:
     def _retire(self, slot: _Slot):
         r = slot.req
         r.done = self.t0_event.elapsed_time(slot.done) / 1e3
+        r.status = "done"
         if r.kind == "query":
             x0, y0, w, h = r.window
             r.result = slot.occ_h[:w * h].numpy().reshape(h, w).copy()
@@ -147,6 +153,16 @@ class Server:
                 if s.req is not None and s.done.query():
                     busy.discard(s.req.robot)
                     finished.append(self._retire(s))
+            if any(r.deadline is not None for r in waiting):
+                keep = []
+                for r in waiting:
+                    arrived = r.arrival if realtime else 0.0
+                    if r.deadline is not None and now > arrived + r.deadline:
+                        r.status = "expired"
+                        finished.append(r)
+                    else:
+                        keep.append(r)
+                waiting = keep
             for s in self.slots:
                 if s.req is not None:
                     continue
@@ -176,9 +192,11 @@ def fleet_configs(fleet, D: int = 8192, decode_prec: int = V.DECODE_BF16X3, seed
 
 
 def poisson_requests(fleet, rate: float, duration: float, query_frac: float = 0.5,
-                     seed: int = 0, win_lo: int = 128, win_hi: int = 512) -> list[Request]:
+                     seed: int = 0, win_lo: int = 128, win_hi: int = 512,
+                     deadline: float | None = None) -> list[Request]:
     """Poisson arrivals at `rate` requests/s for `duration` s over the fleet:
-    scan updates (the robot's next scan) and window queries (128^2 to 512^2)."""
+    scan updates (the robot's next scan) and window queries (128^2 to 512^2),
+    each with the start deadline `deadline` (seconds, None for none)."""
     from . import synth
     rng = np.random.default_rng(seed)
     t, reqs = 0.0, []
@@ -190,21 +208,27 @@ def poisson_requests(fleet, rate: float, duration: float, query_frac: float = 0.
         rb = int(rng.integers(len(fleet)))
         if rng.uniform() < query_frac:
             win = synth.window_sizes(rng, fleet[rb].cells, win_lo, win_hi)
-            reqs.append(Request("query", rb, t, window=win))
+            reqs.append(Request("query", rb, t, window=win, deadline=deadline))
         else:
             xy, lab = fleet[rb].scans[next_scan[rb] % len(fleet[rb].scans)]
             next_scan[rb] += 1
-            reqs.append(Request("update", rb, t, xy=xy, labels=lab))
+            reqs.append(Request("update", rb, t, xy=xy, labels=lab, deadline=deadline))
     return reqs
 
 
 def summarize(reqs: list[Request], duration: float) -> dict:
+    """Latency percentiles per request kind over the completed requests, the
+    count of expired ones, and completed requests per second."""
     out = {}
+    done = [r for r in reqs if r.status != "expired"]
     for kind in ("update", "query"):
-        lat = np.array([r.latency for r in reqs if r.kind == kind]) * 1e3
+        lat = np.array([r.latency for r in done if r.kind == kind]) * 1e3
         if len(lat):
             out[kind] = {"count": int(len(lat)), "p50_ms": float(np.percentile(lat, 50)),
                          "p99_ms": float(np.percentile(lat, 99)), "max_ms": float(lat.max())}
-    end = max((r.done for r in reqs), default=0.0)
-    out["requests_per_s"] = len(reqs) / max(end, duration, 1e-9)
+        n_exp = sum(1 for r in reqs if r.kind == kind and r.status == "expired")
+        if n_exp:
+            out.setdefault(kind, {"count": 0})["expired"] = n_exp
+    end = max((r.done for r in done), default=0.0)
+    out["requests_per_s"] = len(done) / max(end, duration, 1e-9)
     return out

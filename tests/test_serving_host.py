@@ -26,6 +26,7 @@ class World:
         self.launches = []         # (robot, kind, payload) in launch order
         self.max_in_flight = 0
         self.max_busy_robots = 0
+        self.work_s = 0.0          # least wall time a slot's work takes
 
 
 class FakeStream:
@@ -52,8 +53,8 @@ class FakeEvent:
     def query(self):
         if self.t_done is not None:
             return True
-        if self.polls > 0:
-            self.polls -= 1
+        if self.polls > 0 or time.perf_counter() - self.t_rec < self.world.work_s:
+            self.polls = max(0, self.polls - 1)
             return False
         self.t_done = time.perf_counter()
         for r in self.robots:
@@ -185,6 +186,72 @@ def test_admission_and_per_robot_order(realtime, n_slots):
     # with more than one slot, requests of different robots overlap
     if n_slots > 1:
         assert world.max_busy_robots > 1
+
+
+def _check_order(world, reqs, n_robots):
+    """Every request ends once, done or expired; an expired one never launched;
+    each robot's launched requests ran in arrival order and each query saw
+    exactly the robot's earlier updates that ran."""
+    for r in reqs:
+        assert r.status in ("done", "expired")
+    for rb in range(n_robots):
+        ran = [r for r in reqs if r.robot == rb and r.status == "done"]
+        launched = [(k, p) for (q, k, p) in world.launches if q == rb]
+        assert [k for k, _ in launched] == [r.kind for r in ran]
+        seen = 0
+        for r, (k, p) in zip(ran, launched):
+            if k == "update":
+                assert p[0] == len(r.labels)
+                seen += 1
+            else:
+                assert p == r.window and np.all(r.result == seen)
+
+
+def test_deadline_zero_expires_before_launch_and_none_waits():
+    world = World(seed=4)
+    reqs = make_requests(np.random.default_rng(4), 3, 60, span=0.01)
+    for i, r in enumerate(reqs):
+        r.deadline = 0.0 if i % 2 else None
+    srv = make_server(world, 3, 2)
+    done = srv.run(reqs, realtime=False)
+    assert len(done) == len(reqs)
+    assert all(r.status == ("expired" if i % 2 else "done") for i, r in enumerate(reqs))
+    assert all(np.isnan(r.start) for r in reqs if r.status == "expired")
+    _check_order(world, reqs, 3)
+    s = serving.summarize(done, duration=1e-3)
+    n_exp = sum(v.get("expired", 0) for k, v in s.items() if k in ("update", "query"))
+    assert n_exp == len(reqs) // 2
+    assert sum(v["count"] for k, v in s.items() if k in ("update", "query")) == len(reqs) - n_exp
+
+
+def test_generous_deadlines_expire_nothing():
+    world = World(seed=5)
+    reqs = make_requests(np.random.default_rng(5), 4, 80, span=0.02)
+    for r in reqs:
+        r.deadline = 1e3
+    srv = make_server(world, 4, 3)
+    srv.run(reqs, realtime=True)
+    assert all(r.status == "done" for r in reqs)
+    _check_order(world, reqs, 4)
+
+
+def test_overload_drops_late_requests_and_keeps_order():
+    """One slot whose work takes 2 ms, requests arriving every 0.2 ms with a 3 ms
+    start deadline: most expire, the rest run in order with the right data."""
+    world = World(seed=6)
+    world.work_s = 2e-3
+    rng = np.random.default_rng(6)
+    reqs = make_requests(rng, 3, 40, span=0.008)
+    for r in reqs:
+        r.deadline = 3e-3
+    srv = make_server(world, 3, 1)
+    srv.run(reqs, realtime=True)
+    n_done = sum(r.status == "done" for r in reqs)
+    assert 0 < n_done < len(reqs)
+    for r in reqs:
+        if r.status == "done":
+            assert r.start <= r.arrival + r.deadline + 1e-3
+    _check_order(world, reqs, 3)
 
 
 def test_update_larger_than_the_slot_buffers_is_refused():
