@@ -86,6 +86,33 @@ def test_tile_assignment_exact_including_ties_and_outside():
     assert oracle.tile_of(g, 0.0, 0.3) % g.tiles_x == 1
 
 
+def test_cell_assignment_exact_including_centres_on_boundaries():
+    """Algorithm 1's rule at cell centres x_min + (i + 1/2) res, decided against an
+    exact rational argmin: with 50 cells over 4 tiles a tile is 12.5 cells wide, so
+    the centres of cells 12 and 37 lie exactly on a boundary and go to the lower
+    tile; the decode's cell-to-tile map (shared by the memory and direct forms)
+    is pinned here rather than through them."""
+    g = Grid(W=50, H=30, res=0.1, x_min=-2.5, y_min=-1.5, tiles_x=4, tiles_y=3)
+    cells = np.array([(i, j) for j in range(g.H) for i in range(g.W)], np.int32)
+    got = oracle.assign_cells(g, cells)
+    tw = Fraction(g.W) * Fraction(g.res) / g.tiles_x
+    th = Fraction(g.H) * Fraction(g.res) / g.tiles_y
+    for (i, j), b in zip(cells, got):
+        x = Fraction(g.x_min) + (int(i) + Fraction(1, 2)) * Fraction(g.res)
+        y = Fraction(g.y_min) + (int(j) + Fraction(1, 2)) * Fraction(g.res)
+        best, bd = None, None
+        for by in range(g.tiles_y):
+            for bx in range(g.tiles_x):
+                cx = Fraction(g.x_min) + (bx + Fraction(1, 2)) * tw
+                cy = Fraction(g.y_min) + (by + Fraction(1, 2)) * th
+                d = (x - cx) ** 2 + (y - cy) ** 2
+                if bd is None or d < bd:
+                    best, bd = by * g.tiles_x + bx, d
+        assert b == best, (i, j, b, best)
+    row = got[:g.W]
+    assert row[12] == 0 and row[13] == 1 and row[37] == 2 and row[38] == 3
+
+
 # ---------------------------------------------------------- encode / bundle
 def test_self_similarity_is_D_and_index_is_2beta_plus_psi():
     """|phi_k| = 1, so <phi(p), phi(p)> = D; the point lands in memory 2*beta + psi."""
