@@ -113,3 +113,14 @@ def test_bounds_checked_build_compiles_and_exports_the_same_symbols():
     L2 = ctypes.CDLL(lib)
     missing = [n for n in _declared_functions() if not hasattr(L2, n)]
     assert not missing, missing
+
+
+def test_alu_rate_microbenchmark_compiles_for_sm103a(tmp_path):
+    """The microbenchmark behind the encode's ALU roofline builds for sm_103a."""
+    import subprocess
+    src = os.path.join(ROOT, "paper_2408_09066_gb300", "microbench", "alu_rates.cu")
+    out = tmp_path / "alu_rates.o"
+    r = subprocess.run([build_mod.nvcc(), "-gencode", "arch=compute_103a,code=sm_103a", "-O3",
+                        "-c", src, "-o", str(out)], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    assert out.stat().st_size > 0
