@@ -115,11 +115,13 @@ def test_bounds_checked_build_compiles_and_exports_the_same_symbols():
     assert not missing, missing
 
 
-def test_alu_rate_microbenchmark_compiles_for_sm103a(tmp_path):
-    """The microbenchmark behind the encode's ALU roofline builds for sm_103a."""
+@pytest.mark.parametrize("name", ["alu_rates", "mufu_range"])
+def test_microbenchmarks_compile_for_sm103a(tmp_path, name):
+    """The microbenchmarks behind the encode's ALU roofline and phase tiers build
+    for sm_103a."""
     import subprocess
-    src = os.path.join(ROOT, "paper_2408_09066_gb300", "microbench", "alu_rates.cu")
-    out = tmp_path / "alu_rates.o"
+    src = os.path.join(ROOT, "paper_2408_09066_gb300", "microbench", name + ".cu")
+    out = tmp_path / (name + ".o")
     r = subprocess.run([build_mod.nvcc(), "-gencode", "arch=compute_103a,code=sm_103a", "-O3",
                         "-c", src, "-o", str(out)], capture_output=True, text=True)
     assert r.returncode == 0, r.stderr
