@@ -115,7 +115,7 @@ def test_bounds_checked_build_compiles_and_exports_the_same_symbols():
     assert not missing, missing
 
 
-@pytest.mark.parametrize("name", ["alu_rates", "mufu_range"])
+@pytest.mark.parametrize("name", ["alu_rates", "mufu_range", "f32x2_rates"])
 def test_microbenchmarks_compile_for_sm103a(tmp_path, name):
     """The microbenchmarks behind the encode's ALU roofline and phase tiers build
     for sm_103a."""
