@@ -99,7 +99,9 @@ typedef struct {
 typedef struct vsaogm_map vsaogm_map;
 
 /* Fills *cfg with defaults: D 8192, 400 x 400 cells of 0.1 m from (-20, -20),
- * 4 x 4 tiles, l = 0.1 m, r_occ = r_emp = 3, rho = 0, seed 0, FP32 decode. */
+ * 4 x 4 tiles, l = 0.1 m, r_occ = r_emp = 3, rho = 0, seed 0, FP32 decode.
+ * The radii follow the ToySim and EviLOG rows of the paper's parameter table;
+ * the rest is a service of the library (no counterpart in the paper). */
 void vsaogm_config_default(vsaogm_config *cfg);
 
 /* Creates a map (Sec. III-B2, III-B3): validates *cfg, draws the axis
@@ -111,10 +113,13 @@ void vsaogm_config_default(vsaogm_config *cfg);
 int vsaogm_create(const vsaogm_config *cfg, vsaogm_map **out);
 
 /* Frees the map and everything it owns.  Synchronises the device first.
- * NULL is accepted.                                                         */
+ * NULL is accepted.
+ * No counterpart in the paper: a service of the library. */
 int vsaogm_destroy(vsaogm_map *map);
 
-/* Sets every memory to zero (asynchronous on `stream`). */
+/* Sets every memory to zero (asynchronous on `stream`).
+ * The empty memories a map starts from before Algorithm 1 bundles into it.
+ * Errors: E_INVAL (NULL map), E_CUDA. */
 int vsaogm_reset(vsaogm_map *map, void *stream);
 
 /* Encoding and bundling (Eq. fb-with-ls-2d, Eq. bundling, Algorithm 1):
@@ -176,7 +181,10 @@ int vsaogm_entropy(vsaogm_map *map, const float *heat_dev, float *occ_dev, float
 /* Decode and entropy in one call, with the non-linearity fused into the
  * entropy pass.  heat_dev (float [2][H][W]) is caller-provided scratch that
  * receives the normalised similarity P (before the non-linearity).  Outputs
- * as vsaogm_entropy.  Errors: E_INVAL, E_CUDA.                               */
+ * as vsaogm_entropy.  Errors: E_INVAL, E_CUDA.
+ * Eqs. vector-normalization, loc-query and non-linearities, then Algorithm 2
+ * and Eqs. softmax, psd, classification, as vsaogm_decode followed by
+ * vsaogm_entropy. */
 int vsaogm_query(vsaogm_map *map, float *heat_dev, float *occ_dev, float *ogm_dev,
                  uint8_t *cls_dev, void *stream);
 
@@ -194,14 +202,18 @@ int vsaogm_query_window(vsaogm_map *map, int32_t x0, int32_t y0, int32_t w, int3
                         float *heat_dev, float *occ_dev, float *ogm_dev, uint8_t *cls_dev,
                         void *stream);
 
-/* Floats of heat scratch vsaogm_query_window needs for that window. */
+/* Floats of heat scratch vsaogm_query_window needs for that window.
+ * No counterpart in the paper: a service of the library.
+ * Errors: E_INVAL (NULL, window not inside the map). */
 int vsaogm_window_scratch(const vsaogm_map *map, int32_t x0, int32_t y0, int32_t w, int32_t h,
                           int64_t *floats);
 
 /* End-to-end call on host buffers: copies xy_host/labels_host to the device,
  * bundles them, runs vsaogm_query and copies Pr(psi = 1) back into occ_host
  * (float [H][W]); returns after the stream has finished.  Device staging is
- * owned by the map and grows on demand.  Errors: as the calls it makes.     */
+ * owned by the map and grows on demand.  Errors: as the calls it makes.
+ * The whole method (Algorithm 1, then the decoding and Algorithm 2) on host
+ * buffers. */
 int vsaogm_update_query_host(vsaogm_map *map, const float *xy_host, const uint8_t *labels_host,
                              int64_t n, float *occ_host, void *stream);
 
@@ -209,22 +221,33 @@ int vsaogm_update_query_host(vsaogm_map *map, const float *xy_host, const uint8_
  * vsaogm_encode_bundle with up to max_points points per call, and every
  * vsaogm_decode / vsaogm_query / vsaogm_query_window.  For servers that must
  * not allocate (cudaMalloc synchronises the device) once they serve requests.
- * Synchronous.  Errors: E_INVAL, E_NOMEM, E_CUDA.                            */
+ * Synchronous.  Errors: E_INVAL, E_NOMEM, E_CUDA.
+ * No counterpart in the paper: a service of the library. */
 int vsaogm_reserve(vsaogm_map *map, int64_t max_points);
 
 /* Number of points rejected by vsaogm_encode_bundle since the last reset
- * (synchronises `stream`).                                                  */
+ * (synchronises `stream`).
+ * No counterpart in the paper: a service of the library.
+ * Errors: E_INVAL (NULL), E_CUDA. */
 int vsaogm_rejected(vsaogm_map *map, int64_t *count, void *stream);
 
 /* Synchronises `stream` and reports device-side failures recorded since the
  * last call: E_TIMEOUT if a kernel gave up on a bounded wait (its outputs are
- * then invalid), else VSAOGM_OK.  Clears the record.                        */
+ * then invalid), else VSAOGM_OK.  Clears the record.
+ * No counterpart in the paper: a service of the library. */
 int vsaogm_status(vsaogm_map *map, void *stream);
 
-/* Copies the memories (complex64 [2T][D], tile-centred frame) to omega_dev. */
+/* Copies the memories (complex64 [2T][D], tile-centred frame) to omega_dev.
+ * Checkpoint: the memories with the configuration and seed are the map's whole
+ * state (the model whose size the paper reports); the call itself has no
+ * counterpart in the paper.
+ * Errors: E_INVAL (NULL), E_CUDA. */
 int vsaogm_get_memory(const vsaogm_map *map, float *omega_dev, void *stream);
 
-/* Replaces the memories with omega_dev (complex64 [2T][D]). */
+/* Replaces the memories with omega_dev (complex64 [2T][D]).
+ * Resume from a checkpoint (see vsaogm_get_memory); no counterpart in the
+ * paper as a call.
+ * Errors: E_INVAL (NULL), E_CUDA. */
 int vsaogm_set_memory(vsaogm_map *map, const float *omega_dev, void *stream);
 
 /* Multi-map fusion (Algorithm 3): adds src's memories into dst's.  Both maps
@@ -232,14 +255,18 @@ int vsaogm_set_memory(vsaogm_map *map, const float *omega_dev, void *stream);
  * grid; otherwise E_INVAL.  Maps must be on the same device.              */
 int vsaogm_fuse(vsaogm_map *dst, const vsaogm_map *src, void *stream);
 
-/* Copies the axis frequencies (cycles per metre) into host arrays of D floats. */
+/* Copies the axis frequencies (cycles per metre) into host arrays of D floats.
+ * The axis vectors of Sec. III-B2, as frequencies.
+ * Errors: E_INVAL (NULL). */
 int vsaogm_get_axis_frequencies(const vsaogm_map *map, float *nu_x_host, float *nu_y_host);
 
-/* Geometry of the map: number of tiles and memories. */
+/* Geometry of the map: number of tiles and memories.
+ * delta_x * delta_y tiles and two memories per tile (Sec. III-B3).
+ * Errors: E_INVAL (NULL map). */
 int vsaogm_get_shape(const vsaogm_map *map, int32_t *n_tiles, int32_t *n_memories);
 
 /* Stage timing (tracing).  Stages of the calls above, in order: */
-#define VSAOGM_STAGE_SORT 0      /* tile assignment + counting sort (4 kernels)  */
+#define VSAOGM_STAGE_SORT 0      /* tile assignment + counting sort (1-4 kernels)*/
 #define VSAOGM_STAGE_ENCODE 1    /* FHRR encode + bundle of the chunks           */
 #define VSAOGM_STAGE_REDUCE 2    /* fixed-order sum of partial memories          */
 #define VSAOGM_STAGE_NORMS 3     /* memory norms (Eq. vector-normalization)      */
@@ -251,13 +278,15 @@ int vsaogm_get_shape(const vsaogm_map *map, int32_t *n_tiles, int32_t *n_memorie
 /* Turns stage timing on or off for `map`.  When on, each stage is bracketed
  * by two CUDA events recorded on the call's stream (a few microseconds of
  * overhead per stage).  Kernel launches are counted whether timing is on or
- * not.  Errors: E_INVAL, E_CUDA.                                            */
+ * not.  Errors: E_INVAL, E_CUDA.
+ * No counterpart in the paper: a service of the library. */
 int vsaogm_set_timing(vsaogm_map *map, int enable);
 
 /* Accumulated device milliseconds (ms[VSAOGM_N_STAGES], nullable) and kernel
  * launch counts (launches[VSAOGM_N_STAGES], nullable) per stage since the last
  * reset; resets the counters when `reset` is non-zero.  Synchronises with
- * every stream the timed calls used.  Errors: E_INVAL, E_CUDA.               */
+ * every stream the timed calls used.  Errors: E_INVAL, E_CUDA.
+ * No counterpart in the paper: a service of the library. */
 int vsaogm_stage_times(vsaogm_map *map, double *ms, int64_t *launches, int reset);
 
 /* Batches: many maps in one step.  The paper runs one map per call; a batch
@@ -288,10 +317,12 @@ typedef struct vsaogm_batch vsaogm_batch;
 
 /* Creates a batch over maps[0..count-1] (1 <= count <= VSAOGM_MAX_BATCH,
  * distinct maps).  Allocates a few small device buffers; per-map scratch
- * grows on the first step.                                                 */
+ * grows on the first step.
+ * No counterpart in the paper: a service of the library. */
 int vsaogm_batch_create(vsaogm_map *const *maps, int32_t count, vsaogm_batch **out);
 
-/* Frees the batch (synchronises the device); the maps stay.  NULL is a no-op. */
+/* Frees the batch (synchronises the device); the maps stay.  NULL is a no-op.
+ * No counterpart in the paper: a service of the library. */
 int vsaogm_batch_destroy(vsaogm_batch *batch);
 
 /* One step on `stream`: optional reset, encode + bundle of every map's
@@ -299,7 +330,9 @@ int vsaogm_batch_destroy(vsaogm_batch *batch);
  * whenever a step needs more (cudaMalloc synchronises the device); a step
  * that grows it also drops a captured step, whose graph held the old
  * buffers (vsaogm_batch_replay then fails with E_INVAL until the next
- * capture).                                                                */
+ * capture).
+ * Per map, the same computation as the single-map calls (Algorithm 1 to
+ * Algorithm 2); the batching itself has no counterpart in the paper. */
 int vsaogm_batch_step(vsaogm_batch *batch, const float *const *xy_dev,
                       const uint8_t *const *labels_dev, const int64_t *n,
                       float *const *heat_dev, float *const *occ_dev, float *const *ogm_dev,
@@ -311,13 +344,15 @@ int vsaogm_batch_step(vsaogm_batch *batch, const float *const *xy_dev,
  * (the caller refills them in place with exactly n[i] points each; the point
  * counts and chunk sizes are part of the graph) and writes the same outputs.
  * `stream` must not be the default stream.  Stage
- * timing must be off on every map.  Replaces a previous capture.            */
+ * timing must be off on every map.  Replaces a previous capture.
+ * No counterpart in the paper: a service of the library. */
 int vsaogm_batch_capture(vsaogm_batch *batch, const float *const *xy_dev,
                          const uint8_t *const *labels_dev, const int64_t *n,
                          float *const *heat_dev, float *const *occ_dev,
                          float *const *ogm_dev, int32_t reset, void *stream);
 
-/* Launches the captured step on `stream`.  E_INVAL if nothing is captured. */
+/* Launches the captured step on `stream`.  E_INVAL if nothing is captured.
+ * No counterpart in the paper: a service of the library. */
 int vsaogm_batch_replay(vsaogm_batch *batch, void *stream);
 
 /* Times candidate shapes of the batched step on these inputs (each a few
@@ -327,7 +362,8 @@ int vsaogm_batch_replay(vsaogm_batch *batch, void *stream);
  * sets the chunk size), the decode work items per SM and how many points a
  * map must hold per bundling patch before the finer patches pay.  Synchronous.
  * Drops a captured step (capture again after tuning).  Outputs (nullable):
- * the chosen values.                                                        */
+ * the chosen values.
+ * No counterpart in the paper: a service of the library. */
 int vsaogm_batch_autotune(vsaogm_batch *batch, const float *const *xy_dev,
                           const uint8_t *const *labels_dev, const int64_t *n,
                           float *const *heat_dev, float *const *occ_dev, void *stream,
@@ -337,16 +373,19 @@ int vsaogm_batch_autotune(vsaogm_batch *batch, const float *const *xy_dev,
  * events between its stages on the step's stream.  Stages as VSAOGM_STAGE_*:
  * SORT (with the reset), ENCODE, REDUCE, NORMS, DECODE (with the slice sums
  * and maxima) and ENTROPY (with the fused non-linearity; NONLINEAR stays 0).
- * Replays are not timed per stage; their kernels are counted.               */
+ * Replays are not timed per stage; their kernels are counted.
+ * No counterpart in the paper: a service of the library. */
 int vsaogm_batch_set_timing(vsaogm_batch *batch, int32_t enable);
 
 /* Accumulated milliseconds and kernel launches per stage (both nullable,
  * VSAOGM_N_STAGES entries) since the last reset; resets them when `reset` is
- * non-zero.  Synchronises with the timed steps.  Errors: E_INVAL, E_CUDA.   */
+ * non-zero.  Synchronises with the timed steps.  Errors: E_INVAL, E_CUDA.
+ * No counterpart in the paper: a service of the library. */
 int vsaogm_batch_stage_times(vsaogm_batch *batch, double *ms, int64_t *launches,
                              int32_t reset);
 
-/* Description of the last error on the calling thread ("" if none). */
+/* Description of the last error on the calling thread ("" if none).
+ * No counterpart in the paper: a service of the library. */
 const char *vsaogm_last_error(void);
 
 #ifdef __cplusplus

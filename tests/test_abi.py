@@ -32,6 +32,21 @@ def test_header_declares_the_hot_path_entry_points():
         assert must in names
 
 
+def test_every_declaration_cites_its_passage():
+    """Each entry point's comment cites the passage that defines it (an equation,
+    section or algorithm of the paper) or says that the paper has no counterpart."""
+    src = open(HEADER).read()
+    pat = re.compile(r"/\*((?:(?!\*/).)*)\*/\s*\n(?:int|void|const char)\s*\*?\s*(vsaogm_\w+)\s*\(",
+                     re.S)
+    seen = {}
+    for m in pat.finditer(src):
+        seen[m.group(2)] = m.group(1)
+    assert set(seen) == set(_declared_functions())
+    for name, comment in seen.items():
+        text = re.sub(r"\s*\n\s*\*\s*", " ", comment)   # join the comment's lines
+        assert re.search(r"Eqs?\.|Sec\.|Algorithm|no counterpart", text, re.I), name
+
+
 def test_library_exports_every_declared_symbol(L):
     missing = [n for n in _declared_functions() if not hasattr(L, n)]
     assert not missing, missing
