@@ -193,20 +193,20 @@ def _walk_workload(name, seed, half, n_rect, n_disc, rect_size, disc_r, n_scans,
                     tiles[1], D, length_scale, seed, w)
 
 
-def toysim_like(seed: int = 2001, D: int = 16000) -> Workload:
+def toysim_like(seed: int = 2001, D: int = 16000, n_scans: int = 90) -> Workload:
     """Shaped like the ToySim row of the paper's dataset table: a 100 m x 100 m
     world, 90 scans of 50 beams, about as many occupied as empty points; with
     the ToySim parameters d = 32000 (D = 16000), l = 1, delta = 2; 0.25 m cells."""
     return _walk_workload("toysim_like_400x400_2x2tiles", seed, 50.0, 30, 15, (2.0, 10.0),
-                          (1.0, 4.0), 90, 50, 40.0, 1, 400, 0.25, (2, 2), D, 1.0, step=1.0)
+                          (1.0, 4.0), n_scans, 50, 40.0, 1, 400, 0.25, (2, 2), D, 1.0, step=1.0)
 
 
-def intel_like(seed: int = 2002, D: int = 16000) -> Workload:
+def intel_like(seed: int = 2002, D: int = 16000, n_scans: int = 910) -> Workload:
     """Shaped like the Intel Map row: a 38 m x 38 m building-sized world, 910 scans
     of 421 beams, a little more occupied than empty; d = 32000, l = 0.2,
     delta = 8, 0.1 m cells."""
     return _walk_workload("intel_like_380x380_8x8tiles", seed, 19.0, 40, 10, (0.5, 4.0),
-                          (0.3, 1.0), 910, 421, 20.0, 1, 380, 0.1, (8, 8), D, 0.2, step=0.25)
+                          (0.3, 1.0), n_scans, 421, 20.0, 1, 380, 0.1, (8, 8), D, 0.2, step=0.25)
 
 
 def evilog_like(seed: int = 2003, D: int = 16000) -> Workload:
