@@ -147,16 +147,26 @@ int vsaogm_encode_bundle(vsaogm_map *map, const float *xy_dev, const uint8_t *la
  * owned by another allocator.  Map creation still allocates; do that at
  * set-up time.
  * Scratch lives in one static 4 MiB device array inside the library, which
- * every GPU that loads the library keeps until the process exits.  The first
- * call on each device looks up that array's device address
- * (cudaGetSymbolAddress) with the device current, so make the first call
- * before any stream capture.  All calls share the array: calls whose work
- * overlaps on the GPU (different streams, or different maps at the same
- * time) race and give wrong results; order them on one stream.  Bundling adds
- * into the memories with atomics, so the result is not bitwise reproducible.
- * Limits: n <= 262144 points per call (E_INVAL above, before any GPU work);
- * the map's device must be current.  No stage timing is recorded.
- * Errors: E_INVAL, E_CUDA.                                                  */
+ * every GPU that loads the library keeps until the process exits.  Its
+ * device address is looked up (cudaGetSymbolAddress) once per device by
+ * vsaogm_create, with that device current, so the call itself does no
+ * lookup and loads no module.  All calls share the array and each call
+ * writes every scratch word it reads, so nothing carries over between calls;
+ * calls whose work overlaps on the GPU (different streams, or different maps
+ * at the same time) race and give wrong results: order them on one stream.
+ * Bundling adds into the memories with atomics, so the result is not bitwise
+ * reproducible.  Each tile is bundled relative to its own centre (no bundling
+ * patches), so points far from the centre of a wide tile take the exact phase
+ * reduction.
+ * Limits, both checked on the host before any GPU work (E_INVAL): n <=
+ * 262144 points per call; and the sort's tables plus the sorted points must
+ * fit the array: 4 B x ceil(n / 2048) x (2T + 1) for the per-block counts,
+ * 16 B per chunk, 8 B per point and a few 256-byte roundings, which only
+ * maps of many tiles with n near the limit can exceed.  The map's device must
+ * be current.  With VSAOGM_FLAG_CHECKED the call synchronises and returns
+ * E_DATA when points were rejected, as vsaogm_encode_bundle does (reading the
+ * counter into host stack variables allocates nothing).  No stage timing is
+ * recorded.  Errors: E_INVAL, E_CUDA, E_DATA.                               */
 int vsaogm_encode_bundle_noalloc(vsaogm_map *map, const float *xy_dev,
                                  const uint8_t *labels_dev, int64_t n, void *stream);
 

@@ -1355,8 +1355,11 @@ constexpr int kNoAllocMaxPoints = 1 << 18;
 constexpr int kNoAllocMaxDevices = 64;
 
 // Device address of g_noalloc_scratch on the current device, looked up once
-// per device (with that device current) and cached.
-static int noalloc_scratch(int device, unsigned char **out)
+// per device (with that device current) and cached.  vsaogm_create calls this
+// for its device, so the lookup (which under lazy module loading also loads
+// this file's module and reserves the array) happens at set-up time and not
+// in the first allocation-free call.
+int noalloc_scratch(int device, unsigned char **out)
 {
     static std::mutex mu;
     static unsigned char *addr[kNoAllocMaxDevices] = {};
@@ -1446,5 +1449,23 @@ extern "C" int vsaogm_encode_bundle_noalloc(vsaogm_map *m, const float *xy, cons
                          (long long)n, kNoAllocMaxPoints);
     if (!xy || !lab) return set_error(VSAOGM_E_INVAL, "xy and labels must not be NULL");
     if ((uintptr_t)xy % 8 != 0) return set_error(VSAOGM_E_INVAL, "xy must be 8-byte aligned");
-    return encode_bundle_noalloc(m, xy, lab, (int)n, (cudaStream_t)stream);
+    cudaStream_t st = (cudaStream_t)stream;
+    // checked maps report rejected points as vsaogm_encode_bundle does: the
+    // counter is read into host stack variables before and after (no allocation)
+    const bool checked = (m->cfg.flags & VSAOGM_FLAG_CHECKED) != 0;
+    unsigned long long before = 0, after = 0;
+    cudaError_t e;
+    if (checked && (e = cudaMemcpyAsync(&before, m->rejected, sizeof(before),
+                                        cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+        return cuda_error(e, "encode_noalloc");
+    int rc = encode_bundle_noalloc(m, xy, lab, (int)n, st);
+    if (rc || !checked) return rc;
+    if ((e = cudaMemcpyAsync(&after, m->rejected, sizeof(after), cudaMemcpyDeviceToHost, st)) !=
+            cudaSuccess ||
+        (e = cudaStreamSynchronize(st)) != cudaSuccess)
+        return cuda_error(e, "encode_noalloc");
+    if (after != before)
+        return set_error(VSAOGM_E_DATA, "%llu points rejected (label > 1 or non-finite)",
+                         after - before);
+    return VSAOGM_OK;
 }

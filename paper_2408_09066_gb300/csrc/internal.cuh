@@ -321,6 +321,9 @@ inline AxisDev axis_y(const vsaogm_map *m) { return {m->cfg.tiles_y, m->bnd_y_lo
 
 // encode.cu
 int encode_bundle(vsaogm_map *m, const float *xy, const uint8_t *lab, int64_t n, cudaStream_t st);
+// Device address of the allocation-free encode's static scratch on `device`
+// (which must be current); looked up once per device and cached.
+int noalloc_scratch(int device, unsigned char **out);
 int reserve_encode(vsaogm_map *m, int64_t n);
 // decode.cu
 int reserve_decode(vsaogm_map *m);

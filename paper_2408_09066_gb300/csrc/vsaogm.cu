@@ -407,6 +407,10 @@ int vsaogm_create(const vsaogm_config *cfg, vsaogm_map **out)
             break;
         }
         if (cfg->decode_prec != VSAOGM_DECODE_FP32 && (rc = build_tc_tables(m))) break;
+        // set-up of vsaogm_encode_bundle_noalloc on this device (the address
+        // of its static scratch), so that its first call does no lookup
+        unsigned char *scratch = nullptr;
+        if ((rc = noalloc_scratch(m->device, &scratch))) break;
     } while (0);
     if (rc != VSAOGM_OK) {
         free_map(m);
