@@ -10,8 +10,19 @@ steps, outside the step's own events.
 
 Prints one JSON line.  `value` is points bundled per second over whole steps
 (all ranks); cells decoded per second and p50/p99 step latency sit beside it.
+On one GPU the paper workload's line also carries, each timed on its own after
+the headline's timed region:
+  small          latency (p50/p99) of the 64 x 64 cell, D = 1024 map's step;
+  batch64        the 64-map batch as CUDA-graph replays, its stage rooflines
+                 and the same maps stepped one at a time;
+  serving        the 32-robot serving loop at several Poisson rates;
+  paper_shaped   the ToySim-, Intel- and EviLOG-shaped workloads;
+and, from the oracle (skipped with --no-cpu-baseline): cpu_baseline (one whole
+step of the oracle timed on the host cores), parity_full_size (every output
+element of each decode path against that step) and precision (the error of
+each decode path against the oracle on the 64 x 64 map at D = 1024 to 16384).
 `--impl reference` times the FP64 CPU oracle on bounded samples of the same
-workload instead (rank 0 only).
+workload instead (rank 0 only), plus one whole step.
 """
 from __future__ import annotations
 
@@ -29,10 +40,9 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
-# GB300 figures used for the rooflines: 152 SMs at up to 2070 MHz; per SM and
-# clock 16 MUFU sin/cos operations (a microbenchmark measured 15.2) and 128
-# FP32 FMA lane operations.
-SMS = 152
+# GB300 figures used for the rooflines: the SM count is read from the device
+# (152 on GB300); up to 2070 MHz; per SM and clock 16 MUFU sin/cos operations
+# (a microbenchmark measured 15.2) and 128 FP32 FMA lane operations.
 SM_MAX_MHZ = 2070.0
 MUFU_PER_SM_CLK = 16          # sin/cos ops per SM per clock (measured 15.2 at max clock)
 FP32_FMA_PER_SM_CLK = 128
@@ -69,7 +79,11 @@ def parse_args():
                         "batch64: 64 maps of uneven size stepped together (one launch per "
                         "stage, CUDA graph, autotuned)")
     p.add_argument("--no-cpu-baseline", action="store_true",
-                   help="skip the oracle timing (for quick runs)")
+                   help="skip everything that runs the oracle: the CPU baseline, the "
+                        "full-size parity record and the precision study (quick runs)")
+    p.add_argument("--headline-only", action="store_true",
+                   help="only the headline workload (skip the small-map, batch, serving and "
+                        "paper-shaped sections of the paper workload's line)")
     return p.parse_args()
 
 
@@ -176,6 +190,25 @@ class ClockSampler:
                                    if r[4].replace(".", "").isdigit()) if rows else None}
 
 
+def sm_count(torch, dev) -> int:
+    """Streaming multiprocessors of the device the roofline peaks are for."""
+    return int(torch.cuda.get_device_properties(dev).multi_processor_count)
+
+
+def alu_peaks(sms: int) -> dict:
+    """Joint MUFU + FMA bound of the encode in G exponentials/s (see the
+    constants above) and the MUFU-only bound, for `sms` SMs at SM_MAX_MHZ."""
+    sm_hz = sms * SM_MAX_MHZ * 1e6
+    a = (2 * FP32_FMA_PER_SM_CLK / MUFU_PER_SM_CLK - MUFU_PATH_FMA) / (
+        2 * FP32_FMA_PER_SM_CLK / MUFU_PER_SM_CLK - MUFU_PATH_FMA + POLY_PATH_FMA)
+    return {"joint": sm_hz / (2.0 * (1.0 - a) / MUFU_PER_SM_CLK) / 1e9,
+            "mufu": sm_hz * MUFU_PER_SM_CLK / 2.0 / 1e9, "poly_share": a,
+            "basis": (f"{sms} SMs x {SM_MAX_MHZ:.0f} MHz; MUFU sin/cos {MUFU_PER_SM_CLK}/clk/SM "
+                      f"and FP32 FMA {FP32_FMA_PER_SM_CLK}/clk/SM; an exponential costs 2 MUFU + "
+                      f"{MUFU_PATH_FMA} FMA lane-ops or {POLY_PATH_FMA} FMA lane-ops "
+                      f"(polynomial); both pipes saturate with {a:.3f} of them on the polynomial")}
+
+
 def percentile(xs, q):
     s = sorted(xs)
     if not s:
@@ -199,8 +232,8 @@ def _oracle_setup(wl):
 def oracle_step_time(wl, n_pts: int, n_cells: int, rng, r_occ=3, r_emp=3):
     """Times the oracle on a bounded sample of one step: encode + bundle n_pts
     random points with all D frequencies, decode n_cells random cells, and the
-    entropy / softmax pass over the full grid; extrapolates to the whole step
-    (cost is linear in points and in cells).  Returns (seconds, parts)."""
+    entropy / softmax pass over the full grid.  Returns (seconds of the whole
+    sampled step, parts)."""
     import numpy as np
     oracle, g, nx, ny = _oracle_setup(wl)
     idx = rng.choice(wl.n, n_pts, replace=False)
@@ -217,8 +250,27 @@ def oracle_step_time(wl, n_pts: int, n_cells: int, rng, r_occ=3, r_emp=3):
     H1 = oracle.entropy(Ph[1], r_occ)
     oracle.softmax_psd(H0, H1)
     t_ent = time.perf_counter() - t0
-    total = t_enc * wl.n / n_pts + t_dec * (wl.W * wl.H) / n_cells + t_ent
-    return total, {"encode_s": t_enc, "decode_s": t_dec, "entropy_s": t_ent}
+    return t_enc + t_dec + t_ent, {"encode_s": t_enc, "decode_s": t_dec, "entropy_s": t_ent}
+
+
+def oracle_full_step(wl, r_occ=3, r_emp=3):
+    """One whole step of the workload on the oracle, timed: the memories of
+    all points at all D frequencies, the similarity of every cell, the
+    non-linearity, the entropy of both classes, softmax and signed difference.
+    Returns (seconds, outputs, parts)."""
+    oracle, g, nx, ny = _oracle_setup(wl)
+    t0 = time.perf_counter()
+    om = oracle.memories(g, nx, ny, wl.xy, wl.labels, "tile")
+    t1 = time.perf_counter()
+    P = oracle.decode_map(g, nx, ny, om, "tile")
+    t2 = time.perf_counter()
+    Ph, _ = oracle.nonlinear(P)
+    H0 = oracle.entropy(Ph[0], r_emp)
+    H1 = oracle.entropy(Ph[1], r_occ)
+    pr1, _, ogm = oracle.softmax_psd(H0, H1)
+    t3 = time.perf_counter()
+    out = {"omega": om, "P": P, "Phat": Ph, "pr1": pr1, "ogm": ogm}
+    return t3 - t0, out, {"encode_s": t1 - t0, "decode_s": t2 - t1, "entropy_s": t3 - t2}
 
 
 def calibrate_oracle(wl, budget_s: float, rng):
@@ -238,24 +290,40 @@ def calibrate_oracle(wl, budget_s: float, rng):
     return n_pts, n_cells
 
 
-def cpu_baseline(wl, budget_s: float = 12.0) -> dict:
-    import numpy as np
+def sample_fraction(wl, budget_s: float, rng) -> float:
+    """Fraction f of the workload (f of its points and f of its cells, so the
+    sample keeps the step's mix of encode and decode work) whose oracle step
+    takes about budget_s, from two bounded probes; 1 when the whole step fits."""
+    probe_pts, probe_cells = min(wl.n, 2048), min(wl.W * wl.H, 512)
+    _, parts = oracle_step_time(wl, probe_pts, probe_cells, rng)
+    est = (parts["encode_s"] / probe_pts * wl.n + parts["decode_s"] / probe_cells * wl.W * wl.H
+           + parts["entropy_s"])
+    return 1.0 if est <= budget_s else budget_s / est
 
+
+def cpu_baseline(wl):
+    """The oracle timed over one whole step of the workload on the host cores
+    (no sampling, no extrapolation).  Returns (the line's cpu_baseline object,
+    the oracle's outputs for the full-size parity record)."""
     import oracle
-    rng = np.random.default_rng(7)
-    n_pts, n_cells = calibrate_oracle(wl, budget_s, rng)
-    t_step, parts = oracle_step_time(wl, n_pts, n_cells, rng)
-    return {"value": wl.n / t_step, "unit": "points/s", "cores": oracle.num_threads(),
+    t, out, parts = oracle_full_step(wl)
+    line = {"value": wl.n / t, "unit": "points/s", "cores": oracle.num_threads(),
             "kind": "oracle",
-            "sample": (f"FP64 oracle (memory-vector form) on {n_pts} random points x all "
-                       f"{wl.D} frequencies and {n_cells} random cells, plus the full-grid "
-                       f"entropy pass; extrapolated linearly to {wl.n} points and "
-                       f"{wl.W * wl.H} cells per step"),
-            "step_s_extrapolated": t_step, "sample_parts_s": parts}
+            "sample": (f"one whole step, not sampled: FP64 oracle (memory-vector form) on all "
+                       f"{wl.n} points x all {wl.D} frequencies, all {wl.W * wl.H} cells of "
+                       f"both classes, the non-linearity, entropy, softmax and signed "
+                       f"difference"),
+            "step_s": t, "parts_s": parts, "cells_per_s": wl.W * wl.H / t}
+    return line, out
 
 
 def run_reference(args):
-    """The FP64 CPU oracle on the same workload, bounded samples per step."""
+    """The FP64 CPU oracle on the same workload.  Each step is a bounded random
+    sample of the workload (a fraction f of its points with all frequencies,
+    the same fraction of its cells, the full-grid entropy), timed as it runs:
+    `value` is the points those steps processed over their measured time, and
+    `ms_per_step` the measured time of a sampled step.  One whole, unsampled
+    step is timed as well (`full_step`)."""
     import numpy as np
 
     import oracle
@@ -265,27 +333,35 @@ def run_reference(args):
     name = getattr(args, "workload", "paper")
     wl = make_workload(name)
     rng = np.random.default_rng(11)
-    n_pts, n_cells = calibrate_oracle(wl, 2.0, rng)
+    frac = sample_fraction(wl, 2.0, rng)
+    n_pts = max(1, min(wl.n, int(round(frac * wl.n))))
+    n_cells = max(1, min(wl.W * wl.H, int(round(frac * wl.W * wl.H))))
+    full_s, _, full_parts = oracle_full_step(wl)
     for _ in range(args.warmup):
         oracle_step_time(wl, n_pts, n_cells, rng)
     steps = [oracle_step_time(wl, n_pts, n_cells, rng)[0] for _ in range(args.steps)]
     mean_s = sum(steps) / len(steps)
-    value = wl.n / mean_s
+    value = n_pts * len(steps) / sum(steps)
+    sample = (f"each step: {n_pts} random points x all {wl.D} frequencies and {n_cells} "
+              f"random cells (the fraction {n_pts / wl.n:.4g} of the workload's "
+              f"{wl.n} points and {wl.W * wl.H} cells), full-grid entropy; value = points "
+              f"processed / measured time")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "points/s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": mean_s * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": data_of(name, wl),
         "config": workload_config(wl, "fp64 oracle"),
-        "cells_per_s": wl.W * wl.H / mean_s,
+        "points_per_sampled_step": n_pts, "cells_per_sampled_step": n_cells,
+        "cells_per_s": n_cells * len(steps) / sum(steps),
         "p50_ms": percentile(steps, 50) * 1e3, "p99_ms": percentile(steps, 99) * 1e3,
+        "full_step": {"s": full_s, "points_per_s": wl.n / full_s,
+                      "cells_per_s": wl.W * wl.H / full_s, "parts_s": full_parts,
+                      "how": "one whole step, every point and every cell, timed once"},
         "e2e": {"value": value, "unit": "points/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
         "cpu_baseline": {"value": value, "unit": "points/s", "cores": oracle.num_threads(),
-                         "kind": "oracle",
-                         "sample": (f"each step: {n_pts} random points x {wl.D} frequencies, "
-                                    f"{n_cells} random cells, full-grid entropy; extrapolated "
-                                    f"to {wl.n} points and {wl.W * wl.H} cells")},
+                         "kind": "oracle", "sample": sample},
         "gpu_launches": 0,
     }
     print(json.dumps(line), flush=True)
@@ -375,6 +451,193 @@ def _timed_steps(torch, m, bufs, steps, warmup, flush, d, clocks=None):
     m.set_timing(False)
     m.status()
     return [a.elapsed_time(b) for a, b in ev], stages, clk, t_wall
+
+
+def _cfg_of(V, wl, decode):
+    return V.default_config(D=wl.D, grid_w=wl.W, grid_h=wl.H, resolution=wl.res, x_min=wl.x_min,
+                            y_min=wl.y_min, tiles_x=wl.tiles_x, tiles_y=wl.tiles_y,
+                            length_scale=wl.length_scale, seed=wl.seed,
+                            decode_prec=DECODES[decode])
+
+
+def _bufs_of(torch, wl, dev):
+    return (torch.from_numpy(wl.xy).to(dev), torch.from_numpy(wl.labels).to(dev),
+            torch.empty((2, wl.H, wl.W), dtype=torch.float32, device=dev),
+            torch.empty((wl.H, wl.W), dtype=torch.float32, device=dev))
+
+
+def section_small(torch, V, dev, flush, d, steps=200, warmup=20):
+    """Latency of one step on the 64 x 64 cell, one-tile, D = 1024 map with one
+    360-beam scan (3960 points): reset, encode + bundle, query, per step."""
+    wl = make_workload("small")
+    bufs = _bufs_of(torch, wl, dev)
+    out = {"workload": workload_config(wl, "fp32 and bf16x3")["workload"], "steps": steps}
+    for decode in ("fp32", "bf16x3"):
+        with V.Map(_cfg_of(V, wl, decode)) as m:
+            ms, st, _, _ = _timed_steps(torch, m, bufs, steps, warmup, flush, d)
+        out[decode] = {"p50_ms": percentile(ms, 50), "p99_ms": percentile(ms, 99),
+                       "mean_ms": sum(ms) / len(ms), "points_per_s": wl.n * len(ms) / sum(ms) * 1e3,
+                       "launches_per_step": sum(v[1] for v in st.values()) / steps}
+    return out
+
+
+def section_paper_shaped(torch, V, dev, flush, d, steps=10, warmup=3):
+    """The ToySim-, Intel- and EviLOG-shaped workloads: step time with the
+    BF16x3 and the FP32-plain decode, throughput, stage fractions and map
+    quality."""
+    from paper_2408_09066_gb300 import metrics
+    pk = alu_peaks(sm_count(torch, dev))
+    peaks = measured_peaks()
+    rows = {}
+    for name in ("toysim", "intel", "evilog"):
+        wl = make_workload(name)
+        bufs = _bufs_of(torch, wl, dev)
+        row = {"workload": workload_config(wl, "bf16x3")["workload"]}
+        for decode in ("bf16x3", "fp32"):
+            with V.Map(_cfg_of(V, wl, decode)) as m:
+                ms, st, _, _ = _timed_steps(torch, m, bufs, steps, warmup, flush, d)
+            r = {"ms_per_step": sum(ms) / len(ms), "p50_ms": percentile(ms, 50),
+                 "p99_ms": percentile(ms, 99), "points_per_s": wl.n * len(ms) / sum(ms) * 1e3,
+                 "stage_ms_per_step": {k: v[0] / steps for k, v in st.items()}}
+            enc_s = st["encode"][0] / 1e3 / max(st["encode"][1], 1)
+            r["encode_frac_of_alu_peak"] = wl.n * wl.D / enc_s / 1e9 / pk["joint"]
+            dec_s = st["decode"][0] / 1e3 / steps
+            if decode == "bf16x3":
+                tf = 3 * 8.0 * wl.W * wl.H * wl.D / dec_s / 1e12
+                r["decode_tflops"] = tf
+                r["decode_frac_of_tensor_peak"] = tf / peaks["bf16_tflops"]
+                r["map_quality"] = metrics.evaluate(bufs[3].cpu().numpy(), wl.xy, wl.labels,
+                                                    wl.res, wl.x_min, wl.y_min)
+            row[decode] = r
+        rows[name] = row
+    return rows
+
+
+def section_serving(torch, V, duration=1.5):
+    """The serving loop: 32 robots with resident maps (256^2 to 1024^2 cells,
+    D = 8192, BF16x3), Poisson arrivals of scan updates (1080 beams x 21
+    points) and window queries (128^2 to 512^2 cells), half each, at a rate
+    below saturation and at rates at and beyond it; the last row drops requests
+    not started within 50 ms of arrival."""
+    from paper_2408_09066_gb300 import serving, synth
+    fleet = synth.robot_fleet(32)
+    cfgs = serving.fleet_configs(fleet, D=8192, decode_prec=V.DECODE_BF16X3)
+    max_points = max(len(sc[1]) for r in fleet for sc in r.scans)
+    srv = serving.Server(cfgs, max_points=max_points, max_window=512, n_slots=8)
+    rows = []
+    try:
+        srv.run(serving.poisson_requests(fleet, 2000.0, 0.5, 0.5, seed=99), realtime=False)
+        for i, (rate, deadline) in enumerate([(2000.0, None), (5000.0, None), (8000.0, None),
+                                              (8000.0, 0.05)]):
+            reqs = serving.poisson_requests(fleet, rate, duration, 0.5, seed=i,
+                                            deadline=deadline)
+            sm = serving.summarize(srv.run(reqs, realtime=True), duration)
+            sm.update({"offered_per_s": rate, "deadline_ms": None if deadline is None
+                       else deadline * 1e3, "saturated": sm["requests_per_s"] < 0.9 * rate})
+            rows.append(sm)
+        slots = srv.n_slots
+    finally:
+        srv.close()
+    return {"robots": 32, "D": 8192, "decode": "bf16x3", "slots": slots,
+            "duration_s_per_rate": duration, "rates": rows}
+
+
+def section_batch64(torch, V, dev, d, steps=20, warmup=3):
+    """The 64-map batch, as `--workload batch64` measures it (graph replays),
+    in summary."""
+    r = measure_batch(torch, V, dev, d, steps, warmup)
+    wls = r.pop("wls")
+    r["config"] = batch_config(wls, r.pop("tune"))
+    r.pop("n_total")
+    r.pop("cells_total")
+    r["steps"] = steps
+    return r
+
+
+TOL_FULL = {"omega": 3e-5, "P": {"fp32": 1e-4, "bf16x3": 1e-4, "fp16x3": 1e-4, "fp8x3": 1e-2},
+            "pr1": 1e-3, "ogm": 2e-3}
+
+
+def gpu_outputs(torch, V, dev, wl, decode, time_decode: int = 0):
+    """One map of `wl` through the C ABI: encode + bundle, the query (P,
+    Pr(psi = 1), OGM), the decode (P_hat) and the memories; optionally the
+    decode stage's mean milliseconds over `time_decode` further queries."""
+    import numpy as np
+    xy, lab, heat, occ = _bufs_of(torch, wl, dev)
+    ogm = torch.empty_like(occ)
+    ph = torch.empty_like(heat)
+    out = {}
+    with V.Map(_cfg_of(V, wl, decode)) as m:
+        m.encode_bundle(xy, lab)
+        m.query(heat, occ, ogm)
+        m.decode(ph)
+        om = m.get_memory()
+        torch.cuda.synchronize()
+        m.status()
+        if time_decode:
+            m.set_timing(True)
+            m.stage_times(reset=True)
+            for _ in range(time_decode):
+                m.query(heat, occ)
+            st = m.stage_times(reset=True)
+            m.set_timing(False)
+            out["decode_ms"] = st["decode"][0] / time_decode
+        out.update(omega=om.cpu().numpy(), P=heat.cpu().numpy(),
+                   Phat=ph.cpu().numpy(), pr1=occ.cpu().numpy(), ogm=ogm.cpu().numpy())
+    assert all(np.all(np.isfinite(v)) for v in out.values() if isinstance(v, np.ndarray))
+    return out
+
+
+def parity_errors(got, want, decode) -> dict:
+    """Every element of one map's outputs against the oracle's: normwise
+    max|gpu - oracle| / max|oracle| for the memories, P and P_hat, max absolute
+    difference for Pr(psi = 1) and OGM, and whether each is within tolerance."""
+    import numpy as np
+
+    def nw(a, b):
+        den = np.abs(b).max()
+        return float(np.abs(a - b).max() / den) if den > 0 else float(np.abs(a - b).max())
+    e = {"omega": nw(got["omega"], want["omega"]), "P": nw(got["P"], want["P"]),
+         "Phat": nw(got["Phat"], want["Phat"]),
+         "pr1": float(np.abs(got["pr1"] - want["pr1"]).max()),
+         "ogm": float(np.abs(got["ogm"] - want["ogm"]).max())}
+    tp = TOL_FULL["P"][decode]
+    e["within_tolerance"] = bool(e["omega"] <= TOL_FULL["omega"] and e["P"] <= tp and
+                                 e["Phat"] <= tp and e["pr1"] <= TOL_FULL["pr1"] and
+                                 e["ogm"] <= TOL_FULL["ogm"])
+    return e
+
+
+def oracle_legs(torch, V, dev, wl):
+    """Everything that runs the oracle, after the timed region: one whole step
+    of the headline workload timed on the host cores (the CPU baseline), every
+    element of each decode path's outputs at full size against that step's
+    outputs, and the precision study on the 64 x 64 map at D = 1024 to 16384."""
+    import oracle
+    from paper_2408_09066_gb300 import synth
+    cb, ref = cpu_baseline(wl)
+    full = {"workload": workload_config(wl, "all four")["workload"],
+            "tolerance": TOL_FULL, "compared": "every memory at every frequency, every cell "
+            "of P, P_hat, Pr(psi = 1) and OGM, against the oracle's whole step"}
+    for decode in ("fp32", "bf16x3", "fp16x3", "fp8x3"):
+        got = gpu_outputs(torch, V, dev, wl, decode, time_decode=5)
+        full[decode] = parity_errors(got, ref, decode)
+        full[decode]["decode_ms"] = got["decode_ms"]
+    prec = {"tolerance": TOL_FULL, "rows": []}
+    for D in (1024, 4096, 8192, 16384):
+        w = synth.small_scan(D=D)
+        o, g, nx, ny = _oracle_setup(w)
+        want = o.pipeline(g, nx, ny, w.xy, w.labels, 3, 3, 0.0, "tile")
+        for decode in ("fp32", "bf16x3", "fp16x3", "fp8x3"):
+            e = parity_errors(gpu_outputs(torch, V, dev, w, decode), want, decode)
+            prec["rows"].append({"map": "64x64, 1 tile, one 360-beam scan", "D": D,
+                                 "decode": decode, **e})
+    prec["rows"].extend({"map": "400x400, 4x4 tiles, 2.268M points", "D": wl.D,
+                         "decode": k, **{kk: v for kk, v in full[k].items() if kk != "decode_ms"}}
+                        for k in ("fp32", "bf16x3", "fp16x3", "fp8x3"))
+    prec["all_within_tolerance"] = all(r["within_tolerance"] for r in prec["rows"])
+    assert oracle.num_threads() == cb["cores"]
+    return cb, full, prec
 
 
 def run_ours(args):
@@ -487,21 +750,14 @@ def run_ours(args):
     exps = float(wl.n) * wl.D
     enc_avg_s = enc_ms / 1e3 / max(enc_n, 1)
     achieved = exps / enc_avg_s / 1e9
-    sm_hz = SMS * SM_MAX_MHZ * 1e6
-    peak_mufu = sm_hz * MUFU_PER_SM_CLK / 2.0 / 1e9
-    a = (2 * FP32_FMA_PER_SM_CLK / MUFU_PER_SM_CLK - MUFU_PATH_FMA) / (
-        2 * FP32_FMA_PER_SM_CLK / MUFU_PER_SM_CLK - MUFU_PATH_FMA + POLY_PATH_FMA)
-    peak_joint = sm_hz / (2.0 * (1.0 - a) / MUFU_PER_SM_CLK) / 1e9
+    sms = sm_count(torch, dev)
+    pk = alu_peaks(sms)
     src = os.path.join(ROOT, "paper_2408_09066_gb300", "csrc", "encode.cu")
     traffic = ENCODE_TRAFFIC["bytes"] if ENCODE_TRAFFIC["sha1"] == _sha1(src) else None
     roofline = {"bound": "alu", "kernel": "encode_chunk_x2_kernel", "achieved": achieved,
-                "peak": peak_joint, "unit": "Gexp/s", "frac": achieved / peak_joint,
-                "traffic": traffic, "peak_mufu_only": peak_mufu,
-                "frac_of_mufu_only": achieved / peak_mufu,
-                "peak_basis": (f"152 SMs x 2070 MHz; MUFU sin/cos 16/clk/SM and FP32 FMA "
-                               f"128/clk/SM; an exponential costs 2 MUFU + {MUFU_PATH_FMA} FMA "
-                               f"lane-ops or {POLY_PATH_FMA} FMA lane-ops (polynomial); both "
-                               f"pipes saturate with {a:.3f} of them on the polynomial")}
+                "peak": pk["joint"], "unit": "Gexp/s", "frac": achieved / pk["joint"],
+                "traffic": traffic, "peak_mufu_only": pk["mufu"],
+                "frac_of_mufu_only": achieved / pk["mufu"], "peak_basis": pk["basis"]}
     peaks = measured_peaks()
     cells = wl.W * wl.H
     dec_ms, dec_n = stages["decode"]
@@ -510,7 +766,7 @@ def run_ours(args):
     dec_s = dec_ms / 1e3 / args.steps
     ent_gbs = (2 * 4 + 4) * cells / (ent_ms / 1e3 / max(ent_n, 1)) / 1e9
     if args.decode == "fp32":
-        fp32_peak = SMS * FP32_FMA_PER_SM_CLK * 2 * SM_MAX_MHZ * 1e6 / 1e12
+        fp32_peak = sms * FP32_FMA_PER_SM_CLK * 2 * SM_MAX_MHZ * 1e6 / 1e12
         dec_tflops = 8.0 * cells * wl.D / dec_s / 1e12
         dec_line = {"bound": "alu", "achieved": dec_tflops, "peak": fp32_peak,
                     "unit": "TFLOP/s", "frac": dec_tflops / fp32_peak,
@@ -521,6 +777,7 @@ def run_ours(args):
         tc_peak = peaks["bf16_tflops"] * (2.0 if args.decode == "fp8x3" else 1.0)
         dec_line = {"bound": "tensor", "achieved": dec_tflops, "peak": tc_peak,
                     "unit": "TFLOP/s", "frac": dec_tflops / tc_peak,
+                    "method_tflops": dec_tflops / 3,
                     "peak_source": peaks["source"] + (
                         " bf16 x 2 (nominal fp8 / bf16 dense ratio)" if args.decode == "fp8x3"
                         else " bf16 (fp16 has the same dense rate)"),
@@ -555,8 +812,26 @@ def run_ours(args):
         "map_quality": map_quality,
     }
     m.close()
+    del xy_h, lab_h, occ_h
+    # the other configurations, each after the headline's timed region and
+    # timed on its own: latency of the small map, the 64-map batch, the
+    # serving loop and the paper-shaped workloads (one GPU only)
+    if d.world == 1 and args.workload == "paper" and not args.headline_only:
+        sections = (("small", lambda: section_small(torch, V, dev, flush, d)),
+                    ("batch64", lambda: section_batch64(torch, V, dev, d)),
+                    ("serving", lambda: section_serving(torch, V)),
+                    ("paper_shaped", lambda: section_paper_shaped(torch, V, dev, flush, d)))
+        for key, fn in sections:
+            t0 = time.perf_counter()
+            line[key] = fn()
+            line[key]["wall_s"] = time.perf_counter() - t0
     if d.rank == 0 and d.world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(wl)
+        t0 = time.perf_counter()
+        cb, full, prec = oracle_legs(torch, V, dev, wl)
+        line["cpu_baseline"] = cb
+        line["parity_full_size"] = full
+        line["precision"] = prec
+        line["oracle_legs_wall_s"] = time.perf_counter() - t0
     if d.rank == 0:
         print(json.dumps(line), flush=True)
     d.close()
@@ -615,21 +890,16 @@ def batch_oracle_time(wls, plan, rng):
     return total, text
 
 
-def run_batch(args):
-    import numpy as np
-    import torch
-
-    from paper_2408_09066_gb300 import build, synth
-    from paper_2408_09066_gb300 import vsaogm as V
-    d = Dist("nccl" if int(os.environ.get("WORLD_SIZE", "1")) > 1 else None)
-    torch.cuda.set_device(d.local)
-    if d.local == 0:
-        build.build()
-    d.barrier()
-    dev = torch.device("cuda", d.local)
+def measure_batch(torch, V, dev, d, steps, warmup, clocks=None, loop_steps=None):
+    """The 64-map batch on one GPU: the same maps stepped one at a time (FP32
+    plain and BF16x3 decode), then the batch autotuned, timed per stage on
+    uncaptured steps and timed as CUDA-graph replays, then end to end with
+    pinned host buffers around each replay.  Returns the measurements."""
+    from paper_2408_09066_gb300 import synth
     wls = synth.batch_maps(seed=1004 + d.rank)
     n_total = sum(len(w.labels) for w in wls)
     cells_total = sum(w.W * w.H for w in wls)
+    loop_steps = loop_steps or max(3, steps // 4)
 
     def cfg(w, prec):
         return V.default_config(D=w.D, grid_w=w.W, grid_h=w.H, resolution=w.res,
@@ -644,23 +914,18 @@ def run_batch(args):
     ogm = [torch.empty((w.H, w.W), dtype=torch.float32, device=dev) for w in wls]
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
     s = torch.cuda.Stream(dev)
-    bus = None
-    try:
-        bus = torch.cuda.get_device_properties(dev).pci_bus_id
-    except Exception:
-        pass
 
-    def timed(step, steps, warmup, clocks=None):
-        for _ in range(warmup):
+    def timed(step, n_steps, n_warm, clk=None):
+        for _ in range(n_warm):
             step()
         torch.cuda.synchronize()
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-              for _ in range(steps)]
+              for _ in range(n_steps)]
         d.barrier()
         torch.cuda.synchronize()
-        if clocks:
-            clocks.start()
-        for i in range(steps):
+        if clk:
+            clk.start()
+        for i in range(n_steps):
             with torch.cuda.stream(s):
                 flush.fill_(float(i))
             ev[i][0].record(s)
@@ -668,8 +933,8 @@ def run_batch(args):
             ev[i][1].record(s)
         torch.cuda.synchronize()
         d.barrier()
-        clk = clocks.stop() if clocks else None
-        return [a.elapsed_time(b) for a, b in ev], clk
+        rec = clk.stop() if clk else None
+        return [x.elapsed_time(y) for x, y in ev], rec
 
     # 1. the same maps stepped one at a time: FP32 plain decode, and BF16x3
     loops = {}
@@ -683,7 +948,7 @@ def run_batch(args):
                 m.encode_bundle(xy[i], lab[i], s)
                 m.query(heat[i], occ[i], ogm[i], stream=s)
 
-        ms, _ = timed(loop_step, max(3, args.steps // 4), args.warmup)
+        ms, _ = timed(loop_step, loop_steps, min(warmup, 3))
         tot = d.max(sum(ms) / 1e3)
         loops[name] = {"value": d.sum(float(n_total * len(ms))) / tot, "unit": "points/s",
                        "ms_per_step": tot / len(ms) * 1e3, "p50_ms": percentile(ms, 50),
@@ -694,66 +959,66 @@ def run_batch(args):
     # 2. the batch: autotune, per-stage timing (uncaptured steps), then graph replays
     maps = [V.Map(cfg(w, V.DECODE_BF16X3)) for w in wls]
     batch = V.Batch(maps)
-    tune = batch.autotune(xy, lab, heat, occ, stream=s)
-    batch.set_timing(True)
-    for _ in range(args.warmup):
-        batch.step(xy, lab, heat, occ, ogm, stream=s)
-    batch.stage_times(reset=True)
-    n_stage = max(3, args.steps // 4)
-    for i in range(n_stage):
-        with torch.cuda.stream(s):
+    try:
+        tune = batch.autotune(xy, lab, heat, occ, stream=s)
+        batch.set_timing(True)
+        for _ in range(warmup):
+            batch.step(xy, lab, heat, occ, ogm, stream=s)
+        batch.stage_times(reset=True)
+        n_stage = max(3, steps // 4)
+        for i in range(n_stage):
+            with torch.cuda.stream(s):
+                flush.fill_(float(i))
+            batch.step(xy, lab, heat, occ, ogm, stream=s)
+        stages = batch.stage_times(reset=True)
+        batch.set_timing(False)
+        batch.capture(xy, lab, heat, occ, ogm, stream=s)
+        batch.stage_times(reset=True)
+        step_ms, clk = timed(lambda: batch.replay(s), steps, warmup, clocks)
+        launches = sum(v[1] for v in batch.stage_times(reset=True).values()) / (steps + warmup)
+        batch.status()
+        total_s = d.max(sum(step_ms) / 1e3)
+
+        # 3. end to end: pinned host points in, occupancy maps out, around each replay
+        xy_h = [torch.from_numpy(w.xy).pin_memory() for w in wls]
+        lab_h = [torch.from_numpy(w.labels).pin_memory() for w in wls]
+        occ_h = [torch.empty((w.H, w.W), dtype=torch.float32).pin_memory() for w in wls]
+
+        def e2e_step():
+            with torch.cuda.stream(s):
+                for i in range(len(wls)):
+                    xy[i].copy_(xy_h[i], non_blocking=True)
+                    lab[i].copy_(lab_h[i], non_blocking=True)
+                batch.replay(s)
+                for i in range(len(wls)):
+                    occ_h[i].copy_(occ[i], non_blocking=True)
+            s.synchronize()
+
+        for _ in range(max(1, warmup)):
+            e2e_step()
+        e2e_s = []
+        for i in range(steps):
             flush.fill_(float(i))
-        batch.step(xy, lab, heat, occ, ogm, stream=s)
-    stages = batch.stage_times(reset=True)
-    batch.set_timing(False)
-    batch.capture(xy, lab, heat, occ, ogm, stream=s)
-    batch.stage_times(reset=True)
-    step_ms, clk = timed(lambda: batch.replay(s), args.steps, args.warmup, ClockSampler(bus))
-    launches = sum(v[1] for v in batch.stage_times(reset=True).values()) / (
-        args.steps + args.warmup)
-    batch.status()
-    total_s = d.max(sum(step_ms) / 1e3)
-    value = d.sum(float(n_total * args.steps)) / total_s
-
-    # 3. end to end: pinned host points in, occupancy maps out, around each replay
-    xy_h = [torch.from_numpy(w.xy).pin_memory() for w in wls]
-    lab_h = [torch.from_numpy(w.labels).pin_memory() for w in wls]
-    occ_h = [torch.empty((w.H, w.W), dtype=torch.float32).pin_memory() for w in wls]
-
-    def e2e_step():
-        with torch.cuda.stream(s):
-            for i in range(len(wls)):
-                xy[i].copy_(xy_h[i], non_blocking=True)
-                lab[i].copy_(lab_h[i], non_blocking=True)
-            batch.replay(s)
-            for i in range(len(wls)):
-                occ_h[i].copy_(occ[i], non_blocking=True)
-        s.synchronize()
-
-    for _ in range(max(1, args.warmup)):
-        e2e_step()
-    e2e_s = []
-    for i in range(args.steps):
-        flush.fill_(float(i))
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        e2e_step()
-        e2e_s.append(time.perf_counter() - t0)
-    e2e_total = d.max(sum(e2e_s))
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            e2e_step()
+            e2e_s.append(time.perf_counter() - t0)
+        e2e_total = d.max(sum(e2e_s))
+    finally:
+        batch.close()
+        for m in maps:
+            m.close()
 
     # rooflines from the per-stage times of the uncaptured steps
     peaks = measured_peaks()
+    pk = alu_peaks(sm_count(torch, dev))
     exps = float(sum(len(w.labels) * w.D for w in wls))
     enc_s = stages["encode"][0] / 1e3 / n_stage
-    sm_hz = SMS * SM_MAX_MHZ * 1e6
-    a = (2 * FP32_FMA_PER_SM_CLK / MUFU_PER_SM_CLK - MUFU_PATH_FMA) / (
-        2 * FP32_FMA_PER_SM_CLK / MUFU_PER_SM_CLK - MUFU_PATH_FMA + POLY_PATH_FMA)
-    peak_joint = sm_hz / (2.0 * (1.0 - a) / MUFU_PER_SM_CLK) / 1e9
     achieved = exps / enc_s / 1e9
     roofline = {"bound": "alu", "kernel": "encode_batch_kernel", "achieved": achieved,
-                "peak": peak_joint, "unit": "Gexp/s", "frac": achieved / peak_joint,
-                "traffic": None, "peak_mufu_only": sm_hz * MUFU_PER_SM_CLK / 2.0 / 1e9,
-                "peak_basis": "as the single-map encode: MUFU + FMA pipes, 152 SMs x 2070 MHz"}
+                "peak": pk["joint"], "unit": "Gexp/s", "frac": achieved / pk["joint"],
+                "traffic": None, "peak_mufu_only": pk["mufu"],
+                "peak_basis": "as the single-map encode: " + pk["basis"]}
     dec_s = stages["decode"][0] / 1e3 / n_stage
     flops = 3 * 8.0 * sum(w.W * w.H * w.D for w in wls)
     ent_s = stages["entropy"][0] / 1e3 / n_stage
@@ -762,32 +1027,61 @@ def run_batch(args):
         "decode_bf16x3_batch": {
             "bound": "tensor", "achieved": flops / dec_s / 1e12, "peak": peaks["bf16_tflops"],
             "unit": "TFLOP/s", "frac": flops / dec_s / 1e12 / peaks["bf16_tflops"],
+            "peak_source": peaks["source"] + " bf16 burst",
+            "method_tflops": flops / 3 / dec_s / 1e12,
             "kernels": "decode_tc_batch_kernel + slice sums",
-            "work": "3 split products x 8 flops per cell, class pair and frequency"},
+            "work": "3 split products x 8 flops per cell, class pair and frequency "
+                    "(method_tflops: the method's own 8 flops)"},
         "entropy_batch": {
             "bound": "hbm", "achieved": ent_bytes / ent_s / 1e9, "peak": peaks["hbm_gbs"],
             "unit": "GB/s", "frac": ent_bytes / ent_s / 1e9 / peaks["hbm_gbs"],
+            "peak_source": peaks["source"],
             "work": "16 B per cell: two class maps read, occupancy and signed difference written"},
     }
-    line = {
-        "metric": METRIC, "value": value, "unit": "points/s", "n_gpus": d.world,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_s / args.steps * 1e3,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-        "data": BATCH_DATA, "config": batch_config(wls, tune),
-        "cells_per_s": d.sum(float(cells_total * args.steps)) / total_s,
+    return {
+        "wls": wls, "tune": tune, "n_total": n_total, "cells_total": cells_total,
+        "value": d.sum(float(n_total * steps)) / total_s, "ms_per_step": total_s / steps * 1e3,
+        "cells_per_s": d.sum(float(cells_total * steps)) / total_s,
         "p50_ms": percentile(step_ms, 50), "p99_ms": percentile(step_ms, 99),
         "stage_ms_per_step": {k: v[0] / n_stage for k, v in stages.items()},
         "per_map_loops": loops,
-        "e2e": {"value": d.sum(float(n_total * args.steps)) / e2e_total, "unit": "points/s",
+        "e2e": {"value": d.sum(float(n_total * steps)) / e2e_total, "unit": "points/s",
                 "h2d_bytes_per_step": int(sum(w.xy.nbytes + w.labels.nbytes for w in wls)),
                 "d2h_bytes_per_step": int(4 * cells_total),
                 "p50_ms": percentile(e2e_s, 50) * 1e3, "p99_ms": percentile(e2e_s, 99) * 1e3},
         "roofline": roofline, "rooflines_other": other, "gpu_launches": int(launches),
         "clocks": clk,
     }
-    batch.close()
-    for m in maps:
-        m.close()
+
+
+def run_batch(args):
+    import numpy as np
+    import torch
+
+    from paper_2408_09066_gb300 import build
+    from paper_2408_09066_gb300 import vsaogm as V
+    d = Dist("nccl" if int(os.environ.get("WORLD_SIZE", "1")) > 1 else None)
+    torch.cuda.set_device(d.local)
+    if d.local == 0:
+        build.build()
+    d.barrier()
+    dev = torch.device("cuda", d.local)
+    bus = None
+    try:
+        bus = torch.cuda.get_device_properties(dev).pci_bus_id
+    except Exception:
+        pass
+    r = measure_batch(torch, V, dev, d, args.steps, args.warmup, ClockSampler(bus))
+    wls = r.pop("wls")
+    n_total = r.pop("n_total")
+    r.pop("cells_total")
+    line = {
+        "metric": METRIC, "value": r.pop("value"), "unit": "points/s", "n_gpus": d.world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": r.pop("ms_per_step"),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": BATCH_DATA, "config": batch_config(wls, r.pop("tune")),
+    }
+    line.update(r)
     if d.rank == 0 and d.world == 1 and not args.no_cpu_baseline:
         import oracle
         rng = np.random.default_rng(7)

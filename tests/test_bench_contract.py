@@ -43,8 +43,28 @@ def test_reference_line_has_the_contract_keys():
     assert e2e == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0,
                    "d2h_bytes_per_step": 0}
     assert d["gpu_launches"] == 0
-    # throughput is the workload's points over the mean step time
+    # throughput is the points the timed steps processed over their measured
+    # time: the whole workload per step when it fits the step budget
+    assert d["points_per_sampled_step"] == 3960
     assert abs(d["value"] * d["ms_per_step"] / 1e3 - 3960) < 1e-6 * 3960
+    # one whole, unsampled step is timed too
+    assert d["full_step"]["s"] > 0
+    assert abs(d["full_step"]["points_per_s"] * d["full_step"]["s"] - 3960) < 1e-6 * 3960
+
+
+def test_reference_steps_are_measured_samples_of_the_paper_workload(monkeypatch):
+    """On a workload too large for one step within the budget, each step is a
+    random sample with the workload's mix of points and cells, and `value` is
+    what the samples processed over their measured time (no extrapolation)."""
+    from paper_2408_09066_gb300 import synth
+    wl = synth.paper_trajectory(n_scans=4, D=2048)
+    monkeypatch.setattr(bench, "make_workload", lambda name, rank=0: wl)
+    monkeypatch.setattr(bench, "sample_fraction", lambda w, budget, rng: 0.125)
+    d = _reference_line("paper", steps=2, warmup=0)
+    n, c = d["points_per_sampled_step"], d["cells_per_sampled_step"]
+    assert n == round(0.125 * wl.n) and c == round(0.125 * wl.W * wl.H)
+    assert abs(d["value"] * d["ms_per_step"] / 1e3 - n) < 1e-6 * n
+    assert "fraction 0.125" in d["cpu_baseline"]["sample"]
 
 
 def test_data_field_names_the_workload():
