@@ -82,7 +82,7 @@ def test_only_the_allowed_entry_points_load_the_oracle():
     (their functions, or a branch taken unless --no-cpu-baseline is given)."""
     allowed_bench = {"cpu_baseline", "run_reference", "run_reference_batch", "_oracle_setup",
                      "calibrate_oracle", "oracle_step_time", "batch_oracle_plan",
-                     "batch_oracle_time"}
+                     "batch_oracle_time", "oracle_full_step", "sample_fraction", "oracle_legs"}
     for path in _files(ROOT, (".py",)):
         rel = os.path.relpath(path, ROOT)
         if rel.startswith(("tests" + os.sep, "oracle" + os.sep, "_work" + os.sep,
