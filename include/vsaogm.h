@@ -394,6 +394,18 @@ int vsaogm_batch_set_timing(vsaogm_batch *batch, int32_t enable);
 int vsaogm_batch_stage_times(vsaogm_batch *batch, double *ms, int64_t *launches,
                              int32_t reset);
 
+/* Device memory the library holds right now, in bytes, over every map and
+ * batch of the process (memories, tables, scratch, staging); the static
+ * scratch of vsaogm_encode_bundle_noalloc is not counted.  For callers that
+ * budget device memory (a server admitting maps), and to check that a failed
+ * call left nothing allocated.  Every device allocation of the library is
+ * counted here; with the environment variable VSAOGM_FAIL_ALLOC=n (n >= 1) set,
+ * the n-th device allocation made by one call fails as if the device were out
+ * of memory (a test hook for the E_NOMEM paths).
+ * No counterpart in the paper: a service of the library.
+ * Errors: E_INVAL (NULL). */
+int vsaogm_device_bytes(int64_t *bytes);
+
 /* Description of the last error on the calling thread ("" if none).
  * No counterpart in the paper: a service of the library. */
 const char *vsaogm_last_error(void);

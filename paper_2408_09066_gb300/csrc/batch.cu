@@ -102,9 +102,9 @@ int build_decode_items(vsaogm_batch *b)
         if (rc) return rc;
     }
     if ((int)items.size() > b->items_cap) {
-        if (b->items) cudaFree(b->items);
+        if (b->items) dev_free(b->items);
         b->items = nullptr;
-        cudaError_t e = cudaMalloc((void **)&b->items, sizeof(BatchDecodeItem) * items.size());
+        cudaError_t e = dev_malloc((void **)&b->items, sizeof(BatchDecodeItem) * items.size());
         if (e != cudaSuccess) return cuda_error(e, "batch decode items");
         b->items_cap = (int)items.size();
     }
@@ -265,7 +265,7 @@ int enqueue_step(vsaogm_batch *b, const float *const *xy, const uint8_t *const *
         dt.m[i] = BatchDecodeMap{m->omega, m->inv_norm, m->nu, m->col_off, m->row_off,
                                  m->tc_rot, m->row_tile, (float *)b->ws[i].dec_partial.ptr,
                                  m->status, D, kps, m->cfg.grid_w, m->cfg.grid_h,
-                                 m->cfg.tiles_x, u};
+                                 m->cfg.tiles_x, u, m->debug_wait_ns};
         BatchMapOut &o = ot.m[i];
         o.partial = (const float *)b->ws[i].dec_partial.ptr;
         o.heat = heat[i];
@@ -353,6 +353,7 @@ extern "C" {
 
 int vsaogm_batch_create(vsaogm_map *const *maps, int32_t count, vsaogm_batch **out)
 {
+    alloc_scope_begin();
     if (!out || !maps) return set_error(VSAOGM_E_INVAL, "NULL argument");
     *out = nullptr;
     if (count < 1 || count > kMaxBatchMaps)
@@ -377,7 +378,7 @@ int vsaogm_batch_create(vsaogm_map *const *maps, int32_t count, vsaogm_batch **o
     b->ws.resize(count);
     b->decode_prec = maps[0]->cfg.decode_prec;
     b->enc_ctas = encode_batch_ctas();
-    cudaError_t e = cudaMalloc((void **)&b->counter, sizeof(unsigned long long));
+    cudaError_t e = dev_malloc((void **)&b->counter, sizeof(unsigned long long));
     if (e != cudaSuccess) {
         int rc = cuda_error(e, "batch create");
         vsaogm_batch_destroy(b);
@@ -392,8 +393,8 @@ int vsaogm_batch_destroy(vsaogm_batch *b)
     if (!b) return VSAOGM_OK;
     cudaDeviceSynchronize();
     drop_graph(b);
-    if (b->counter) cudaFree(b->counter);
-    if (b->items) cudaFree(b->items);
+    if (b->counter) dev_free(b->counter);
+    if (b->items) dev_free(b->items);
     for (Scratch &w : b->ws) free_scratch(w);
     for (cudaEvent_t e : b->free_events) cudaEventDestroy(e);
     for (auto &p : b->pending)
@@ -419,6 +420,7 @@ int vsaogm_batch_step(vsaogm_batch *b, const float *const *xy, const uint8_t *co
                       const int64_t *n, float *const *heat, float *const *occ,
                       float *const *ogm, int32_t reset, void *stream)
 {
+    alloc_scope_begin();
     int rc = check_step_args(b, xy, lab, n, heat, occ);
     if (rc) return rc;
     const size_t sig = scratch_signature(b);
@@ -431,6 +433,7 @@ int vsaogm_batch_capture(vsaogm_batch *b, const float *const *xy, const uint8_t 
                          const int64_t *n, float *const *heat, float *const *occ,
                          float *const *ogm, int32_t reset, void *stream)
 {
+    alloc_scope_begin();
     int rc = check_step_args(b, xy, lab, n, heat, occ);
     if (rc) return rc;
     cudaStream_t st = (cudaStream_t)stream;
@@ -475,6 +478,7 @@ int vsaogm_batch_autotune(vsaogm_batch *b, const float *const *xy, const uint8_t
                           const int64_t *n, float *const *heat, float *const *occ, void *stream,
                           int32_t *poly_warps, int32_t *items_per_cta, int32_t *decode_waves)
 {
+    alloc_scope_begin();
     int rc = check_step_args(b, xy, lab, n, heat, occ);
     if (rc) return rc;
     drop_graph(b);  // the candidates grow and move the scratch a captured step uses

@@ -26,9 +26,11 @@
 //
 // Pipeline per CTA (one CTA per SM): 16 producer warps generate stage s into one
 // of two shared-memory buffers while the tensor cores run stage s - 1 from the
-// other; the memories and frequencies of stage s + 1 are loaded into registers
-// meanwhile.  A 17th warp issues the 24 MMAs of a stage (2 classes x 3 products
-// x 4 K-steps of 32 bytes) and commits them to the buffer's mbarrier.  The
+// other; a loader warp stages the memories, frequencies and step phasors of
+// each stage in the buffer's aux area ahead of the producers, and a further
+// warp issues the 24 MMAs of a stage (2 classes x 3 products x 4 K-steps of
+// 32 bytes) and commits them to the buffer's mbarrier; the warps hand stages
+// over through mbarriers only.  The
 // 128-byte swizzle puts 4-byte word kk of row m at byte
 // m * 128 + ((kk / 4) xor (m mod 8)) * 16 + (kk mod 4) * 4.  The epilogue reads
 // the two 128 x N FP32 accumulators from tensor memory, stages each warp's rows
@@ -57,7 +59,9 @@ constexpr int kM = 128;            // rows per block (MMA M)
 constexpr int kRowBytes = 128;
 constexpr int kProducers = 512;    // 16 warps generate the operands ...
 constexpr int kWarps = kProducers / 32;
-constexpr int kThreads = kProducers + 32;  // ... and one more issues the MMAs
+constexpr int kMmaWarp = kWarps;       // ... one issues the MMAs ...
+constexpr int kLoadWarp = kWarps + 1;  // ... and one stages each stage's inputs
+constexpr int kThreads = kProducers + 64;
 constexpr int kQ = kM / kWarps;    // rows (and columns) per thread
 constexpr int kATile = kM * kRowBytes;          // one A operand tile (16 KB)
 constexpr int kAStage = 4 * kATile;             // 2 classes x hi/lo (64 KB)
@@ -66,16 +70,28 @@ constexpr uint64_t kWaitNs = 2000000000ull;     // 2 s: far above any legitimate
 
 // Frequencies per stage (one 128-byte operand row).
 __host__ __device__ constexpr int stage_freqs(int prec) { return prec == kPrecFP8 ? 64 : 32; }
-// Bytes of the staged memories of one stage: (tile row, class, frequency) float2.
-__host__ __device__ constexpr int w_bytes(int prec) { return kMaxBlockTiles * 2 * stage_freqs(prec) * 8; }
+// Tile rows one block may span: kMaxBlockTiles, fewer for FP8, whose staged
+// memories per tile row are twice as long (two stages must fit in shared memory).
+__host__ __device__ constexpr int max_block_tiles(int prec)
+{
+    return prec == kPrecFP8 ? 14 : kMaxBlockTiles;
+}
+// Bytes of the aux area of one stage: the staged memories (tile row, class,
+// frequency) float2, then per frequency (nu_x, nu_y) and the x and y step
+// phasors, float2 each; rounded up so that every stage starts 1024-aligned.
+__host__ __device__ constexpr int aux_bytes(int prec)
+{
+    return ((max_block_tiles(prec) * 2 + 3) * stage_freqs(prec) * 8 + 1023) / 1024 * 1024;
+}
 // Bytes of one pipeline stage for MMA width N: A (both classes, hi and lo),
-// B (hi and lo) and the staged memories.
+// B (hi and lo) and the aux area.
 __host__ __device__ constexpr int stage_size(int prec, int N)
 {
-    return kAStage + 2 * N * kRowBytes + w_bytes(prec);
+    return kAStage + 2 * N * kRowBytes + aux_bytes(prec);
 }
 __host__ __device__ constexpr size_t smem_max(int prec) { return 1024 + 2 * (size_t)stage_size(prec, kM); }
-static_assert(smem_max(kPrecFP8) <= 232448, "two FP8 stages fit in shared memory");
+static_assert(smem_max(kPrecFP8) <= 232448 - 256, "two FP8 stages fit in shared memory");
+static_assert(smem_max(kPrecBF16) <= 232448 - 256, "two 16-bit stages fit in shared memory");
 
 __device__ __forceinline__ float2 phasor(float nu, float d)
 {
@@ -117,6 +133,44 @@ __device__ __forceinline__ void split_pair(float x, float y, uint32_t &hi, uint3
     }
 }
 
+// The split of both classes' operand values of one row and frequency, held as
+// packed pairs X = (x_0, x_1), Y = (y_0, y_1): class c's pair (x_c, y_c) gives
+// the words hi_c and lo_c, bit for bit as split_pair would.
+template <int P>
+__device__ __forceinline__ void split_classes(f32x2 X, f32x2 Y, uint32_t &h0, uint32_t &l0,
+                                              uint32_t &h1, uint32_t &l1)
+{
+    const float2 x = unpack2(X), y = unpack2(Y);
+    if (P == kPrecBF16) {
+        __nv_bfloat162 a = __floats2bfloat162_rn(x.x, y.x);
+        __nv_bfloat162 c = __floats2bfloat162_rn(x.y, y.y);
+        const uint32_t ha = *reinterpret_cast<uint32_t *>(&a);
+        const uint32_t hc = *reinterpret_cast<uint32_t *>(&c);
+        // bf16 -> f32 is a shift (low half) or a mask (high half) of the bits
+        const f32x2 fx = pack2(__uint_as_float(ha << 16), __uint_as_float(hc << 16));
+        const f32x2 fy = pack2(__uint_as_float(ha & 0xffff0000u), __uint_as_float(hc & 0xffff0000u));
+        const float2 rx = unpack2(sub2(X, fx)), ry = unpack2(sub2(Y, fy));
+        __nv_bfloat162 la = __floats2bfloat162_rn(rx.x, ry.x);
+        __nv_bfloat162 lc = __floats2bfloat162_rn(rx.y, ry.y);
+        h0 = ha;
+        h1 = hc;
+        l0 = *reinterpret_cast<uint32_t *>(&la);
+        l1 = *reinterpret_cast<uint32_t *>(&lc);
+    } else {
+        __half2 a = __floats2half2_rn(x.x, y.x);
+        __half2 c = __floats2half2_rn(x.y, y.y);
+        const float2 fa = __half22float2(a), fc = __half22float2(c);
+        const float2 rx = unpack2(sub2(X, pack2(fa.x, fc.x)));
+        const float2 ry = unpack2(sub2(Y, pack2(fa.y, fc.y)));
+        __half2 la = __floats2half2_rn(rx.x, ry.x);
+        __half2 lc = __floats2half2_rn(rx.y, ry.y);
+        h0 = *reinterpret_cast<uint32_t *>(&a);
+        h1 = *reinterpret_cast<uint32_t *>(&c);
+        l0 = *reinterpret_cast<uint32_t *>(&la);
+        l1 = *reinterpret_cast<uint32_t *>(&lc);
+    }
+}
+
 // The same for four FP8 (e4m3) values (x, y, z, w) in one word.  Conversions
 // saturate; the scaled operands stay far below e4m3's 448.
 __device__ __forceinline__ void split_quad_e4m3(float x, float y, float z, float w, uint32_t &hi,
@@ -155,43 +209,57 @@ __host__ __device__ constexpr uint32_t idesc_of(int N)
     return idesc_f16(kM, N, P == kPrecBF16);
 }
 
-// One (block of cells, frequency slice) item, executed by the whole CTA:
-// kProducers threads (16 warps) generate the operands, one more warp issues
-// the MMAs.  The block's columns lie in tile column b.tile; its rows may cross
-// tile rows (at most kMaxBlockTiles of them), each row using the memories of
-// its own tile: row j of the A operand is U_psi of tile (row_tile[j], b.tile).
+// One (block of cells, frequency slice) item, executed by the whole CTA: 16
+// producer warps generate the operands, one warp issues the MMAs and one warp
+// stages each stage's inputs.  The block's columns lie in tile column b.tile;
+// its rows may cross tile rows (at most max_block_tiles(P) of them), each row
+// using the memories of its own tile: row j of the A operand is U_psi of tile
+// (row_tile[j], b.tile).
 //
-// Hand-offs: producers arrive on full_bar[buf] (one arrival per warp, after
-// each thread's proxy fence) when stage s is in buffer buf = s & 1; the MMA
-// warp waits on it, issues the stage's 24 MMAs and commits them to
-// empty_bar[buf], which producers wait on before refilling buf at stage s + 2.
-// Producers also meet at named barrier 1 once per stage, because each stage's
-// memories are staged by all of them for all of them.  Every wait is bounded;
-// after a time-out the CTA stops waiting, records VSAOGM_E_TIMEOUT, drains
-// and frees its tensor memory.
+// Hand-offs, all through mbarriers (no CTA-wide barrier inside the loop):
+//  * the loader warp writes stage s's inputs (the memories of the block's
+//    tiles scaled by 1 / norm, the frequencies and the 16-cell step phasors)
+//    into the aux area of buffer buf = s & 1 and each of its lanes arrives
+//    on aux_full[buf];
+//    it refills buf for stage s + 2 once every producer warp has arrived on
+//    full_bar[buf] for stage s (they read the aux area before arriving);
+//  * producers wait on aux_full[buf] and, from stage 2 on, on empty_bar[buf]
+//    (the tensor cores have finished reading buf), generate stage s and
+//    arrive on full_bar[buf] (one arrival per warp, after a proxy fence);
+//  * the MMA warp waits on full_bar[buf], issues the stage's 24 MMAs and
+//    commits them to empty_bar[buf].
+// Producer warps therefore drift apart by up to a stage instead of meeting
+// at a barrier every stage.  Every wait is bounded; after a time-out the CTA
+// stops waiting, records VSAOGM_E_TIMEOUT, drains its MMAs and frees its
+// tensor memory.
 //
 // Producer lane l owns frequencies FPL l .. FPL l + FPL - 1 of the stage (FPL =
-// 1 for 16-bit operands, 2 for FP8): one 4-byte word per operand row.
+// 1 for 16-bit operands, 2 for FP8): one 4-byte word per operand row.  Each
+// thread carries the two classes' operand values of a row as packed pairs,
+// (Re U_0, Re U_1) and (-Im U_0, -Im U_1), so one packed multiply-add
+// advances both classes.
 template <int P>
 __device__ __forceinline__ void decode_tc_body(
     const DecodeBlock b, const int split, const float2 *__restrict__ omega,
     const float *__restrict__ inv_norm, const float *__restrict__ nu, int D, int tiles_x,
     const int *__restrict__ row_tile, OutGeom og, const float *__restrict__ col_off,
     const float *__restrict__ row_off, const float2 *__restrict__ rot, int k_per_split, int N,
-    float u_scale, float *__restrict__ partial, int *__restrict__ status)
+    float u_scale, float *__restrict__ partial, int *__restrict__ status,
+    uint64_t debug_wait_ns)
 {
     constexpr int KS = stage_freqs(P);       // frequencies per stage
     constexpr int FPL = KS / 32;             // frequencies per producer lane
-    constexpr int kWEnt = kMaxBlockTiles * 2 * KS;
-    constexpr int kWPerThread = kWEnt / kProducers;
-    static_assert(kWEnt % kProducers == 0, "staged memories split evenly");
     extern __shared__ uint8_t smem_raw[];
-    __shared__ uint64_t full_bar[2], empty_bar[2], done_bar;
+    __shared__ uint64_t full_bar[2], empty_bar[2], aux_full[2], done_bar, never_bar;
+    __shared__ float s_scale[2 * kMaxBlockTiles];  // 1 / norm x u_scale per (tile row, class)
     __shared__ uint32_t tmem_base_s;
     __shared__ int abort_s;
     volatile int *abort_v = &abort_s;
     uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     const int stage_bytes = stage_size(P, N);
+    // limit of the pipeline's waits: 2 s, or the failure-test knob (the drain
+    // before the tensor memory is freed always keeps the 2 s limit)
+    const uint64_t wait_ns = debug_wait_ns ? debug_wait_ns : kWaitNs;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int k_begin = split * k_per_split;
@@ -200,7 +268,7 @@ __device__ __forceinline__ void decode_tc_body(
     const int ni = b.i1 - b.i0, nj = b.j1 - b.j0;
     const int by0 = row_tile[b.j0];
     const int nt = row_tile[b.j1 - 1] - by0 + 1;  // tile rows of the block
-    if (nt < 1 || nt > kMaxBlockTiles || N > kM || N < 16 || (N & 15)) {
+    if (nt < 1 || nt > max_block_tiles(P) || N > kM || N < 16 || (N & 15)) {
         // the host never builds such a block; refuse it rather than index past smem
         if (tid == 0) atomicExch(status, VSAOGM_E_INVAL);
         return;
@@ -211,43 +279,51 @@ __device__ __forceinline__ void decode_tc_body(
         tmem_relinquish();
     }
     if (tid == 0) {
-        mbar_init(&full_bar[0], kWarps);
-        mbar_init(&full_bar[1], kWarps);
-        mbar_init(&empty_bar[0], 1);
-        mbar_init(&empty_bar[1], 1);
+        for (int q = 0; q < 2; ++q) {
+            mbar_init(&full_bar[q], kWarps);
+            mbar_init(&empty_bar[q], 1);
+            mbar_init(&aux_full[q], 32);  // every loader lane arrives after its stores
+        }
         mbar_init(&done_bar, 1);
+        mbar_init(&never_bar, 1);  // nothing arrives on it (failure test only)
         mbar_fence_init();
         abort_s = 0;
+    }
+    if (tid < 2 * nt) {
+        const int mem = 2 * ((by0 + (tid >> 1)) * tiles_x + b.tile) + (tid & 1);
+        s_scale[tid] = inv_norm[mem] * u_scale;
     }
     tc_fence_before_sync();
     __syncthreads();
     tc_fence_after_sync();
     const uint32_t tmem = tmem_base_s;
 
-    if (warp == kWarps) {
+    if (warp == kMmaWarp) {
         // ------------------------------------------------------ MMA warp
         const uint32_t idesc = idesc_of<P>(N);
+        // descriptors of buffer 0; buffer 1 and each K-step (32 bytes) add
+        // their byte offset / 16 to the start-address field
+        const uint32_t base = smem_addr(smem);
+        const uint64_t d_a = desc_k_sw128(base), d_bh = desc_k_sw128(base + kAStage),
+                       d_bl = desc_k_sw128(base + kAStage + N * kRowBytes);
         for (int s = 0; s < n_stages; ++s) {
             const int buf = s & 1;
-            if (!*abort_v && !mbar_wait(&full_bar[buf], (uint32_t)(s >> 1) & 1u, kWaitNs))
+            if (!*abort_v && !mbar_wait(&full_bar[buf], (uint32_t)(s >> 1) & 1u, wait_ns))
                 atomicExch(&abort_s, 1);
             tc_fence_after_sync();
             if (lane == 0) {
-                uint8_t *st = smem + (size_t)buf * stage_bytes;
-                const uint32_t a0 = smem_addr(st), bhi = smem_addr(st + kAStage);
-                const uint32_t blo = bhi + (uint32_t)(N * kRowBytes);
+                const uint64_t ob = (uint64_t)((buf * stage_bytes) >> 4);
 #pragma unroll
                 for (int kk = 0; kk < 4; ++kk) {
-                    const uint32_t off = kk * 32;  // one K-step: 32 bytes of each row
-                    const uint64_t dbh = desc_k_sw128(bhi + off), dbl = desc_k_sw128(blo + off);
+                    const uint64_t o = ob + (uint64_t)(kk * 2);  // 32 bytes of each row
 #pragma unroll
                     for (int c = 0; c < 2; ++c) {
-                        const uint64_t dah = desc_k_sw128(a0 + (2 * c) * kATile + off);
-                        const uint64_t dal = desc_k_sw128(a0 + (2 * c + 1) * kATile + off);
+                        const uint64_t dah = d_a + o + (uint64_t)((2 * c) * kATile >> 4);
+                        const uint64_t dal = d_a + o + (uint64_t)((2 * c + 1) * kATile >> 4);
                         const uint32_t d = tmem + 128u * c;
-                        mma<P>(d, dah, dbh, idesc, (s > 0 || kk > 0) ? 1u : 0u);
-                        mma<P>(d, dah, dbl, idesc, 1u);
-                        mma<P>(d, dal, dbh, idesc, 1u);
+                        mma<P>(d, dah, d_bh + o, idesc, (s > 0 || kk > 0) ? 1u : 0u);
+                        mma<P>(d, dah, d_bl + o, idesc, 1u);
+                        mma<P>(d, dal, d_bh + o, idesc, 1u);
                     }
                 }
                 mma_commit(&empty_bar[buf]);
@@ -257,11 +333,54 @@ __device__ __forceinline__ void decode_tc_body(
         // one more commit arrives when every MMA issued above has finished
         if (lane == 0) mma_commit(&done_bar);
         __syncwarp();
+    } else if (warp == kLoadWarp) {
+        // --------------------------------------------------- loader warp
+        // aux area of a buffer: the raw memories (tile row, class, frequency)
+        // as float2 [nt][2][KS], then per frequency (nu_x, nu_y) float2 [KS]
+        // and the step phasors along x and y, float2 [2][KS].  Copied with
+        // per-thread async copies that land on aux_full[buf]; frequencies past
+        // the slice's end are zero-filled (memories 0, so their U and hence
+        // their products vanish).  Lane l copies frequency l + 32 (i mod FPL)
+        // of memory row i / FPL for i = 0, 1, ...
+        const int n_rows = nt * 2;
+        // failure test: stall on a barrier nothing arrives at, for four times
+        // the pipeline's wait limit, so that the other warps' waits run out
+        if (debug_wait_ns) mbar_wait(&never_bar, 0u, 4 * debug_wait_ns);
+        for (int s = 0; s < n_stages; ++s) {
+            const int buf = s & 1;
+            // buf's aux area held stage s - 2, which every producer has read
+            // before arriving on full_bar[buf]
+            if (s >= 2 && !*abort_v &&
+                !mbar_wait(&full_bar[buf], (uint32_t)((s - 2) >> 1) & 1u, wait_ns))
+                atomicExch(&abort_s, 1);
+            float2 *aw = reinterpret_cast<float2 *>(smem + (size_t)buf * stage_bytes + kAStage +
+                                                    2 * N * kRowBytes);
+            float2 *af = aw + max_block_tiles(P) * 2 * KS;
+            const int k0 = k_begin + s * KS;
+            for (int i = 0; i < n_rows * FPL; ++i) {
+                const int r = i / FPL, kk = lane + 32 * (i % FPL), k = k0 + kk;
+                const int mem = 2 * ((by0 + (r >> 1)) * tiles_x + b.tile) + (r & 1);
+                const bool in = k < k_end;
+                cp_async<8>(&aw[r * KS + kk], omega + (size_t)mem * D + (in ? k : 0), in);
+            }
+#pragma unroll
+            for (int j = 0; j < FPL; ++j) {
+                const int kk = lane + 32 * j, k = k0 + kk;
+                const bool in = k < k_end;
+                const int kc = in ? k : 0;
+                cp_async<4>(&af[kk].x, nu + kc, in);
+                cp_async<4>(&af[kk].y, nu + D + kc, in);
+                cp_async<8>(&af[KS + kk], rot + kc, in);
+                cp_async<8>(&af[2 * KS + kk], rot + D + kc, in);
+            }
+            cp_async_mbar_arrive(&aux_full[buf]);
+        }
+        cp_async_wait_all();
     } else {
         // ------------------------------------------------------ producers
         // Fixed per-thread geometry: rows / columns warp + kWarps q, whose
         // 128-byte swizzle phase (row & 7) is warp & 7.
-        float dy[kQ], dx[kQ];
+        float dy[kQ], dx0;
         int tl[kQ];  // tile row of each A row, relative to by0
 #pragma unroll
         for (int q = 0; q < kQ; ++q) {
@@ -269,112 +388,52 @@ __device__ __forceinline__ void decode_tc_body(
             dy[q] = m < nj ? row_off[b.j0 + m] : 0.f;
             const int t = m < nj ? row_tile[b.j0 + m] - by0 : 0;
             tl[q] = VSAOGM_IN_BOUNDS(t >= 0 && t < nt) ? t : 0;  // staged memories exist for [0, nt)
-            dx[q] = m < ni ? col_off[b.i0 + m] : 0.f;
         }
+        dx0 = warp < ni ? col_off[b.i0 + warp] : 0.f;
         const uint32_t soff = (uint32_t)(warp * kRowBytes +
                                          ((((lane >> 2) ^ (warp & 7)) << 4) | ((lane & 3) << 2)));
-        // The memories of a stage's KS frequencies for the block's tiles are
-        // staged (scaled by 1 / norm) in the stage buffer's W area: entry
-        // e = (tile row, class, kk), kWPerThread entries per thread.
-        int w_mem[kWPerThread];
-        float w_scale[kWPerThread];
-#pragma unroll
-        for (int r = 0; r < kWPerThread; ++r) {
-            const int e = tid + kProducers * r;
-            const bool ev = e < nt * 2 * KS;
-            const int mem = 2 * ((by0 + e / (2 * KS)) * tiles_x + b.tile) + ((e / KS) & 1);
-            w_mem[r] = ev ? mem : -1;
-            w_scale[r] = ev ? inv_norm[mem] * u_scale : 0.f;
-        }
-        // prefetch registers: this lane's frequencies and staged memory entries
-        float pnx[FPL], pny[FPL];
-        float2 prx[FPL], pry[FPL];  // the 16-cell step phasors along x and y
-        float2 pw[kWPerThread];
-        auto prefetch = [&](int s) {
-#pragma unroll
-            for (int j = 0; j < FPL; ++j) {
-                const int k = k_begin + s * KS + FPL * lane + j;
-                pnx[j] = k < k_end ? nu[k] : 0.f;
-                pny[j] = k < k_end ? nu[D + k] : 0.f;
-                prx[j] = k < k_end ? rot[k] : make_float2(1.f, 0.f);
-                pry[j] = k < k_end ? rot[D + k] : make_float2(1.f, 0.f);
-            }
-#pragma unroll
-            for (int r = 0; r < kWPerThread; ++r) {
-                const int kk = k_begin + s * KS + (tid + kProducers * r) % KS;
-                pw[r] = (w_mem[r] >= 0 && kk < k_end) ? omega[(size_t)w_mem[r] * D + kk]
-                                                       : make_float2(0.f, 0.f);
-            }
-        };
-        // the memories of stage s go to the W area of buffer s & 1 (no MMA reads it)
-        auto stage_w = [&](int s) {
-            float2 *sw = reinterpret_cast<float2 *>(smem + (size_t)(s & 1) * stage_bytes +
-                                                    kAStage + 2 * N * kRowBytes);
-#pragma unroll
-            for (int r = 0; r < kWPerThread; ++r)
-                if (w_mem[r] >= 0)
-                    sw[tid + kProducers * r] =
-                        make_float2(pw[r].x * w_scale[r], pw[r].y * w_scale[r]);
-        };
-#pragma unroll
-        for (int j = 0; j < FPL; ++j) {
-            pnx[j] = pny[j] = 0.f;
-            prx[j] = pry[j] = make_float2(1.f, 0.f);
-        }
-        if (n_stages > 0) {
-            prefetch(0);
-            stage_w(0);
-        }
-        float nux[FPL], nuy[FPL];
-        float2 rsx[FPL], rsy[FPL];
-        // the phasors of the thread's first column and first row at the
-        // stage's frequencies, taken as soon as the frequencies are in (the
-        // end of the previous stage), off the next stage's dependency chain
-        float2 ax0[FPL], ey0[FPL];
-#pragma unroll
-        for (int j = 0; j < FPL; ++j) {
-            nux[j] = pnx[j];
-            nuy[j] = pny[j];
-            rsx[j] = prx[j];
-            rsy[j] = pry[j];
-            ax0[j] = phasor(nux[j], dx[0]);
-            ey0[j] = phasor(nuy[j], dy[0]);
-        }
-        named_bar_sync(1, kProducers);
         uint32_t phase_bits = 0u;  // bit b: parity to wait for on empty_bar[b]
 
         for (int s = 0; s < n_stages; ++s) {
             const int buf = s & 1;
             if (s >= 2) {
-                if (!*abort_v && !mbar_wait(&empty_bar[buf], (phase_bits >> buf) & 1u, kWaitNs))
+                if (!*abort_v && !mbar_wait(&empty_bar[buf], (phase_bits >> buf) & 1u, wait_ns))
                     atomicExch(&abort_s, 1);
                 phase_bits ^= 1u << buf;
             }
+            if (!*abort_v && !mbar_wait(&aux_full[buf], (uint32_t)(s >> 1) & 1u, wait_ns))
+                atomicExch(&abort_s, 1);
             uint8_t *st = smem + (size_t)buf * stage_bytes;
             uint8_t *bh = st + kAStage, *bl = bh + N * kRowBytes;
             const float2 *sw = reinterpret_cast<const float2 *>(bl + N * kRowBytes);
+            const float2 *sf = sw + max_block_tiles(P) * 2 * KS;
+            float nux[FPL], nuy[FPL];
+            float2 rsx[FPL], rsy[FPL];
+#pragma unroll
+            for (int j = 0; j < FPL; ++j) {
+                const float2 f = sf[FPL * lane + j];
+                nux[j] = f.x;
+                nuy[j] = f.y;
+                rsx[j] = sf[KS + FPL * lane + j];
+                rsy[j] = sf[2 * KS + FPL * lane + j];
+            }
             // No masking below: frequencies past the slice's end have staged
             // memories 0, so their U and hence their products vanish; rows and
             // columns past the block (its MMA padding) are never written out.
-            if (s + 1 < n_stages) prefetch(s + 1);  // in flight while this stage is generated
+            //
             // B operand: x phasors of the N columns.  Column warp + 16 (q + 1)
             // is 16 cells right of column warp + 16 q in the same tile, so its
             // phasor is the previous one times exp(i 2 pi nu_x 16 res).
-            // (Straight-line: every thread computes all kQ columns and stores
-            // those below N, so the compiler can interleave the B and A chains.)
             {
-                float2 rot[FPL], a[FPL];
+                float2 a[FPL];
 #pragma unroll
-                for (int j = 0; j < FPL; ++j) {
-                    rot[j] = rsx[j];
-                    a[j] = ax0[j];
-                }
+                for (int j = 0; j < FPL; ++j) a[j] = phasor(nux[j], dx0);
 #pragma unroll
                 for (int q = 0; q < kQ; ++q) {
                     const int n = warp + kWarps * q;
 #pragma unroll
                     for (int j = 0; j < FPL; ++j)
-                        if (q > 0) a[j] = cmul(a[j], rot[j]);
+                        if (q > 0) a[j] = cmul(a[j], rsx[j]);
                     uint32_t hi, lo;
                     if (FPL == 1)
                         split_pair<P>(a[0].x, a[0].y, hi, lo);
@@ -386,26 +445,32 @@ __device__ __forceinline__ void decode_tc_body(
                     }
                 }
             }
-            // A operands: U_psi = conj(w_hat_psi) * y phasor, stored as
-            // (Re, -Im).  Rows step by 16 cells too, except where a row enters
-            // the next tile (warp-uniform): there the phasor and the memories
-            // are reloaded.
+            // A operands: (Re U_psi, -Im U_psi) with U_psi = conj(w_hat_psi) x
+            // the y phasor, i.e. V_psi = conj(U_psi) = w_hat_psi x conj(phasor),
+            // held for both classes as packed pairs X = (Re V_0, Re V_1), Y =
+            // (Im V_0, Im V_1).  Rows step by 16 cells: V times conj(exp(i 2 pi
+            // nu_y 16 res)), except where a row enters the next tile
+            // (warp-uniform): there the phasor and the memories are reloaded.
             {
-                // U_psi of the thread's current row; the next row of the same
-                // tile is U_psi times exp(i 2 pi nu_y 16 res)
-                float2 rot[FPL], u0[FPL], u1[FPL];
+                f32x2 X[FPL], Y[FPL], R2[FPL], I2[FPL], NI2[FPL];
+#pragma unroll
+                for (int j = 0; j < FPL; ++j) {
+                    R2[j] = pack2(rsy[j].x, rsy[j].x);
+                    I2[j] = pack2(rsy[j].y, rsy[j].y);
+                    NI2[j] = pack2(-rsy[j].y, -rsy[j].y);
+                }
                 auto start_row = [&](int q) {
+                    const f32x2 sc = pack2(s_scale[2 * tl[q]], s_scale[2 * tl[q] + 1]);
 #pragma unroll
                     for (int j = 0; j < FPL; ++j) {
-                        const float2 e = q == 0 ? ey0[j] : phasor(nuy[j], dy[q]);
+                        const float2 e = phasor(nuy[j], dy[q]);
                         const float2 w0 = sw[(2 * tl[q]) * KS + FPL * lane + j];
                         const float2 w1 = sw[(2 * tl[q] + 1) * KS + FPL * lane + j];
-                        u0[j] = make_float2(w0.x * e.x + w0.y * e.y, w0.x * e.y - w0.y * e.x);
-                        u1[j] = make_float2(w1.x * e.x + w1.y * e.y, w1.x * e.y - w1.y * e.x);
+                        // V = w_hat x conj(e), w_hat = w / norm (x u_scale)
+                        X[j] = mul2(pack2(w0.x * e.x + w0.y * e.y, w1.x * e.x + w1.y * e.y), sc);
+                        Y[j] = mul2(pack2(w0.y * e.x - w0.x * e.y, w1.y * e.x - w1.x * e.y), sc);
                     }
                 };
-#pragma unroll
-                for (int j = 0; j < FPL; ++j) rot[j] = rsy[j];
                 start_row(0);
 #pragma unroll
                 for (int q = 0; q < kQ; ++q) {
@@ -413,48 +478,35 @@ __device__ __forceinline__ void decode_tc_body(
                         if (tl[q] != tl[q - 1]) {
                             start_row(q);
                         } else {
+                            // V' = V x conj(r) = (a r_x + b r_y, b r_x - a r_y)
 #pragma unroll
                             for (int j = 0; j < FPL; ++j) {
-                                u0[j] = cmul(u0[j], rot[j]);
-                                u1[j] = cmul(u1[j], rot[j]);
+                                const f32x2 x = fma2(X[j], R2[j], mul2(Y[j], I2[j]));
+                                Y[j] = fma2(Y[j], R2[j], mul2(X[j], NI2[j]));
+                                X[j] = x;
                             }
                         }
                     }
                     const uint32_t o = q * kWarps * kRowBytes + soff;
-                    uint32_t hi, lo;
-                    if (FPL == 1)
-                        split_pair<P>(u0[0].x, -u0[0].y, hi, lo);
-                    else
-                        split_quad_e4m3(u0[0].x, -u0[0].y, u0[FPL - 1].x, -u0[FPL - 1].y, hi, lo);
-                    *reinterpret_cast<uint32_t *>(st + 0 * kATile + o) = hi;
-                    *reinterpret_cast<uint32_t *>(st + 1 * kATile + o) = lo;
-                    if (FPL == 1)
-                        split_pair<P>(u1[0].x, -u1[0].y, hi, lo);
-                    else
-                        split_quad_e4m3(u1[0].x, -u1[0].y, u1[FPL - 1].x, -u1[FPL - 1].y, hi, lo);
-                    *reinterpret_cast<uint32_t *>(st + 2 * kATile + o) = hi;
-                    *reinterpret_cast<uint32_t *>(st + 3 * kATile + o) = lo;
+                    uint32_t h0, l0, h1, l1;
+                    if (FPL == 1) {
+                        split_classes<P>(X[0], Y[0], h0, l0, h1, l1);
+                    } else {
+                        const float2 x0 = unpack2(X[0]), y0 = unpack2(Y[0]);
+                        const float2 x1 = unpack2(X[FPL - 1]), y1 = unpack2(Y[FPL - 1]);
+                        split_quad_e4m3(x0.x, y0.x, x1.x, y1.x, h0, l0);
+                        split_quad_e4m3(x0.y, y0.y, x1.y, y1.y, h1, l1);
+                    }
+                    *reinterpret_cast<uint32_t *>(st + 0 * kATile + o) = h0;
+                    *reinterpret_cast<uint32_t *>(st + 1 * kATile + o) = l0;
+                    *reinterpret_cast<uint32_t *>(st + 2 * kATile + o) = h1;
+                    *reinterpret_cast<uint32_t *>(st + 3 * kATile + o) = l1;
                 }
             }
             // hand the stage to the MMA warp
             fence_async_shared();
             __syncwarp();
             if (lane == 0) mbar_arrive(&full_bar[buf]);
-            // the next stage's memories into the other buffer's W area (its
-            // readers finished before the previous producer barrier)
-            if (s + 1 < n_stages) {
-                stage_w(s + 1);
-#pragma unroll
-                for (int j = 0; j < FPL; ++j) {
-                    nux[j] = pnx[j];
-                    nuy[j] = pny[j];
-                    rsx[j] = prx[j];
-                    rsy[j] = pry[j];
-                    ax0[j] = phasor(nux[j], dx[0]);
-                    ey0[j] = phasor(nuy[j], dy[0]);
-                }
-            }
-            named_bar_sync(1, kProducers);
         }
     }
     // epilogue (producers): warp w reads TMEM lanes 32 (w & 3) .. + 31 (its lane
@@ -509,10 +561,11 @@ __global__ void __launch_bounds__(kThreads, 1) decode_tc_kernel(
     const float *__restrict__ nu, int D, int tiles_x, const int *__restrict__ row_tile, OutGeom og,
     const float *__restrict__ col_off, const float *__restrict__ row_off,
     const float2 *__restrict__ rot, int k_per_split, int N, float u_scale,
-    float *__restrict__ partial, int *__restrict__ status)
+    float *__restrict__ partial, int *__restrict__ status, uint64_t debug_wait_ns)
 {
     decode_tc_body<P>(blocks.b[blockIdx.x], blockIdx.y, omega, inv_norm, nu, D, tiles_x, row_tile,
-                      og, col_off, row_off, rot, k_per_split, N, u_scale, partial, status);
+                      og, col_off, row_off, rot, k_per_split, N, u_scale, partial, status,
+                      debug_wait_ns);
 }
 
 // Many maps in one launch: CTA q decodes item q of a device list of
@@ -526,7 +579,7 @@ __global__ void __launch_bounds__(kThreads, 1) decode_tc_batch_kernel(
     const int N = ((it.b.i1 - it.b.i0) + 15) / 16 * 16;
     decode_tc_body<P>(it.b, it.split, M.omega, M.inv_norm, M.nu, M.D, M.tiles_x, M.row_tile,
                       OutGeom{0, 0, M.W, M.H}, M.col_off, M.row_off, M.rot, M.k_per_split, N,
-                      M.u_scale, M.partial, M.status);
+                      M.u_scale, M.partial, M.status, M.debug_wait_ns);
 }
 
 // rot[k] = exp(i 2 pi nu[k] step) for the x frequencies, then the y ones: the
@@ -574,11 +627,12 @@ int tc_stage_freqs(int decode_prec) { return stage_freqs(prec_of(decode_prec)); 
 VSAOGM_CHECK_TU(decode_tc)
 
 // Blocks of at most 128 x 128 cells covering region r for the tensor-core
-// decode: columns inside one tile column, rows across at most kMaxBlockTiles
-// tile rows.
+// decode: columns inside one tile column, rows across at most
+// max_block_tiles tile rows (kMaxBlockTiles; 14 for FP8).
 void tc_blocks(const vsaogm_map *m, Region r, std::vector<DecodeBlock> &out)
 {
     out.clear();
+    const int max_tiles = max_block_tiles(prec_of(m->cfg.decode_prec));
     const std::vector<int> &yl = m->tile_last[1];  // tiles are monotonic in the row index
     const int ty = m->cfg.tiles_y;
     for (int bx = 0; bx < m->cfg.tiles_x; ++bx) {
@@ -590,9 +644,9 @@ void tc_blocks(const vsaogm_map *m, Region r, std::vector<DecodeBlock> &out)
             int by = 0;
             for (int j0 = r.y0; j0 < r.y1;) {
                 while (by < ty - 1 && yl[by] <= j0) ++by;  // tile row of row j0
-                // rows up to the end of the kMaxBlockTiles-th tile row from by
+                // rows up to the end of the max_tiles-th tile row from by
                 int cap = j0 + 1;
-                for (int t = by; t < std::min(by + kMaxBlockTiles, ty); ++t) cap = std::max(cap, yl[t]);
+                for (int t = by; t < std::min(by + max_tiles, ty); ++t) cap = std::max(cap, yl[t]);
                 const int j1 = std::min({j0 + kM, r.y1, cap});
                 out.push_back(DecodeBlock{bx, i0, j0, i1, j1});
                 j0 = j1;
@@ -634,7 +688,7 @@ float tc_u_scale(const vsaogm_map *m)
 int build_tc_tables(vsaogm_map *m)
 {
     const int D = m->cfg.D;
-    cudaError_t e = cudaMalloc((void **)&m->tc_rot, sizeof(float2) * 2 * (size_t)D);
+    cudaError_t e = dev_malloc((void **)&m->tc_rot, sizeof(float2) * 2 * (size_t)D);
     if (e != cudaSuccess) return cuda_error(e, "decode tables");
     // the same float step as the kernel's rows and columns: kWarps cells
     tc_rot_kernel<<<(2 * D + 255) / 256, 256>>>(m->nu, 2 * D, (float)kWarps * m->cfg.resolution,
@@ -684,7 +738,7 @@ int decode_tensor_cores(vsaogm_map *m, Region r, float *heat, cudaStream_t st)
 #define VSAOGM_LAUNCH_TC(PP)                                                                   \
     decode_tc_kernel<PP><<<grid, kThreads, smem, st>>>(                                        \
         batch, m->omega, m->inv_norm, m->nu, D, m->cfg.tiles_x, m->row_tile, og, m->col_off,    \
-        m->row_off, m->tc_rot, kps, N, u_scale, part, m->status)
+        m->row_off, m->tc_rot, kps, N, u_scale, part, m->status, m->debug_wait_ns)
         if (P == kPrecFP8)
             VSAOGM_LAUNCH_TC(kPrecFP8);
         else if (P == kPrecFP16)

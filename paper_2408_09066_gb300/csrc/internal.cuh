@@ -189,6 +189,7 @@ struct BatchDecodeMap {
     int *status;
     int D, k_per_split, W, H, tiles_x;
     float u_scale;
+    uint64_t debug_wait_ns;  // the failure-test wait limit (0: off)
 };
 struct BatchDecodeTable {
     int n_maps;
@@ -280,6 +281,10 @@ struct vsaogm_map {
     float *col_off, *row_off;    // [W], [H]
     unsigned *enc_cnt;           // [S][ceil(D / 512)]: the encode's finished-chunk counters
     float2 *tc_rot;              // tensor-core decode: [2][D] phasors of a 16-cell step
+    // failure test (VSAOGM_DEBUG_WAIT_NS at creation; 0: off): the tensor-core
+    // decode's pipeline waits give up after this many nanoseconds and its
+    // loader warp first stalls for four times as long, so that they do
+    uint64_t debug_wait_ns;
     // bundling patches: [0] coarse (phases below 32 turns), [1] fine (below 4
     // turns); device tables of patch centres below
     vsaogm_impl::PatchDev patches[2];
@@ -293,6 +298,16 @@ struct vsaogm_map {
 };
 
 namespace vsaogm_impl {
+
+// Every device allocation of the library goes through dev_malloc / dev_free,
+// which keep count of the bytes held (vsaogm_device_bytes).  Test hook: with
+// VSAOGM_FAIL_ALLOC=n (n >= 1) in the environment, the n-th device allocation
+// made since the calling entry point began (alloc_scope_begin) fails as if the
+// device were out of memory, without calling cudaMalloc.
+cudaError_t dev_malloc(void **p, size_t bytes);
+cudaError_t dev_free(void *p);
+void alloc_scope_begin();
+long long device_bytes_held();
 
 // Error reporting (thread-local message; see vsaogm_last_error).
 int set_error(int code, const char *fmt, ...);

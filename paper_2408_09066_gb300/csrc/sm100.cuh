@@ -65,6 +65,31 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, uint64
     return false;
 }
 
+// ------------------------------------------------- per-thread async copies
+// cp.async of `bytes` (4 or 8) bytes from global to shared memory; when
+// `valid` is false nothing is read and the destination is zero-filled.
+template <int bytes>
+__device__ __forceinline__ void cp_async(void *dst_smem, const void *src, bool valid)
+{
+    static_assert(bytes == 4 || bytes == 8, "cp.async.ca copies 4, 8 or 16 bytes");
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;" ::"r"(smem_addr(dst_smem)),
+                 "l"(src), "n"(bytes), "r"(valid ? bytes : 0)
+                 : "memory");
+}
+
+// Arrives on *bar once every cp.async this thread issued before has landed
+// (the arrival is one of the barrier's expected count).
+__device__ __forceinline__ void cp_async_mbar_arrive(uint64_t *bar)
+{
+    asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_addr(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void cp_async_wait_all()
+{
+    asm volatile("cp.async.wait_all;" ::: "memory");
+}
+
 // Named barrier `id` (1..15) over `count` threads (a multiple of 32).
 __device__ __forceinline__ void named_bar_sync(uint32_t id, uint32_t count)
 {

@@ -6,6 +6,8 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
+#include <unordered_map>
 #include <vector>
 
 #include "internal.cuh"
@@ -14,9 +16,52 @@ using namespace vsaogm_impl;
 
 namespace {
 thread_local char g_err[512] = "";
+std::mutex g_alloc_mu;
+std::unordered_map<void *, size_t> g_alloc_live;  // device blocks the library holds
+long long g_alloc_bytes = 0;
+thread_local int g_alloc_count = 0;  // allocations since the entry point began
 }
 
 namespace vsaogm_impl {
+
+void alloc_scope_begin() { g_alloc_count = 0; }
+
+cudaError_t dev_malloc(void **p, size_t bytes)
+{
+    *p = nullptr;
+    ++g_alloc_count;
+    if (const char *v = getenv("VSAOGM_FAIL_ALLOC"))
+        if (atoi(v) == g_alloc_count) return cudaErrorMemoryAllocation;
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        return e;
+    }
+    std::lock_guard<std::mutex> lock(g_alloc_mu);
+    g_alloc_live[*p] = bytes;
+    g_alloc_bytes += (long long)bytes;
+    return e;
+}
+
+cudaError_t dev_free(void *p)
+{
+    if (!p) return cudaSuccess;
+    {
+        std::lock_guard<std::mutex> lock(g_alloc_mu);
+        auto it = g_alloc_live.find(p);
+        if (it != g_alloc_live.end()) {
+            g_alloc_bytes -= (long long)it->second;
+            g_alloc_live.erase(it);
+        }
+    }
+    return cudaFree(p);
+}
+
+long long device_bytes_held()
+{
+    std::lock_guard<std::mutex> lock(g_alloc_mu);
+    return g_alloc_bytes;
+}
 
 int set_error(int code, const char *fmt, ...)
 {
@@ -41,11 +86,11 @@ int cuda_error(cudaError_t e, const char *what)
 int ensure(DevBuf &b, size_t bytes)
 {
     if (b.bytes >= bytes) return VSAOGM_OK;
-    if (b.ptr) cudaFree(b.ptr);
+    if (b.ptr) dev_free(b.ptr);
     b.ptr = nullptr;
     b.bytes = 0;
     size_t want = bytes + bytes / 8 + 256;  // headroom against repeated growth
-    cudaError_t e = cudaMalloc(&b.ptr, want);
+    cudaError_t e = dev_malloc(&b.ptr, want);
     if (e != cudaSuccess) {
         b.ptr = nullptr;
         return cuda_error(e, "scratch allocation");
@@ -105,7 +150,7 @@ void free_scratch(Scratch &ws)
                       &ws.partial,  &ws.stage_xy,  &ws.stage_lab, &ws.stage_heat,
                       &ws.stage_occ, &ws.dec_partial};
     for (DevBuf *b : bufs) {
-        if (b->ptr) cudaFree(b->ptr);
+        if (b->ptr) dev_free(b->ptr);
         b->ptr = nullptr;
         b->bytes = 0;
     }
@@ -144,7 +189,7 @@ void free_map(vsaogm_map *m)
                     m->col_off, m->row_off, m->status, m->patch_cx[0], m->patch_cy[0],
                     m->patch_cx[1], m->patch_cy[1], m->tc_rot};
     for (void *p : ptrs)
-        if (p) cudaFree(p);
+        if (p) dev_free(p);
     free_scratch(m->ws);
     for (cudaEvent_t e : m->timer.free_events) cudaEventDestroy(e);
     for (auto &p : m->timer.pending) {
@@ -232,7 +277,7 @@ template <typename T>
 int upload(T **dst, const std::vector<T> &v)
 {
     size_t bytes = sizeof(T) * (v.empty() ? 1 : v.size());
-    cudaError_t e = cudaMalloc((void **)dst, bytes);
+    cudaError_t e = dev_malloc((void **)dst, bytes);
     if (e != cudaSuccess) {
         *dst = nullptr;
         return cuda_error(e, "map allocation");
@@ -278,6 +323,13 @@ extern "C" {
 
 const char *vsaogm_last_error(void) { return g_err; }
 
+int vsaogm_device_bytes(int64_t *bytes)
+{
+    if (!bytes) return set_error(VSAOGM_E_INVAL, "bytes is NULL");
+    *bytes = (int64_t)device_bytes_held();
+    return VSAOGM_OK;
+}
+
 void vsaogm_config_default(vsaogm_config *c)
 {
     if (!c) return;
@@ -297,6 +349,7 @@ void vsaogm_config_default(vsaogm_config *c)
 
 int vsaogm_create(const vsaogm_config *cfg, vsaogm_map **out)
 {
+    alloc_scope_begin();
     if (!out) return set_error(VSAOGM_E_INVAL, "out is NULL");
     *out = nullptr;
     VSA_TRY(validate(cfg));
@@ -336,6 +389,10 @@ int vsaogm_create(const vsaogm_config *cfg, vsaogm_map **out)
             m->encode_poly_pairs = std::max(0, std::min(3, atoi(v)));
         if (const char *v = getenv("VSAOGM_ENCODE_POLY_WARPS"))
             m->encode_poly_warps = std::max(-1, std::min(8, atoi(v)));
+        // failure test of the bounded waits (see vsaogm_status)
+        m->debug_wait_ns = 0;
+        if (const char *v = getenv("VSAOGM_DEBUG_WAIT_NS"))
+            m->debug_wait_ns = (uint64_t)std::max(0LL, std::min(1000000000LL, atoll(v)));
         std::vector<float> nu(m->host_nu, m->host_nu + 2 * (size_t)D);
         if ((rc = upload(&m->nu, nu))) break;
         // Tiling and cell tables (Sec. III-B3, Algorithm 1).
@@ -390,16 +447,16 @@ int vsaogm_create(const vsaogm_config *cfg, vsaogm_map **out)
         disk_half_widths(cfg->r_emp, m->r_hw[0]);
         disk_half_widths(cfg->r_occ, m->r_hw[1]);
         // Memories and per-map device state.
-        cudaError_t e = cudaMalloc((void **)&m->omega, sizeof(float2) * (size_t)m->S * D);
-        if (e == cudaSuccess) e = cudaMalloc((void **)&m->inv_norm, sizeof(float) * m->S);
-        if (e == cudaSuccess) e = cudaMalloc((void **)&m->maxima, sizeof(unsigned) * 2);
-        if (e == cudaSuccess) e = cudaMalloc((void **)&m->rejected, sizeof(unsigned long long));
+        cudaError_t e = dev_malloc((void **)&m->omega, sizeof(float2) * (size_t)m->S * D);
+        if (e == cudaSuccess) e = dev_malloc((void **)&m->inv_norm, sizeof(float) * m->S);
+        if (e == cudaSuccess) e = dev_malloc((void **)&m->maxima, sizeof(unsigned) * 2);
+        if (e == cudaSuccess) e = dev_malloc((void **)&m->rejected, sizeof(unsigned long long));
         if (e == cudaSuccess) e = cudaMemset(m->omega, 0, sizeof(float2) * (size_t)m->S * D);
         if (e == cudaSuccess) e = cudaMemset(m->rejected, 0, sizeof(unsigned long long));
         // the encode's finished-chunk counters: one per memory and slice of at
         // least 512 frequencies; each is back at zero when a launch ends
         const size_t n_cnt = (size_t)m->S * ((D + 511) / 512);
-        if (e == cudaSuccess) e = cudaMalloc((void **)&m->enc_cnt, sizeof(unsigned) * n_cnt);
+        if (e == cudaSuccess) e = dev_malloc((void **)&m->enc_cnt, sizeof(unsigned) * n_cnt);
         if (e == cudaSuccess) e = cudaMemset(m->enc_cnt, 0, sizeof(unsigned) * n_cnt);
         if (e == cudaSuccess) e = cudaDeviceSynchronize();
         if (e != cudaSuccess) {
@@ -442,6 +499,7 @@ int vsaogm_reset(vsaogm_map *m, void *stream)
 int vsaogm_encode_bundle(vsaogm_map *m, const float *xy, const uint8_t *lab, int64_t n,
                          void *stream)
 {
+    alloc_scope_begin();
     if (!m) return set_error(VSAOGM_E_INVAL, "map is NULL");
     if (n < 0) return set_error(VSAOGM_E_INVAL, "n must be >= 0");
     if (n == 0) return VSAOGM_OK;
@@ -469,6 +527,7 @@ int vsaogm_encode_bundle(vsaogm_map *m, const float *xy, const uint8_t *lab, int
 
 int vsaogm_decode(vsaogm_map *m, float *heat, void *stream)
 {
+    alloc_scope_begin();
     if (!m || !heat) return set_error(VSAOGM_E_INVAL, "map and heat must not be NULL");
     cudaStream_t st = (cudaStream_t)stream;
     VSA_TRY(decode_raw(m, heat, st));
@@ -478,6 +537,7 @@ int vsaogm_decode(vsaogm_map *m, float *heat, void *stream)
 int vsaogm_entropy(vsaogm_map *m, const float *heat, float *occ, float *ogm, uint8_t *cls,
                    void *stream)
 {
+    alloc_scope_begin();
     if (!m || !heat || !occ) return set_error(VSAOGM_E_INVAL, "map, heat and occ must not be NULL");
     return entropy(m, heat, full_region(m), full_region(m), false, occ, ogm, cls,
                    (cudaStream_t)stream);
@@ -485,6 +545,7 @@ int vsaogm_entropy(vsaogm_map *m, const float *heat, float *occ, float *ogm, uin
 
 int vsaogm_query(vsaogm_map *m, float *heat, float *occ, float *ogm, uint8_t *cls, void *stream)
 {
+    alloc_scope_begin();
     if (!m || !heat || !occ) return set_error(VSAOGM_E_INVAL, "map, heat and occ must not be NULL");
     cudaStream_t st = (cudaStream_t)stream;
     VSA_TRY(decode_raw(m, heat, st));
@@ -507,6 +568,7 @@ int vsaogm_window_scratch(const vsaogm_map *m, int32_t x0, int32_t y0, int32_t w
 int vsaogm_query_window(vsaogm_map *m, int32_t x0, int32_t y0, int32_t w, int32_t h, float *heat,
                         float *occ, float *ogm, uint8_t *cls, void *stream)
 {
+    alloc_scope_begin();
     int64_t need;
     VSA_TRY(vsaogm_window_scratch(m, x0, y0, w, h, &need));
     if (!heat || !occ) return set_error(VSAOGM_E_INVAL, "heat and occ must not be NULL");
@@ -522,6 +584,7 @@ int vsaogm_query_window(vsaogm_map *m, int32_t x0, int32_t y0, int32_t w, int32_
 int vsaogm_update_query_host(vsaogm_map *m, const float *xy_host, const uint8_t *lab_host,
                              int64_t n, float *occ_host, void *stream)
 {
+    alloc_scope_begin();
     if (!m || !occ_host) return set_error(VSAOGM_E_INVAL, "map and occ_host must not be NULL");
     if (n < 0 || (n > 0 && (!xy_host || !lab_host)))
         return set_error(VSAOGM_E_INVAL, "bad point arguments");
@@ -549,6 +612,7 @@ int vsaogm_update_query_host(vsaogm_map *m, const float *xy_host, const uint8_t 
 
 int vsaogm_reserve(vsaogm_map *m, int64_t max_points)
 {
+    alloc_scope_begin();
     if (!m) return set_error(VSAOGM_E_INVAL, "map is NULL");
     if (max_points < 0) return set_error(VSAOGM_E_INVAL, "max_points must be >= 0");
     VSA_TRY(reserve_encode(m, max_points));

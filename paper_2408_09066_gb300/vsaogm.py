@@ -72,6 +72,7 @@ _SIGNATURES = {
     "vsaogm_set_timing": (ctypes.c_int, [_V, ctypes.c_int]),
     "vsaogm_stage_times": (ctypes.c_int, [_V, _V, _V, ctypes.c_int]),
     "vsaogm_last_error": (ctypes.c_char_p, []),
+    "vsaogm_device_bytes": (ctypes.c_int, [_V]),
     "vsaogm_batch_create": (ctypes.c_int, [_V, ctypes.c_int32, _V]),
     "vsaogm_batch_destroy": (ctypes.c_int, [_V]),
     "vsaogm_batch_step": (ctypes.c_int, [_V, _V, _V, _V, _V, _V, _V, ctypes.c_int32, _V]),
@@ -103,6 +104,13 @@ def lib():
 def _check(rc: int):
     if rc != OK:
         raise VsaogmError(rc, lib().vsaogm_last_error().decode())
+
+
+def device_bytes() -> int:
+    """Device memory the library holds right now (vsaogm_device_bytes)."""
+    v = ctypes.c_int64()
+    _check(lib().vsaogm_device_bytes(ctypes.byref(v)))
+    return int(v.value)
 
 
 def default_config(**kw) -> Config:
