@@ -75,6 +75,10 @@ extern "C" {
 #define VSAOGM_FLAG_CHECKED 1u /* encode synchronises and reports rejected points */
 #define VSAOGM_FLAG_ATOMIC 2u  /* bundle with atomics (no partial-sum scratch,
                                   result not bitwise reproducible)             */
+#define VSAOGM_FLAG_WINDOW_MAP_MAX 4u /* window queries normalise by the maxima of
+                                  the whole map (Eq. non-linearities, Fig. 2E),
+                                  so a window equals the same cells of
+                                  vsaogm_query; see vsaogm_query_window     */
 
 /* Map parameters (Sec. III-B2 Initialization, Sec. III-B3 tiling, Table of
  * VSA-OGM parameters).  Memory per map: 2 * tiles_x * tiles_y * D * 8 bytes. */
@@ -205,6 +209,14 @@ int vsaogm_query(vsaogm_map *map, float *heat_dev, float *occ_dev, float *ogm_de
  * clipped to the map, so every window cell sees its whole disk; the maximum of
  * Eq. non-linearities is taken over that region (a local query normalises by
  * what it decodes; for the whole map this equals vsaogm_query).
+ * With VSAOGM_FLAG_WINDOW_MAP_MAX the maximum is the whole map's, as the
+ * paper defines it, and the window's outputs equal the same cells of
+ * vsaogm_query: the whole map is decoded into library-owned scratch (float
+ * [2][H][W], grown on first use or by vsaogm_reserve) whenever the memories
+ * have changed since the last such decode (every call that writes them counts
+ * as a change), and the window's entropy reads from it; heat_dev still
+ * receives P of the region.  Calls on the map must then be ordered on one
+ * stream, as for every call.
  * heat_dev: caller scratch of vsaogm_window_scratch() floats (receives P of
  * the region); occ_dev (float [h][w], row stride w); ogm_dev, cls_dev nullable
  * [h][w].  Errors: E_INVAL (window not inside the map, NULL), E_CUDA.       */

@@ -347,6 +347,13 @@ void drop_graph(vsaogm_batch *b)
     b->graph = nullptr;
 }
 
+// A step writes every map's memories (window queries that normalise by the
+// whole map must decode it again).
+void bump_generations(vsaogm_batch *b)
+{
+    for (vsaogm_map *m : b->maps) ++m->mem_gen;
+}
+
 }  // namespace
 
 extern "C" {
@@ -423,6 +430,7 @@ int vsaogm_batch_step(vsaogm_batch *b, const float *const *xy, const uint8_t *co
     alloc_scope_begin();
     int rc = check_step_args(b, xy, lab, n, heat, occ);
     if (rc) return rc;
+    bump_generations(b);
     const size_t sig = scratch_signature(b);
     rc = run_step(b, xy, lab, n, heat, occ, ogm, reset, (cudaStream_t)stream);
     if (b->exec && scratch_signature(b) != sig) drop_graph(b);
@@ -436,6 +444,7 @@ int vsaogm_batch_capture(vsaogm_batch *b, const float *const *xy, const uint8_t 
     alloc_scope_begin();
     int rc = check_step_args(b, xy, lab, n, heat, occ);
     if (rc) return rc;
+    bump_generations(b);
     cudaStream_t st = (cudaStream_t)stream;
     if (!st) return set_error(VSAOGM_E_INVAL, "capture needs a non-default stream");
     for (vsaogm_map *m : b->maps)
@@ -468,6 +477,7 @@ int vsaogm_batch_replay(vsaogm_batch *b, void *stream)
 {
     if (!b) return set_error(VSAOGM_E_INVAL, "batch is NULL");
     if (!b->exec) return set_error(VSAOGM_E_INVAL, "no captured step: call vsaogm_batch_capture");
+    bump_generations(b);
     cudaError_t e = cudaGraphLaunch(b->exec, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_error(e, "batch replay");
     for (int s = 0; s < VSAOGM_N_STAGES; ++s) b->launches[s] += b->graph_launches[s];
@@ -481,6 +491,7 @@ int vsaogm_batch_autotune(vsaogm_batch *b, const float *const *xy, const uint8_t
     alloc_scope_begin();
     int rc = check_step_args(b, xy, lab, n, heat, occ);
     if (rc) return rc;
+    bump_generations(b);
     drop_graph(b);  // the candidates grow and move the scratch a captured step uses
     const bool timing = b->timing;
     b->timing = false;  // candidates are timed here, not in the stage record

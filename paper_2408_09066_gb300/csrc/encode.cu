@@ -1444,6 +1444,7 @@ extern "C" int vsaogm_encode_bundle_noalloc(vsaogm_map *m, const float *xy, cons
     if (!m) return set_error(VSAOGM_E_INVAL, "map is NULL");
     if (n < 0) return set_error(VSAOGM_E_INVAL, "n must be >= 0");
     if (n == 0) return VSAOGM_OK;
+    ++m->mem_gen;
     if (n > kNoAllocMaxPoints)
         return set_error(VSAOGM_E_INVAL, "encode_noalloc: n = %lld exceeds the maximum of %d points",
                          (long long)n, kNoAllocMaxPoints);

@@ -189,7 +189,10 @@ struct BatchDecodeMap {
     int *status;
     int D, k_per_split, W, H, tiles_x;
     float u_scale;
-    uint64_t debug_wait_ns;  // the failure-test wait limit (0: off)
+    uint64_t debug_wait_ns;
+    // generation of the memories (bumped by every call that writes them) and
+    // the generation whose whole-map P ws.map_heat holds (~0: none)
+    uint64_t mem_gen, map_heat_gen;  // the failure-test wait limit (0: off)
 };
 struct BatchDecodeTable {
     int n_maps;
@@ -243,6 +246,7 @@ struct Scratch {
     DevBuf stage_heat;   // float [2][H][W]
     DevBuf stage_occ;    // float [H][W]
     DevBuf dec_partial;  // float [slices][2][H][W]: tensor-core decode partial maps
+    DevBuf map_heat;     // float [2][H][W]: P of the whole map for map-max window queries
 };
 
 // CUDA-event timing of the stages of each call (tracing) and launch counts.
@@ -285,6 +289,9 @@ struct vsaogm_map {
     // decode's pipeline waits give up after this many nanoseconds and its
     // loader warp first stalls for four times as long, so that they do
     uint64_t debug_wait_ns;
+    // generation of the memories (bumped by every call that writes them) and
+    // the generation whose whole-map P ws.map_heat holds (~0: none)
+    uint64_t mem_gen, map_heat_gen;
     // bundling patches: [0] coarse (phases below 32 turns), [1] fine (below 4
     // turns); device tables of patch centres below
     vsaogm_impl::PatchDev patches[2];

@@ -52,15 +52,37 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
     return ok != 0;
 }
 
+// The same test, but a thread whose phase is not complete is suspended until
+// it completes or about `hint_ns` nanoseconds pass, so that waiting warps do
+// not take issue slots from the working ones.
+__device__ __forceinline__ bool mbar_try_wait_sleep(uint64_t *bar, uint32_t parity,
+                                                    uint32_t hint_ns)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity), "r"(hint_ns)
+        : "memory");
+    return ok != 0;
+}
+
 // Waits for the phase with the given parity to complete; gives up after
 // `limit_ns` nanoseconds (returns false) so that no wait can hang the GPU.
+// Between tests the thread sleeps in the barrier (at most 10 us at a time,
+// and never past the limit).
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, uint64_t limit_ns)
 {
     if (mbar_try_wait(bar, parity)) return true;
     const uint64_t t0 = global_ns();
     for (uint32_t it = 0; it < (1u << 30); ++it) {
-        if (mbar_try_wait(bar, parity)) return true;
-        if ((it & 63) == 0 && global_ns() - t0 > limit_ns) return false;
+        const uint64_t spent = global_ns() - t0;
+        if (spent > limit_ns) return false;
+        const uint64_t left = limit_ns - spent;
+        if (mbar_try_wait_sleep(bar, parity, left < 10000u ? (uint32_t)left : 10000u))
+            return true;
     }
     return false;
 }

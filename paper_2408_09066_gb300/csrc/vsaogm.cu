@@ -148,7 +148,7 @@ void free_scratch(Scratch &ws)
 {
     DevBuf *bufs[] = {&ws.blk_hist, &ws.seg_meta,  &ws.chunks,    &ws.sorted,
                       &ws.partial,  &ws.stage_xy,  &ws.stage_lab, &ws.stage_heat,
-                      &ws.stage_occ, &ws.dec_partial};
+                      &ws.stage_occ, &ws.dec_partial, &ws.map_heat};
     for (DevBuf *b : bufs) {
         if (b->ptr) dev_free(b->ptr);
         b->ptr = nullptr;
@@ -222,7 +222,7 @@ int validate(const vsaogm_config *c)
     if (c->decode_prec != VSAOGM_DECODE_FP32 && c->decode_prec != VSAOGM_DECODE_BF16X3 &&
         c->decode_prec != VSAOGM_DECODE_FP16X3 && c->decode_prec != VSAOGM_DECODE_FP8X3)
         return set_error(VSAOGM_E_INVAL, "unknown decode_prec %d", c->decode_prec);
-    if (c->flags & ~(VSAOGM_FLAG_CHECKED | VSAOGM_FLAG_ATOMIC))
+    if (c->flags & ~(VSAOGM_FLAG_CHECKED | VSAOGM_FLAG_ATOMIC | VSAOGM_FLAG_WINDOW_MAP_MAX))
         return set_error(VSAOGM_E_INVAL, "unknown flags 0x%x", c->flags);
     if ((c->decode_mode & ~(VSAOGM_MODE_NO_NORM | VSAOGM_MODE_NO_SQUARE | VSAOGM_ACT_MASK)) ||
         (c->decode_mode & VSAOGM_ACT_MASK) > VSAOGM_ACT_NONE)
@@ -391,6 +391,8 @@ int vsaogm_create(const vsaogm_config *cfg, vsaogm_map **out)
             m->encode_poly_warps = std::max(-1, std::min(8, atoi(v)));
         // failure test of the bounded waits (see vsaogm_status)
         m->debug_wait_ns = 0;
+        m->mem_gen = 0;
+        m->map_heat_gen = ~0ull;
         if (const char *v = getenv("VSAOGM_DEBUG_WAIT_NS"))
             m->debug_wait_ns = (uint64_t)std::max(0LL, std::min(1000000000LL, atoll(v)));
         std::vector<float> nu(m->host_nu, m->host_nu + 2 * (size_t)D);
@@ -490,6 +492,7 @@ int vsaogm_destroy(vsaogm_map *m)
 int vsaogm_reset(vsaogm_map *m, void *stream)
 {
     if (!m) return set_error(VSAOGM_E_INVAL, "map is NULL");
+    ++m->mem_gen;
     cudaStream_t st = (cudaStream_t)stream;
     VSA_CUDA(cudaMemsetAsync(m->omega, 0, sizeof(float2) * (size_t)m->S * m->cfg.D, st), "reset");
     VSA_CUDA(cudaMemsetAsync(m->rejected, 0, sizeof(unsigned long long), st), "reset");
@@ -501,6 +504,7 @@ int vsaogm_encode_bundle(vsaogm_map *m, const float *xy, const uint8_t *lab, int
 {
     alloc_scope_begin();
     if (!m) return set_error(VSAOGM_E_INVAL, "map is NULL");
+    ++m->mem_gen;
     if (n < 0) return set_error(VSAOGM_E_INVAL, "n must be >= 0");
     if (n == 0) return VSAOGM_OK;
     if (!xy || !lab) return set_error(VSAOGM_E_INVAL, "xy and labels must not be NULL");
@@ -577,8 +581,26 @@ int vsaogm_query_window(vsaogm_map *m, int32_t x0, int32_t y0, int32_t w, int32_
     const Region r{std::max(0, x0 - R), std::max(0, y0 - R), std::min(m->cfg.grid_w, x0 + w + R),
                    std::min(m->cfg.grid_h, y0 + h + R)};
     cudaStream_t st = (cudaStream_t)stream;
-    VSA_TRY(decode_region(m, r, heat, st));
-    return entropy(m, heat, r, win, true, occ, ogm, cls, st);
+    if (!(m->cfg.flags & VSAOGM_FLAG_WINDOW_MAP_MAX)) {
+        VSA_TRY(decode_region(m, r, heat, st));
+        return entropy(m, heat, r, win, true, occ, ogm, cls, st);
+    }
+    // the whole map's P and maxima (Eq. non-linearities over the map), decoded
+    // again only when the memories have changed since
+    const size_t W = m->cfg.grid_w, H = m->cfg.grid_h;
+    VSA_TRY(ensure(m->ws.map_heat, sizeof(float) * 2 * W * H));
+    float *mh = (float *)m->ws.map_heat.ptr;
+    if (m->map_heat_gen != m->mem_gen) {
+        m->map_heat_gen = ~0ull;
+        VSA_TRY(decode_raw(m, mh, st));
+        m->map_heat_gen = m->mem_gen;
+    }
+    for (int c = 0; c < 2; ++c)
+        VSA_CUDA(cudaMemcpy2DAsync(heat + (size_t)c * r.w() * r.h(), sizeof(float) * r.w(),
+                                   mh + c * W * H + (size_t)r.y0 * W + r.x0, sizeof(float) * W,
+                                   sizeof(float) * r.w(), r.h(), cudaMemcpyDeviceToDevice, st),
+                 "query_window");
+    return entropy(m, mh, full_region(m), win, true, occ, ogm, cls, st);
 }
 
 int vsaogm_update_query_host(vsaogm_map *m, const float *xy_host, const uint8_t *lab_host,
@@ -617,6 +639,9 @@ int vsaogm_reserve(vsaogm_map *m, int64_t max_points)
     if (max_points < 0) return set_error(VSAOGM_E_INVAL, "max_points must be >= 0");
     VSA_TRY(reserve_encode(m, max_points));
     VSA_TRY(reserve_decode(m));
+    if (m->cfg.flags & VSAOGM_FLAG_WINDOW_MAP_MAX)
+        VSA_TRY(ensure(m->ws.map_heat,
+                       sizeof(float) * 2 * (size_t)m->cfg.grid_w * m->cfg.grid_h));
     VSA_CUDA(cudaDeviceSynchronize(), "reserve");
     return VSAOGM_OK;
 }
@@ -643,6 +668,7 @@ int vsaogm_get_memory(const vsaogm_map *m, float *omega, void *stream)
 int vsaogm_set_memory(vsaogm_map *m, const float *omega, void *stream)
 {
     if (!m || !omega) return set_error(VSAOGM_E_INVAL, "map and omega must not be NULL");
+    ++m->mem_gen;
     VSA_CUDA(cudaMemcpyAsync(m->omega, omega, sizeof(float2) * (size_t)m->S * m->cfg.D,
                              cudaMemcpyDeviceToDevice, (cudaStream_t)stream), "set_memory");
     return VSAOGM_OK;
@@ -661,6 +687,7 @@ int vsaogm_fuse(vsaogm_map *dst, const vsaogm_map *src, void *stream)
                          "fusion needs the same axis vectors (D, seed, l) and the same tiling");
     if (dst->device != src->device) return set_error(VSAOGM_E_INVAL, "maps on different devices");
     if (dst == src) return set_error(VSAOGM_E_INVAL, "cannot fuse a map into itself");
+    ++dst->mem_gen;
     return add_memories(dst->omega, src->omega, (int64_t)dst->S * a.D, (cudaStream_t)stream);
 }
 

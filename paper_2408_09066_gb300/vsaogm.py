@@ -20,7 +20,7 @@ LIB_PATH = os.path.join(_HERE, "libvsaogm_checked.so" if os.environ.get("VSAOGM_
 STAGES = ("sort", "encode", "reduce", "norms", "decode", "nonlinear", "entropy")
 OK, E_INVAL, E_NOMEM, E_CUDA, E_TIMEOUT, E_DATA = 0, -1, -2, -3, -4, -5
 DECODE_FP32, DECODE_BF16X3, DECODE_FP16X3, DECODE_FP8X3 = 0, 1, 2, 3
-FLAG_CHECKED, FLAG_ATOMIC = 1, 2
+FLAG_CHECKED, FLAG_ATOMIC, FLAG_WINDOW_MAP_MAX = 1, 2, 4
 MODE_NO_NORM, MODE_NO_SQUARE = 1, 2
 ACT_ENTROPY, ACT_RELU, ACT_TANH, ACT_SIGMOID, ACT_NONE = 0, 16, 32, 48, 64
 MAX_BATCH = 64

@@ -80,3 +80,54 @@ def test_window_outside_the_map_is_rejected():
             with pytest.raises(V.VsaogmError) as ei:
                 m.window_scratch(*bad)
             assert ei.value.code == V.E_INVAL
+
+
+@pytest.mark.parametrize("prec", [V.DECODE_FP32, V.DECODE_BF16X3])
+def test_map_max_windows_equal_the_map_query(prec):
+    """With VSAOGM_FLAG_WINDOW_MAP_MAX a window query normalises by the whole
+    map's maxima (Eq. non-linearities, Fig. 2E): its outputs are those of the
+    same cells of the map query and match the oracle's whole-map pipeline
+    there; after more points are bundled the next window query decodes the map
+    again.  The window's P is the map query's P bit for bit; its entropy sums
+    the same disks, but as differences of running sums that start at the
+    window's own blocks, so Pr differs from the map query's only by float
+    rounding (held to 1e-5)."""
+    import torch
+    wl = synth.small_scan(seed=80)
+    more = synth.small_scan(seed=81)
+    cfg = config_for(wl, tiles_x=2, tiles_y=2, decode_prec=prec, flags=V.FLAG_WINDOW_MAP_MAX)
+    dev = torch.device("cuda")
+    g = oracle_grid(cfg)
+    nx, ny = oracle.draw_nu(cfg.seed, cfg.D, float(np.float32(cfg.length_scale)))
+    with V.Map(cfg) as m, V.Map(config_for(wl, tiles_x=2, tiles_y=2, decode_prec=prec)) as full:
+        pts = []
+        for w in (wl, more):
+            xy, lab = torch.from_numpy(w.xy).to(dev), torch.from_numpy(w.labels).to(dev)
+            m.encode_bundle(xy, lab)
+            full.encode_bundle(xy, lab)
+            pts.append(w)
+            heat = torch.empty((2, wl.H, wl.W), dtype=torch.float32, device=dev)
+            occ = torch.empty((wl.H, wl.W), dtype=torch.float32, device=dev)
+            ogm = torch.empty((wl.H, wl.W), dtype=torch.float32, device=dev)
+            full.query(heat, occ, ogm)
+            ref = oracle.pipeline(g, nx, ny, np.concatenate([p.xy for p in pts]),
+                                  np.concatenate([p.labels for p in pts]), cfg.r_occ,
+                                  cfg.r_emp, cfg.rho)
+            for (x0, y0, ww, hh) in WINDOWS:
+                wheat = torch.empty(m.window_scratch(x0, y0, ww, hh), dtype=torch.float32,
+                                    device=dev)
+                wocc = torch.empty((hh, ww), dtype=torch.float32, device=dev)
+                wogm = torch.empty((hh, ww), dtype=torch.float32, device=dev)
+                m.query_window(x0, y0, ww, hh, wheat, wocc, wogm)
+                torch.cuda.synchronize()
+                m.status()
+                sl = (slice(y0, y0 + hh), slice(x0, x0 + ww))
+                assert (wocc - occ[sl]).abs().max().item() <= 1e-5, (x0, y0, ww, hh)
+                assert (wogm - ogm[sl]).abs().max().item() <= 2e-5
+                assert np.abs(wocc.cpu().numpy() - ref["pr1"][sl]).max() <= TOL_PR
+                # heat receives P of the window's region, as in the local mode
+                R = max(cfg.r_occ, cfg.r_emp)
+                rx0, ry0 = max(0, x0 - R), max(0, y0 - R)
+                rx1, ry1 = min(wl.W, x0 + ww + R), min(wl.H, y0 + hh + R)
+                P = wheat[:2 * (rx1 - rx0) * (ry1 - ry0)].view(2, ry1 - ry0, rx1 - rx0)
+                assert torch.equal(P, heat[:, ry0:ry1, rx0:rx1])
