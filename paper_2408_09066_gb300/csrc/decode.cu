@@ -336,7 +336,7 @@ int decode_region(vsaogm_map *m, Region r, float *heat, cudaStream_t st)
 
 // Grows the decode scratch so that no map or window query allocates.  A query
 // of a region with nb blocks uses at most (slots / nb) frequency slices, and the
-// blocks cover the region, so slices x cells <= slots x block cells: 152 x 128^2
+// blocks cover the region, so slices x cells <= slots x block cells: 152 x 256 x 128
 // for the tensor-core decode, 456 x 64^2 for the SIMT one; the tensor-core
 // decode's minimum of ceil(D / kTcMaxKPerSplit) slices of the whole map (or
 // one slice) bounds the rest.
@@ -345,7 +345,7 @@ int reserve_decode(vsaogm_map *m)
     const size_t cells = (size_t)m->cfg.grid_w * m->cfg.grid_h;
     const size_t tc_slices = (size_t)(m->cfg.D + kTcMaxKPerSplit - 1) / kTcMaxKPerSplit;
     size_t need = std::max<size_t>(
-        {(size_t)152 * 128 * 128, (size_t)3 * 152 * kBI * kBJ, tc_slices * cells});
+        {(size_t)152 * 256 * 128, (size_t)3 * 152 * kBI * kBJ, tc_slices * cells});
     return ensure(m->ws.dec_partial, sizeof(float) * 2 * need);
 }
 

@@ -55,27 +55,28 @@ using namespace sm100;
 
 enum TcPrec { kPrecBF16 = 0, kPrecFP16 = 1, kPrecFP8 = 2 };
 
-constexpr int kM = 128;            // rows per block (MMA M)
-constexpr int kRowBytes = 128;
+constexpr int kM = 128;            // rows per row block (MMA M)
+constexpr int kRowBytes = 64;      // bytes per operand row and stage (64-byte swizzle)
+constexpr int kWords = kRowBytes / 4;  // 4-byte words per operand row
 constexpr int kProducers = 512;    // 16 warps generate the operands ...
 constexpr int kWarps = kProducers / 32;
 constexpr int kMmaWarp = kWarps;       // ... one issues the MMAs ...
 constexpr int kLoadWarp = kWarps + 1;  // ... and one stages each stage's inputs
 constexpr int kThreads = kProducers + 64;
-constexpr int kQ = kM / kWarps;    // rows (and columns) per thread
-constexpr int kATile = kM * kRowBytes;          // one A operand tile (16 KB)
-constexpr int kAStage = 4 * kATile;             // 2 classes x hi/lo (64 KB)
-constexpr int kTmemCols = 256;                  // class psi accumulates at column 128 psi
+constexpr int kStep = 32;          // cells between a thread's rows (and columns)
+constexpr int kMaxRowBlocks = 2;   // 128-row blocks per CTA
+constexpr int kMaxN = 256;         // MMA N of a one-row-block CTA (128 with two)
+constexpr int kATile = kM * kRowBytes;           // one A operand tile (8 KB)
+constexpr int kAArea = kMaxRowBlocks * 4 * kATile;  // row blocks x classes x hi/lo (64 KB)
+constexpr int kBTile = kMaxN * kRowBytes;        // one B operand tile (16 KB)
+constexpr int kBArea = 2 * kBTile;               // hi and lo (32 KB)
+constexpr int kTmemCols = 512;                   // accumulators: row blocks x classes x N
 constexpr uint64_t kWaitNs = 2000000000ull;     // 2 s: far above any legitimate wait
 
-// Frequencies per stage (one 128-byte operand row).
-__host__ __device__ constexpr int stage_freqs(int prec) { return prec == kPrecFP8 ? 64 : 32; }
-// Tile rows one block may span: kMaxBlockTiles, fewer for FP8, whose staged
-// memories per tile row are twice as long (two stages must fit in shared memory).
-__host__ __device__ constexpr int max_block_tiles(int prec)
-{
-    return prec == kPrecFP8 ? 14 : kMaxBlockTiles;
-}
+// Frequencies per stage (one 64-byte operand row): 16 in the 16-bit formats
+// (one complex value per word), 32 in FP8 (two per word).
+__host__ __device__ constexpr int stage_freqs(int prec) { return prec == kPrecFP8 ? 32 : 16; }
+__host__ __device__ constexpr int max_block_tiles(int) { return kMaxBlockTiles; }
 // Bytes of the aux area of one stage: the staged memories (tile row, class,
 // frequency) float2, then per frequency (nu_x, nu_y) and the x and y step
 // phasors, float2 each; rounded up so that every stage starts 1024-aligned.
@@ -83,15 +84,14 @@ __host__ __device__ constexpr int aux_bytes(int prec)
 {
     return ((max_block_tiles(prec) * 2 + 3) * stage_freqs(prec) * 8 + 1023) / 1024 * 1024;
 }
-// Bytes of one pipeline stage for MMA width N: A (both classes, hi and lo),
-// B (hi and lo) and the aux area.
-__host__ __device__ constexpr int stage_size(int prec, int N)
-{
-    return kAStage + 2 * N * kRowBytes + aux_bytes(prec);
-}
-__host__ __device__ constexpr size_t smem_max(int prec) { return 1024 + 2 * (size_t)stage_size(prec, kM); }
+// Bytes of one pipeline stage: A (row blocks, classes, hi and lo), B (hi and
+// lo) and the aux area.
+__host__ __device__ constexpr int stage_size(int prec) { return kAArea + kBArea + aux_bytes(prec); }
+__host__ __device__ constexpr size_t smem_max(int prec) { return 1024 + 2 * (size_t)stage_size(prec); }
 static_assert(smem_max(kPrecFP8) <= 232448 - 256, "two FP8 stages fit in shared memory");
 static_assert(smem_max(kPrecBF16) <= 232448 - 256, "two 16-bit stages fit in shared memory");
+// epilogue staging: per producer warp 32 rows x 16 columns (pitch 17)
+static_assert(kWarps * 32 * 17 * 4 <= 2 * kAArea, "epilogue staging fits the A areas");
 
 __device__ __forceinline__ float2 phasor(float nu, float d)
 {
@@ -214,27 +214,32 @@ __host__ __device__ constexpr uint32_t idesc_of(int N)
 // stages each stage's inputs.  The block's columns lie in tile column b.tile;
 // its rows may cross tile rows (at most max_block_tiles(P) of them), each row
 // using the memories of its own tile: row j of the A operand is U_psi of tile
-// (row_tile[j], b.tile).
+// (row_tile[j], b.tile).  A block has rb = 1 or 2 row blocks of up to 128
+// rows (rows j0 .. j0 + 127 and j0 + 128 .. j1 - 1) and N <= 256 / rb columns:
+// the tensor memory holds rb x 2 classes accumulators of N columns, and the B
+// operand (the x phasors) is shared by all of them.
 //
 // Hand-offs, all through mbarriers (no CTA-wide barrier inside the loop):
-//  * the loader warp writes stage s's inputs (the memories of the block's
-//    tiles scaled by 1 / norm, the frequencies and the 16-cell step phasors)
-//    into the aux area of buffer buf = s & 1 and each of its lanes arrives
-//    on aux_full[buf];
-//    it refills buf for stage s + 2 once every producer warp has arrived on
-//    full_bar[buf] for stage s (they read the aux area before arriving);
+//  * the loader warp copies stage s's inputs (the memories of the block's
+//    tiles, the frequencies and the 32-cell step phasors) into the aux area of
+//    buffer buf = s & 1 with per-thread async copies that land on
+//    aux_full[buf]; it refills buf for stage s + 2 once every producer warp
+//    has arrived on full_bar[buf] for stage s (they read the aux area before
+//    arriving);
 //  * producers wait on aux_full[buf] and, from stage 2 on, on empty_bar[buf]
 //    (the tensor cores have finished reading buf), generate stage s and
 //    arrive on full_bar[buf] (one arrival per warp, after a proxy fence);
-//  * the MMA warp waits on full_bar[buf], issues the stage's 24 MMAs and
+//  * the MMA warp waits on full_bar[buf], issues the stage's MMAs and
 //    commits them to empty_bar[buf].
 // Producer warps therefore drift apart by up to a stage instead of meeting
 // at a barrier every stage.  Every wait is bounded; after a time-out the CTA
 // stops waiting, records VSAOGM_E_TIMEOUT, drains its MMAs and frees its
 // tensor memory.
 //
-// Producer lane l owns frequencies FPL l .. FPL l + FPL - 1 of the stage (FPL =
-// 1 for 16-bit operands, 2 for FP8): one 4-byte word per operand row.  Each
+// Producer thread (warp w, lane l) owns word l mod 16 of every operand row it
+// writes (frequencies FPL (l mod 16) .. + FPL - 1 of the stage, FPL = 1 for
+// 16-bit operands, 2 for FP8), and the rows and columns 2 w + l / 16 + 32 q:
+// their 64-byte swizzle phase ((row / 2) mod 4) is w mod 4 for every q.  Each
 // thread carries the two classes' operand values of a row as packed pairs,
 // (Re U_0, Re U_1) and (-Im U_0, -Im U_1), so one packed multiply-add
 // advances both classes.
@@ -243,12 +248,12 @@ __device__ __forceinline__ void decode_tc_body(
     const DecodeBlock b, const int split, const float2 *__restrict__ omega,
     const float *__restrict__ inv_norm, const float *__restrict__ nu, int D, int tiles_x,
     const int *__restrict__ row_tile, OutGeom og, const float *__restrict__ col_off,
-    const float *__restrict__ row_off, const float2 *__restrict__ rot, int k_per_split, int N,
+    const float *__restrict__ row_off, const float2 *__restrict__ rot, int k_per_split,
     float u_scale, float *__restrict__ partial, int *__restrict__ status,
     uint64_t debug_wait_ns)
 {
     constexpr int KS = stage_freqs(P);       // frequencies per stage
-    constexpr int FPL = KS / 32;             // frequencies per producer lane
+    constexpr int FPL = KS / kWords;         // frequencies per operand word
     extern __shared__ uint8_t smem_raw[];
     __shared__ uint64_t full_bar[2], empty_bar[2], aux_full[2], done_bar, never_bar;
     __shared__ float s_scale[2 * kMaxBlockTiles];  // 1 / norm x u_scale per (tile row, class)
@@ -256,7 +261,7 @@ __device__ __forceinline__ void decode_tc_body(
     __shared__ int abort_s;
     volatile int *abort_v = &abort_s;
     uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    const int stage_bytes = stage_size(P, N);
+    constexpr int stage_bytes = stage_size(P);
     // limit of the pipeline's waits: 2 s, or the failure-test knob (the drain
     // before the tensor memory is freed always keeps the 2 s limit)
     const uint64_t wait_ns = debug_wait_ns ? debug_wait_ns : kWaitNs;
@@ -266,9 +271,13 @@ __device__ __forceinline__ void decode_tc_body(
     const int k_end = min(D, k_begin + k_per_split);
     const int n_stages = (k_end - k_begin + KS - 1) / KS;
     const int ni = b.i1 - b.i0, nj = b.j1 - b.j0;
+    const int rb = nj > kM ? 2 : 1;               // row blocks
+    const int N = (ni + 15) / 16 * 16;            // MMA N
+    const int acc_cols = kTmemCols / (2 * rb);    // tensor-memory columns per accumulator
     const int by0 = row_tile[b.j0];
     const int nt = row_tile[b.j1 - 1] - by0 + 1;  // tile rows of the block
-    if (nt < 1 || nt > max_block_tiles(P) || N > kM || N < 16 || (N & 15)) {
+    if (nt < 1 || nt > max_block_tiles(P) || ni < 1 || nj < 1 || nj > kMaxRowBlocks * kM ||
+        N > kTmemCols / (2 * rb)) {
         // the host never builds such a block; refuse it rather than index past smem
         if (tid == 0) atomicExch(status, VSAOGM_E_INVAL);
         return;
@@ -282,7 +291,7 @@ __device__ __forceinline__ void decode_tc_body(
         for (int q = 0; q < 2; ++q) {
             mbar_init(&full_bar[q], kWarps);
             mbar_init(&empty_bar[q], 1);
-            mbar_init(&aux_full[q], 32);  // every loader lane arrives after its stores
+            mbar_init(&aux_full[q], 32);  // every loader lane arrives once its copies land
         }
         mbar_init(&done_bar, 1);
         mbar_init(&never_bar, 1);  // nothing arrives on it (failure test only)
@@ -300,30 +309,34 @@ __device__ __forceinline__ void decode_tc_body(
 
     if (warp == kMmaWarp) {
         // ------------------------------------------------------ MMA warp
+        // A area: tiles [row block][class][hi, lo] of 128 rows; B area: the hi
+        // and the lo tile of N rows.  Descriptors are those of buffer 0; buffer
+        // 1 and each K-step (32 bytes) add their byte offset / 16 to the
+        // start-address field.
         const uint32_t idesc = idesc_of<P>(N);
-        // descriptors of buffer 0; buffer 1 and each K-step (32 bytes) add
-        // their byte offset / 16 to the start-address field
-        const uint32_t base = smem_addr(smem);
-        const uint64_t d_a = desc_k_sw128(base), d_bh = desc_k_sw128(base + kAStage),
-                       d_bl = desc_k_sw128(base + kAStage + N * kRowBytes);
+        const uint64_t d0 = desc_k_sw64(smem_addr(smem));
         for (int s = 0; s < n_stages; ++s) {
             const int buf = s & 1;
             if (!*abort_v && !mbar_wait(&full_bar[buf], (uint32_t)(s >> 1) & 1u, wait_ns))
                 atomicExch(&abort_s, 1);
             tc_fence_after_sync();
             if (lane == 0) {
-                const uint64_t ob = (uint64_t)((buf * stage_bytes) >> 4);
+                const uint64_t ob = d0 + (uint64_t)((buf * stage_bytes) >> 4);
 #pragma unroll
-                for (int kk = 0; kk < 4; ++kk) {
-                    const uint64_t o = ob + (uint64_t)(kk * 2);  // 32 bytes of each row
+                for (int kk = 0; kk < kRowBytes / 32; ++kk) {
+                    const uint64_t o = ob + (uint64_t)(kk * 2);
+                    const uint64_t dbh = o + (uint64_t)(kAArea >> 4);
+                    const uint64_t dbl = dbh + (uint64_t)(kBTile >> 4);
+                    for (int r = 0; r < rb; ++r) {
 #pragma unroll
-                    for (int c = 0; c < 2; ++c) {
-                        const uint64_t dah = d_a + o + (uint64_t)((2 * c) * kATile >> 4);
-                        const uint64_t dal = d_a + o + (uint64_t)((2 * c + 1) * kATile >> 4);
-                        const uint32_t d = tmem + 128u * c;
-                        mma<P>(d, dah, d_bh + o, idesc, (s > 0 || kk > 0) ? 1u : 0u);
-                        mma<P>(d, dah, d_bl + o, idesc, 1u);
-                        mma<P>(d, dal, d_bh + o, idesc, 1u);
+                        for (int c = 0; c < 2; ++c) {
+                            const uint64_t dah = o + (uint64_t)((((r * 2 + c) * 2) * kATile) >> 4);
+                            const uint64_t dal = dah + (uint64_t)(kATile >> 4);
+                            const uint32_t d = tmem + (uint32_t)((2 * r + c) * acc_cols);
+                            mma<P>(d, dah, dbh, idesc, (s > 0 || kk > 0) ? 1u : 0u);
+                            mma<P>(d, dah, dbl, idesc, 1u);
+                            mma<P>(d, dal, dbh, idesc, 1u);
+                        }
                     }
                 }
                 mma_commit(&empty_bar[buf]);
@@ -340,9 +353,8 @@ __device__ __forceinline__ void decode_tc_body(
         // and the step phasors along x and y, float2 [2][KS].  Copied with
         // per-thread async copies that land on aux_full[buf]; frequencies past
         // the slice's end are zero-filled (memories 0, so their U and hence
-        // their products vanish).  Lane l copies frequency l + 32 (i mod FPL)
-        // of memory row i / FPL for i = 0, 1, ...
-        const int n_rows = nt * 2;
+        // their products vanish).
+        const int n_w = nt * 2 * KS;
         // failure test: stall on a barrier nothing arrives at, for four times
         // the pipeline's wait limit, so that the other warps' waits run out
         if (debug_wait_ns) mbar_wait(&never_bar, 0u, 4 * debug_wait_ns);
@@ -353,19 +365,18 @@ __device__ __forceinline__ void decode_tc_body(
             if (s >= 2 && !*abort_v &&
                 !mbar_wait(&full_bar[buf], (uint32_t)((s - 2) >> 1) & 1u, wait_ns))
                 atomicExch(&abort_s, 1);
-            float2 *aw = reinterpret_cast<float2 *>(smem + (size_t)buf * stage_bytes + kAStage +
-                                                    2 * N * kRowBytes);
+            float2 *aw = reinterpret_cast<float2 *>(smem + (size_t)buf * stage_bytes + kAArea +
+                                                    kBArea);
             float2 *af = aw + max_block_tiles(P) * 2 * KS;
             const int k0 = k_begin + s * KS;
-            for (int i = 0; i < n_rows * FPL; ++i) {
-                const int r = i / FPL, kk = lane + 32 * (i % FPL), k = k0 + kk;
+            for (int e = lane; e < n_w; e += 32) {
+                const int r = e / KS, k = k0 + e % KS;
                 const int mem = 2 * ((by0 + (r >> 1)) * tiles_x + b.tile) + (r & 1);
                 const bool in = k < k_end;
-                cp_async<8>(&aw[r * KS + kk], omega + (size_t)mem * D + (in ? k : 0), in);
+                cp_async<8>(&aw[e], omega + (size_t)mem * D + (in ? k : 0), in);
             }
-#pragma unroll
-            for (int j = 0; j < FPL; ++j) {
-                const int kk = lane + 32 * j, k = k0 + kk;
+            for (int kk = lane; kk < KS; kk += 32) {
+                const int k = k0 + kk;
                 const bool in = k < k_end;
                 const int kc = in ? k : 0;
                 cp_async<4>(&af[kk].x, nu + kc, in);
@@ -378,20 +389,24 @@ __device__ __forceinline__ void decode_tc_body(
         cp_async_wait_all();
     } else {
         // ------------------------------------------------------ producers
-        // Fixed per-thread geometry: rows / columns warp + kWarps q, whose
-        // 128-byte swizzle phase (row & 7) is warp & 7.
-        float dy[kQ], dx0;
-        int tl[kQ];  // tile row of each A row, relative to by0
+        const int wd = lane & (kWords - 1);  // word of the operand rows
+        const int r0 = 2 * warp + (lane >> 4);  // first row and first column of the thread
+        // rows r0 + 32 q of the block, q < 4 rb: row block q / 4, row r0 + 32 (q mod 4)
+        float dy[2 * 4];
+        int tl[2 * 4];  // tile row of each A row, relative to by0
 #pragma unroll
-        for (int q = 0; q < kQ; ++q) {
-            const int m = warp + kWarps * q;
-            dy[q] = m < nj ? row_off[b.j0 + m] : 0.f;
-            const int t = m < nj ? row_tile[b.j0 + m] - by0 : 0;
+        for (int q = 0; q < 8; ++q) {
+            const int m = r0 + kStep * q;
+            const bool v = q < 4 * rb && m < nj;
+            dy[q] = v ? row_off[b.j0 + m] : 0.f;
+            const int t = v ? row_tile[b.j0 + m] - by0 : 0;
             tl[q] = VSAOGM_IN_BOUNDS(t >= 0 && t < nt) ? t : 0;  // staged memories exist for [0, nt)
         }
-        dx0 = warp < ni ? col_off[b.i0 + warp] : 0.f;
-        const uint32_t soff = (uint32_t)(warp * kRowBytes +
-                                         ((((lane >> 2) ^ (warp & 7)) << 4) | ((lane & 3) << 2)));
+        const float dx0 = r0 < ni ? col_off[b.i0 + r0] : 0.f;
+        // byte of the thread's word in its first row: 64-byte swizzle phase w mod 4
+        const uint32_t soff = (uint32_t)(r0 * kRowBytes +
+                                         ((((wd >> 2) ^ (warp & 3)) << 4) | ((wd & 3) << 2)));
+        constexpr int kQBytes = kStep * kRowBytes;  // 32 rows further on
         uint32_t phase_bits = 0u;  // bit b: parity to wait for on empty_bar[b]
 
         for (int s = 0; s < n_stages; ++s) {
@@ -404,33 +419,33 @@ __device__ __forceinline__ void decode_tc_body(
             if (!*abort_v && !mbar_wait(&aux_full[buf], (uint32_t)(s >> 1) & 1u, wait_ns))
                 atomicExch(&abort_s, 1);
             uint8_t *st = smem + (size_t)buf * stage_bytes;
-            uint8_t *bh = st + kAStage, *bl = bh + N * kRowBytes;
-            const float2 *sw = reinterpret_cast<const float2 *>(bl + N * kRowBytes);
+            uint8_t *bh = st + kAArea, *bl = bh + kBTile;
+            const float2 *sw = reinterpret_cast<const float2 *>(bl + kBTile);
             const float2 *sf = sw + max_block_tiles(P) * 2 * KS;
             float nux[FPL], nuy[FPL];
             float2 rsx[FPL], rsy[FPL];
 #pragma unroll
             for (int j = 0; j < FPL; ++j) {
-                const float2 f = sf[FPL * lane + j];
+                const float2 f = sf[FPL * wd + j];
                 nux[j] = f.x;
                 nuy[j] = f.y;
-                rsx[j] = sf[KS + FPL * lane + j];
-                rsy[j] = sf[2 * KS + FPL * lane + j];
+                rsx[j] = sf[KS + FPL * wd + j];
+                rsy[j] = sf[2 * KS + FPL * wd + j];
             }
             // No masking below: frequencies past the slice's end have staged
             // memories 0, so their U and hence their products vanish; rows and
             // columns past the block (its MMA padding) are never written out.
             //
-            // B operand: x phasors of the N columns.  Column warp + 16 (q + 1)
-            // is 16 cells right of column warp + 16 q in the same tile, so its
-            // phasor is the previous one times exp(i 2 pi nu_x 16 res).
+            // B operand: x phasors of the N columns.  Column r0 + 32 (q + 1) is
+            // 32 cells right of column r0 + 32 q in the same tile, so its
+            // phasor is the previous one times exp(i 2 pi nu_x 32 res).
             {
                 float2 a[FPL];
 #pragma unroll
                 for (int j = 0; j < FPL; ++j) a[j] = phasor(nux[j], dx0);
 #pragma unroll
-                for (int q = 0; q < kQ; ++q) {
-                    const int n = warp + kWarps * q;
+                for (int q = 0; q < kMaxN / kStep; ++q) {
+                    if (kStep * q >= N) break;  // every column of the warp is past N
 #pragma unroll
                     for (int j = 0; j < FPL; ++j)
                         if (q > 0) a[j] = cmul(a[j], rsx[j]);
@@ -439,18 +454,18 @@ __device__ __forceinline__ void decode_tc_body(
                         split_pair<P>(a[0].x, a[0].y, hi, lo);
                     else
                         split_quad_e4m3(a[0].x, a[0].y, a[FPL - 1].x, a[FPL - 1].y, hi, lo);
-                    if (n < N) {
-                        *reinterpret_cast<uint32_t *>(bh + q * kWarps * kRowBytes + soff) = hi;
-                        *reinterpret_cast<uint32_t *>(bl + q * kWarps * kRowBytes + soff) = lo;
+                    if (r0 + kStep * q < N) {
+                        *reinterpret_cast<uint32_t *>(bh + q * kQBytes + soff) = hi;
+                        *reinterpret_cast<uint32_t *>(bl + q * kQBytes + soff) = lo;
                     }
                 }
             }
             // A operands: (Re U_psi, -Im U_psi) with U_psi = conj(w_hat_psi) x
             // the y phasor, i.e. V_psi = conj(U_psi) = w_hat_psi x conj(phasor),
             // held for both classes as packed pairs X = (Re V_0, Re V_1), Y =
-            // (Im V_0, Im V_1).  Rows step by 16 cells: V times conj(exp(i 2 pi
-            // nu_y 16 res)), except where a row enters the next tile
-            // (warp-uniform): there the phasor and the memories are reloaded.
+            // (Im V_0, Im V_1).  Rows step by 32 cells: V times conj(exp(i 2 pi
+            // nu_y 32 res)), except where a row enters the next tile: there the
+            // phasor and the memories are reloaded.
             {
                 f32x2 X[FPL], Y[FPL], R2[FPL], I2[FPL], NI2[FPL];
 #pragma unroll
@@ -464,8 +479,8 @@ __device__ __forceinline__ void decode_tc_body(
 #pragma unroll
                     for (int j = 0; j < FPL; ++j) {
                         const float2 e = phasor(nuy[j], dy[q]);
-                        const float2 w0 = sw[(2 * tl[q]) * KS + FPL * lane + j];
-                        const float2 w1 = sw[(2 * tl[q] + 1) * KS + FPL * lane + j];
+                        const float2 w0 = sw[(2 * tl[q]) * KS + FPL * wd + j];
+                        const float2 w1 = sw[(2 * tl[q] + 1) * KS + FPL * wd + j];
                         // V = w_hat x conj(e), w_hat = w / norm (x u_scale)
                         X[j] = mul2(pack2(w0.x * e.x + w0.y * e.y, w1.x * e.x + w1.y * e.y), sc);
                         Y[j] = mul2(pack2(w0.y * e.x - w0.x * e.y, w1.y * e.x - w1.x * e.y), sc);
@@ -473,7 +488,8 @@ __device__ __forceinline__ void decode_tc_body(
                 };
                 start_row(0);
 #pragma unroll
-                for (int q = 0; q < kQ; ++q) {
+                for (int q = 0; q < 8; ++q) {
+                    if (q >= 4 * rb) break;
                     if (q > 0) {
                         if (tl[q] != tl[q - 1]) {
                             start_row(q);
@@ -487,7 +503,8 @@ __device__ __forceinline__ void decode_tc_body(
                             }
                         }
                     }
-                    const uint32_t o = q * kWarps * kRowBytes + soff;
+                    // tiles [row block q / 4][class][hi, lo]
+                    uint8_t *ra = st + (q >> 2) * 4 * kATile + (q & 3) * kQBytes + soff;
                     uint32_t h0, l0, h1, l1;
                     if (FPL == 1) {
                         split_classes<P>(X[0], Y[0], h0, l0, h1, l1);
@@ -497,10 +514,10 @@ __device__ __forceinline__ void decode_tc_body(
                         split_quad_e4m3(x0.x, y0.x, x1.x, y1.x, h0, l0);
                         split_quad_e4m3(x0.y, y0.y, x1.y, y1.y, h1, l1);
                     }
-                    *reinterpret_cast<uint32_t *>(st + 0 * kATile + o) = h0;
-                    *reinterpret_cast<uint32_t *>(st + 1 * kATile + o) = l0;
-                    *reinterpret_cast<uint32_t *>(st + 2 * kATile + o) = h1;
-                    *reinterpret_cast<uint32_t *>(st + 3 * kATile + o) = l1;
+                    *reinterpret_cast<uint32_t *>(ra + 0 * kATile) = h0;
+                    *reinterpret_cast<uint32_t *>(ra + 1 * kATile) = l0;
+                    *reinterpret_cast<uint32_t *>(ra + 2 * kATile) = h1;
+                    *reinterpret_cast<uint32_t *>(ra + 3 * kATile) = l1;
                 }
             }
             // hand the stage to the MMA warp
@@ -509,44 +526,46 @@ __device__ __forceinline__ void decode_tc_body(
             if (lane == 0) mbar_arrive(&full_bar[buf]);
         }
     }
-    // epilogue (producers): warp w reads TMEM lanes 32 (w & 3) .. + 31 (its lane
-    // quarter), class (w >> 2) & 1, and one half of the 16-column chunks (w >> 3),
-    // one row per lane; the rows go through shared memory (free once every MMA
-    // has finished) so that each store writes 32 consecutive cells of a row.
-    // Always drain (bounded), even after a time-out: tensor memory is freed below.
+    // epilogue (producers): accumulator a = 2 r + c (row block r, class c)
+    // holds N columns in 16-column chunks; warp w reads tensor-memory lanes
+    // 32 (w mod 4) .. + 31 (its lane quarter: rows 128 r + 32 (w mod 4) + lane)
+    // of every fourth chunk, starting at chunk w / 4.  Each chunk goes through
+    // shared memory (free once every MMA has finished), so that each store
+    // instruction writes two 64-byte row segments.  Always drain (bounded),
+    // even after a time-out: tensor memory is freed below.
     if (!mbar_wait(&done_bar, 0u, kWaitNs)) atomicExch(&abort_s, 1);
     tc_fence_after_sync();
     __syncthreads();
-    if (warp < kWarps) {
-        const int c = (warp >> 2) & 1, lane_base = 32 * (warp & 3), half = warp >> 3;
-        const int m = lane_base + lane;
-        const int nch = N / 16, ch0 = half ? (nch + 1) / 2 : 0, ch1 = half ? nch : (nch + 1) / 2;
-        float *out = partial + (((size_t)split * 2 + c) * og.OH) * og.OW;
-        if (!abort_s && n_stages > 0) {
-            constexpr int kPitch = kM / 2 + 1;  // floats per staged row (half the columns + 1)
-            float *tile = reinterpret_cast<float *>(smem) + (size_t)warp * 32 * kPitch;
-            for (int cc = ch0; cc < ch1; ++cc) {
-                float v[16];
-                tmem_ld_32x32b_x16(tmem + ((uint32_t)lane_base << 16) + 128u * c + cc * 16, v);
+    if (warp < kWarps && !abort_s) {
+        const int lq = warp & 3, nch = N / 16;
+        float *tile = reinterpret_cast<float *>(smem) + (size_t)warp * 32 * 17;
+        for (int t = warp >> 2; t < 2 * rb * nch; t += 4) {
+            const int a = t / nch, cc = t - a * nch, r = a >> 1, c = a & 1;
+            const int row0 = r * kM + lq * 32;  // block row of lane 0 (warp-uniform)
+            if (row0 >= nj) continue;
+            float v[16];
+            if (n_stages > 0) {
+                tmem_ld_32x32b_x16(tmem + ((uint32_t)(lq * 32) << 16) +
+                                       (uint32_t)(a * acc_cols + cc * 16),
+                                   v);
+            } else {
 #pragma unroll
-                for (int x = 0; x < 16; ++x) tile[lane * kPitch + (cc - ch0) * 16 + x] = v[x];
+                for (int x = 0; x < 16; ++x) v[x] = 0.f;  // no frequencies in this slice
+            }
+#pragma unroll
+            for (int x = 0; x < 16; ++x) tile[lane * 17 + x] = v[x];
+            __syncwarp();
+            float *out = partial + (((size_t)split * 2 + c) * og.OH) * og.OW;
+            const int x = lane & 15, col = cc * 16 + x;
+            for (int i = 0; i < 16; ++i) {
+                const int rr = 2 * i + (lane >> 4), mr = row0 + rr;
+                if (mr < nj && col < ni &&
+                    VSAOGM_IN_BOUNDS(b.j0 + mr - og.oy >= 0 && b.j0 + mr - og.oy < og.OH &&
+                                     b.i0 + col - og.ox >= 0 && b.i0 + col - og.ox < og.OW))
+                    out[(size_t)(b.j0 + mr - og.oy) * og.OW + (b.i0 + col - og.ox)] =
+                        tile[rr * 17 + x];
             }
             __syncwarp();
-            const int x0 = ch0 * 16, cols = min(ni, ch1 * 16) - x0;
-            for (int r = 0; r < 32; ++r) {
-                const int mr = lane_base + r;
-                if (mr >= nj) break;
-                if (VSAOGM_IN_BOUNDS(b.j0 + mr - og.oy >= 0 && b.j0 + mr - og.oy < og.OH &&
-                                     b.i0 - og.ox >= 0 && b.i0 - og.ox + ni <= og.OW)) {
-                    float *row = out + (size_t)(b.j0 + mr - og.oy) * og.OW + (b.i0 - og.ox) + x0;
-                    for (int x = lane; x < cols; x += 32) row[x] = tile[r * kPitch + x];
-                }
-            }
-        } else if (!abort_s && n_stages == 0) {
-            // no frequencies in this slice: its contribution is zero
-            if (m < nj)
-                for (int x = ch0 * 16; x < min(ni, ch1 * 16); ++x)
-                    out[(size_t)(b.j0 + m - og.oy) * og.OW + (b.i0 - og.ox) + x] = 0.f;
         }
     }
     if (abort_s && tid == 0) atomicExch(status, VSAOGM_E_TIMEOUT);
@@ -560,11 +579,11 @@ __global__ void __launch_bounds__(kThreads, 1) decode_tc_kernel(
     const BlockBatch blocks, const float2 *__restrict__ omega, const float *__restrict__ inv_norm,
     const float *__restrict__ nu, int D, int tiles_x, const int *__restrict__ row_tile, OutGeom og,
     const float *__restrict__ col_off, const float *__restrict__ row_off,
-    const float2 *__restrict__ rot, int k_per_split, int N, float u_scale,
+    const float2 *__restrict__ rot, int k_per_split, float u_scale,
     float *__restrict__ partial, int *__restrict__ status, uint64_t debug_wait_ns)
 {
     decode_tc_body<P>(blocks.b[blockIdx.x], blockIdx.y, omega, inv_norm, nu, D, tiles_x, row_tile,
-                      og, col_off, row_off, rot, k_per_split, N, u_scale, partial, status,
+                      og, col_off, row_off, rot, k_per_split, u_scale, partial, status,
                       debug_wait_ns);
 }
 
@@ -576,9 +595,8 @@ __global__ void __launch_bounds__(kThreads, 1) decode_tc_batch_kernel(
 {
     const BatchDecodeItem it = items[blockIdx.x];
     const BatchDecodeMap &M = tab.m[it.map];
-    const int N = ((it.b.i1 - it.b.i0) + 15) / 16 * 16;
     decode_tc_body<P>(it.b, it.split, M.omega, M.inv_norm, M.nu, M.D, M.tiles_x, M.row_tile,
-                      OutGeom{0, 0, M.W, M.H}, M.col_off, M.row_off, M.rot, M.k_per_split, N,
+                      OutGeom{0, 0, M.W, M.H}, M.col_off, M.row_off, M.rot, M.k_per_split,
                       M.u_scale, M.partial, M.status, M.debug_wait_ns);
 }
 
@@ -626,9 +644,13 @@ int tc_stage_freqs(int decode_prec) { return stage_freqs(prec_of(decode_prec)); 
 
 VSAOGM_CHECK_TU(decode_tc)
 
-// Blocks of at most 128 x 128 cells covering region r for the tensor-core
-// decode: columns inside one tile column, rows across at most
-// max_block_tiles tile rows (kMaxBlockTiles; 14 for FP8).
+// Blocks covering region r for the tensor-core decode, one CTA each: columns
+// inside one tile column, rows across at most max_block_tiles tile rows.  In
+// a tile column wider than 128 cells a block is one row block (up to 128 rows)
+// by up to 256 columns, the column range cut into equal parts; in a narrower
+// one it is two row blocks (up to 256 rows) by the whole tile column, so the
+// x-phasor operand serves twice the rows.  Either way the tensor memory holds
+// the block's accumulators (row blocks x 2 classes x N <= 512 columns).
 void tc_blocks(const vsaogm_map *m, Region r, std::vector<DecodeBlock> &out)
 {
     out.clear();
@@ -638,16 +660,21 @@ void tc_blocks(const vsaogm_map *m, Region r, std::vector<DecodeBlock> &out)
     for (int bx = 0; bx < m->cfg.tiles_x; ++bx) {
         const int x0 = std::max(r.x0, m->tile_first[0][bx]);
         const int x1 = std::min(r.x1, m->tile_last[0][bx]);
-        if (x0 >= x1) continue;
-        for (int i0 = x0; i0 < x1; i0 += kM) {
-            const int i1 = std::min(i0 + kM, x1);
+        const int w = x1 - x0;
+        if (w <= 0) continue;
+        const bool wide = w > kM;
+        const int parts = wide ? (w + kMaxN - 1) / kMaxN : 1;
+        const int rows_max = wide ? kM : kMaxRowBlocks * kM;
+        for (int p = 0; p < parts; ++p) {
+            const int i0 = x0 + (int)((long long)w * p / parts);
+            const int i1 = x0 + (int)((long long)w * (p + 1) / parts);
             int by = 0;
             for (int j0 = r.y0; j0 < r.y1;) {
                 while (by < ty - 1 && yl[by] <= j0) ++by;  // tile row of row j0
                 // rows up to the end of the max_tiles-th tile row from by
                 int cap = j0 + 1;
                 for (int t = by; t < std::min(by + max_tiles, ty); ++t) cap = std::max(cap, yl[t]);
-                const int j1 = std::min({j0 + kM, r.y1, cap});
+                const int j1 = std::min({j0 + rows_max, r.y1, cap});
                 out.push_back(DecodeBlock{bx, i0, j0, i1, j1});
                 j0 = j1;
             }
@@ -690,8 +717,8 @@ int build_tc_tables(vsaogm_map *m)
     const int D = m->cfg.D;
     cudaError_t e = dev_malloc((void **)&m->tc_rot, sizeof(float2) * 2 * (size_t)D);
     if (e != cudaSuccess) return cuda_error(e, "decode tables");
-    // the same float step as the kernel's rows and columns: kWarps cells
-    tc_rot_kernel<<<(2 * D + 255) / 256, 256>>>(m->nu, 2 * D, (float)kWarps * m->cfg.resolution,
+    // the same float step as the kernel's rows and columns: kStep cells
+    tc_rot_kernel<<<(2 * D + 255) / 256, 256>>>(m->nu, 2 * D, (float)kStep * m->cfg.resolution,
                                                 m->tc_rot);
     if ((e = cudaGetLastError()) != cudaSuccess || (e = cudaDeviceSynchronize()) != cudaSuccess)
         return cuda_error(e, "decode tables");
@@ -727,18 +754,13 @@ int decode_tensor_cores(vsaogm_map *m, Region r, float *heat, cudaStream_t st)
     for (int b0 = 0; b0 < nb; b0 += kMaxLaunchBlocks) {
         BlockBatch batch;
         batch.n = std::min(kMaxLaunchBlocks, nb - b0);
-        int widest = 16;
-        for (int q = 0; q < batch.n; ++q) {
-            batch.b[q] = blocks[b0 + q];
-            widest = std::max(widest, batch.b[q].i1 - batch.b[q].i0);
-        }
-        const int N = (widest + 15) / 16 * 16;  // MMA N: the widest block, multiple of 16
-        const size_t smem = 1024 + 2 * (size_t)stage_size(P, N);
+        for (int q = 0; q < batch.n; ++q) batch.b[q] = blocks[b0 + q];
+        const size_t smem = smem_max(P);
         dim3 grid(batch.n, splits);
 #define VSAOGM_LAUNCH_TC(PP)                                                                   \
     decode_tc_kernel<PP><<<grid, kThreads, smem, st>>>(                                        \
         batch, m->omega, m->inv_norm, m->nu, D, m->cfg.tiles_x, m->row_tile, og, m->col_off,    \
-        m->row_off, m->tc_rot, kps, N, u_scale, part, m->status, m->debug_wait_ns)
+        m->row_off, m->tc_rot, kps, u_scale, part, m->status, m->debug_wait_ns)
         if (P == kPrecFP8)
             VSAOGM_LAUNCH_TC(kPrecFP8);
         else if (P == kPrecFP16)

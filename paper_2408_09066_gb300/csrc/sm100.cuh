@@ -189,6 +189,19 @@ __device__ __forceinline__ uint64_t desc_k_sw128(uint32_t saddr)
     return d;
 }
 
+// The same for the 64-byte swizzle: rows of 64 bytes (32 16-bit elements),
+// 8-row atoms of 512 bytes placed 512 bytes apart, base 512-aligned.
+__device__ __forceinline__ uint64_t desc_k_sw64(uint32_t saddr)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFFu);      // start address
+    d |= (uint64_t)1u << 16;                       // leading byte offset (unused here)
+    d |= (uint64_t)(512u >> 4) << 32;              // stride byte offset: next 8-row atom
+    d |= (uint64_t)1u << 46;                       // descriptor version for tcgen05
+    d |= (uint64_t)4u << 61;                       // swizzle: 64 bytes
+    return d;
+}
+
 // Instruction descriptor of kind::f16 with FP32 accumulation, both operands
 // K-major, dense: a_bf16 selects BF16 (else FP16) inputs.
 __host__ __device__ constexpr uint32_t idesc_f16(int M, int N, bool bf16)
