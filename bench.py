@@ -636,6 +636,25 @@ def oracle_legs(torch, V, dev, wl):
                          "decode": k, **{kk: v for kk, v in full[k].items() if kk != "decode_ms"}}
                         for k in ("fp32", "bf16x3", "fp16x3", "fp8x3"))
     prec["all_within_tolerance"] = all(r["within_tolerance"] for r in prec["rows"])
+    # a stress case without lidar structure: uniformly spread random points (max P
+    # about 2.6), where FP8x3's error of about 2^-8 per product is a large part of
+    # every cell's value; reported apart, not a configuration of the precision study
+    import numpy as np
+    rng = np.random.default_rng(5)
+    n = 20000
+    uw = synth.Workload("uniform_300x170_2x1tiles", rng.uniform(-9.0, 9.0, (n, 2)).astype(np.float32),
+                        rng.integers(0, 2, n).astype(np.uint8), 300, 170, 0.06, -9.0, -5.1, 2, 1,
+                        1000, 0.15, 9, None)
+    o, g, nx, ny = _oracle_setup(uw)
+    want = o.pipeline(g, nx, ny, uw.xy, uw.labels, 3, 3, 0.0, "tile")
+    prec["uniform_stress"] = {
+        "map": "300x170 at 0.06 m, 2x1 tiles, D=1000, 20000 uniform random points",
+        **{d: parity_errors(gpu_outputs(torch, V, dev, uw, d), want, d)
+           for d in ("fp32", "bf16x3", "fp16x3", "fp8x3")}}
+    prec["fp8x3"] = ("the lower-accuracy path: e4m3 hi + lo carries about 8 significant bits "
+                     "per operand value, so P is off by about 2^-8 in absolute terms and the "
+                     "occupancy error grows as the map's maximum P falls; it meets the stated "
+                     "bounds on every lidar-shaped map here and not on the uniform stress case")
     assert oracle.num_threads() == cb["cores"]
     return cb, full, prec
 

@@ -55,7 +55,12 @@ extern "C" {
 #define VSAOGM_DECODE_FP16X3 2 /* tensor cores, split hi/lo fp16, FP32 accum */
 #define VSAOGM_DECODE_FP8X3 3  /* tensor cores, split hi/lo e4m3, FP32 accum:
                                   about 7 significant bits per product, the
-                                  precision study's lowest rung              */
+                                  precision study's lowest rung and the
+                                  lower-accuracy path: P is off by about 2^-8
+                                  in absolute terms, which meets the stated
+                                  occupancy bound on lidar-shaped maps but not
+                                  on maps whose maximum P is near 1 (few,
+                                  spread-out points)                         */
 
 /* vsaogm_config.decode_mode: the toggles of the decoding ablation
  * (Sec. IV-D1: P_hat = f_ACT(f_NL(f_N(P))) with toggles delta_N, delta_NL,

@@ -78,9 +78,12 @@ def test_ragged_blocks_and_slices(prec):
     cfg = V.default_config(D=1000, grid_w=300, grid_h=170, resolution=0.06, x_min=-9.0,
                            y_min=-5.1, tiles_x=2, tiles_y=1, length_scale=0.15, seed=9,
                            decode_prec=prec)
-    # FP8 on uniformly spread points (max P about 2.6, so its absolute error of
-    # about 1e-2 in P is a large part of every cell's value) misses the 1e-3
-    # occupancy bound: 5.5e-3 measured.  The lidar-shaped cases above meet it.
+    # FP8x3 is the lower-accuracy path (documented as such in the header and
+    # the benchmark's precision record): on uniformly spread points (max P
+    # about 2.6, so its absolute error of about 1e-2 in P is a large part of
+    # every cell's value) it misses the stated 1e-3 occupancy bound (5.5e-3
+    # measured) and is held here to 1e-2; every lidar-shaped case above, the
+    # paper map and the 64-map batch meet 1e-3.
     _check(run_gpu(cfg, xy, lab), _oracle(cfg, xy, lab), prec,
            1e-2 if prec == V.DECODE_FP8X3 else 1e-3)
 
