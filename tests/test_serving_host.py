@@ -273,3 +273,31 @@ def test_summary_percentiles_and_rate():
     assert s["update"]["count"] == 2 and s["query"]["count"] == 2
     assert s["update"]["p50_ms"] == pytest.approx(2.0) and s["query"]["max_ms"] == pytest.approx(4.0)
     assert s["requests_per_s"] == pytest.approx(4.0)
+
+
+def test_garbage_collector_is_paused_while_serving_and_restored():
+    """The loop runs with Python's cyclic garbage collector off (its pauses
+    showed up as isolated ~10 ms latencies) and leaves it as it found it."""
+    import gc
+    world = World(seed=5)
+    srv = make_server(world, n_robots=2, n_slots=2)
+    seen = []
+    orig = FakeEvent.query
+
+    def spy(self):
+        seen.append(gc.isenabled())
+        return orig(self)
+
+    reqs = make_requests(world.rng, 2, 12, 0.001)
+    try:
+        FakeEvent.query = spy
+        assert gc.isenabled()
+        srv.run(reqs, realtime=False)
+        assert seen and not any(seen)
+        assert gc.isenabled()
+        gc.disable()
+        srv.run(make_requests(world.rng, 2, 4, 0.001), realtime=False)
+        assert not gc.isenabled()
+    finally:
+        FakeEvent.query = orig
+        gc.enable()
