@@ -265,7 +265,7 @@ int enqueue_step(vsaogm_batch *b, const float *const *xy, const uint8_t *const *
         dt.m[i] = BatchDecodeMap{m->omega, m->inv_norm, m->nu, m->col_off, m->row_off,
                                  m->tc_rot, m->row_tile, (float *)b->ws[i].dec_partial.ptr,
                                  m->status, D, kps, m->cfg.grid_w, m->cfg.grid_h,
-                                 m->cfg.tiles_x, u, m->debug_wait_ns};
+                                 m->cfg.tiles_x, u, m->debug_wait_ns, m->tc_xtmap};
         BatchMapOut &o = ot.m[i];
         o.partial = (const float *)b->ws[i].dec_partial.ptr;
         o.heat = heat[i];

@@ -39,6 +39,8 @@
 // per-class maxima (Eq. non-linearities needs the map maximum).  Every wait is
 // bounded: on time-out the CTA records VSAOGM_E_TIMEOUT, drains its MMAs, frees
 // its tensor memory and returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_fp8.h>
@@ -58,18 +60,18 @@ enum TcPrec { kPrecBF16 = 0, kPrecFP16 = 1, kPrecFP8 = 2 };
 constexpr int kM = 128;            // rows per row block (MMA M)
 constexpr int kRowBytes = 64;      // bytes per operand row and stage (64-byte swizzle)
 constexpr int kWords = kRowBytes / 4;  // 4-byte words per operand row
-constexpr int kProducers = 512;    // 16 warps generate the operands ...
+constexpr int kProducers = 512;    // 16 warps generate the A operands ...
 constexpr int kWarps = kProducers / 32;
 constexpr int kMmaWarp = kWarps;       // ... one issues the MMAs ...
-constexpr int kLoadWarp = kWarps + 1;  // ... and one stages each stage's inputs
-constexpr int kThreads = kProducers + 64;
-constexpr int kStep = 32;          // cells between a thread's rows (and columns)
+constexpr int kLoadWarp = kWarps + 1;  // ... one stages each stage's inputs ...
+constexpr int kBLoadWarp = kWarps + 2; // ... and one copies the B operand by TMA
+constexpr int kThreads = kProducers + 96;
+constexpr int kStep = 32;          // cells between a thread's rows
 constexpr int kMaxRowBlocks = 2;   // 128-row blocks per CTA
 constexpr int kMaxN = 256;         // MMA N of a one-row-block CTA (128 with two)
 constexpr int kATile = kM * kRowBytes;           // one A operand tile (8 KB)
-constexpr int kAArea = kMaxRowBlocks * 4 * kATile;  // row blocks x classes x hi/lo (64 KB)
-constexpr int kBTile = kMaxN * kRowBytes;        // one B operand tile (16 KB)
-constexpr int kBArea = 2 * kBTile;               // hi and lo (32 KB)
+constexpr int kBoxRows = 64;       // rows of one TMA box of the x-phasor table
+constexpr int kBRing = 4;          // B operand slots (TMA runs this many stages ahead)
 constexpr int kTmemCols = 512;                   // accumulators: row blocks x classes x N
 constexpr uint64_t kWaitNs = 2000000000ull;     // 2 s: far above any legitimate wait
 
@@ -79,19 +81,32 @@ __host__ __device__ constexpr int stage_freqs(int prec) { return prec == kPrecFP
 __host__ __device__ constexpr int max_block_tiles(int) { return kMaxBlockTiles; }
 // Bytes of the aux area of one stage: the staged memories (tile row, class,
 // frequency) float2, then per frequency (nu_x, nu_y) and the x and y step
-// phasors, float2 each; rounded up so that every stage starts 1024-aligned.
+// phasors, float2 each; rounded up to 1024 bytes.
 __host__ __device__ constexpr int aux_bytes(int prec)
 {
     return ((max_block_tiles(prec) * 2 + 3) * stage_freqs(prec) * 8 + 1023) / 1024 * 1024;
 }
-// Bytes of one pipeline stage: A (row blocks, classes, hi and lo), B (hi and
-// lo) and the aux area.
-__host__ __device__ constexpr int stage_size(int prec) { return kAArea + kBArea + aux_bytes(prec); }
-__host__ __device__ constexpr size_t smem_max(int prec) { return 1024 + 2 * (size_t)stage_size(prec); }
-static_assert(smem_max(kPrecFP8) <= 232448 - 256, "two FP8 stages fit in shared memory");
-static_assert(smem_max(kPrecBF16) <= 232448 - 256, "two 16-bit stages fit in shared memory");
+// Shared memory of a CTA with rb row blocks and MMA width N: two A buffers
+// (row blocks x classes x hi/lo tiles), two aux areas, then kBRing B slots of
+// a hi and a lo tile of N rows rounded up to whole TMA boxes.  Every offset
+// is a multiple of 1024 bytes.
+__host__ __device__ constexpr int a_buffer_bytes(int rb) { return rb * 4 * kATile; }
+__host__ __device__ constexpr int b_tile_rows(int N) { return (N + kBoxRows - 1) / kBoxRows * kBoxRows; }
+__host__ __device__ constexpr int b_slot_bytes(int N) { return 2 * b_tile_rows(N) * kRowBytes; }
+__host__ __device__ constexpr int smem_layout_bytes(int prec, int rb, int N)
+{
+    return 2 * a_buffer_bytes(rb) + 2 * aux_bytes(prec) + kBRing * b_slot_bytes(N);
+}
+__host__ __device__ constexpr size_t smem_max(int prec)
+{
+    return 1024 + (size_t)(smem_layout_bytes(prec, 2, kMaxN / 2) > smem_layout_bytes(prec, 1, kMaxN)
+                               ? smem_layout_bytes(prec, 2, kMaxN / 2)
+                               : smem_layout_bytes(prec, 1, kMaxN));
+}
+static_assert(smem_max(kPrecFP8) <= 232448 - 512, "FP8 buffers fit in shared memory");
+static_assert(smem_max(kPrecBF16) <= 232448 - 512, "16-bit buffers fit in shared memory");
 // epilogue staging: per producer warp 32 rows x 16 columns (pitch 17)
-static_assert(kWarps * 32 * 17 * 4 <= 2 * kAArea, "epilogue staging fits the A areas");
+static_assert(kWarps * 32 * 17 * 4 <= 2 * a_buffer_bytes(1), "epilogue staging fits the A buffers");
 
 __device__ __forceinline__ float2 phasor(float nu, float d)
 {
@@ -103,11 +118,6 @@ __device__ __forceinline__ float2 phasor(float nu, float d)
     float s, c;
     __sincosf(__fmul_rn(f, 6.28318530717958647692f), &s, &c);
     return make_float2(c, s);
-}
-
-__device__ __forceinline__ float2 cmul(float2 a, float2 b)
-{
-    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
 
 // Splits two 16-bit operand values (x, y) into a 4-byte word of hi parts and
@@ -250,18 +260,18 @@ __device__ __forceinline__ void decode_tc_body(
     const int *__restrict__ row_tile, OutGeom og, const float *__restrict__ col_off,
     const float *__restrict__ row_off, const float2 *__restrict__ rot, int k_per_split,
     float u_scale, float *__restrict__ partial, int *__restrict__ status,
-    uint64_t debug_wait_ns)
+    uint64_t debug_wait_ns, const uint8_t *__restrict__ xtmap)
 {
     constexpr int KS = stage_freqs(P);       // frequencies per stage
     constexpr int FPL = KS / kWords;         // frequencies per operand word
     extern __shared__ uint8_t smem_raw[];
     __shared__ uint64_t full_bar[2], empty_bar[2], aux_full[2], done_bar, never_bar;
+    __shared__ uint64_t b_full[kBRing], b_empty[kBRing];
     __shared__ float s_scale[2 * kMaxBlockTiles];  // 1 / norm x u_scale per (tile row, class)
     __shared__ uint32_t tmem_base_s;
     __shared__ int abort_s;
     volatile int *abort_v = &abort_s;
     uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    constexpr int stage_bytes = stage_size(P);
     // limit of the pipeline's waits: 2 s, or the failure-test knob (the drain
     // before the tensor memory is freed always keeps the 2 s limit)
     const uint64_t wait_ns = debug_wait_ns ? debug_wait_ns : kWaitNs;
@@ -274,6 +284,11 @@ __device__ __forceinline__ void decode_tc_body(
     const int rb = nj > kM ? 2 : 1;               // row blocks
     const int N = (ni + 15) / 16 * 16;            // MMA N
     const int acc_cols = kTmemCols / (2 * rb);    // tensor-memory columns per accumulator
+    // shared memory layout (offsets from `smem`): A buffers, aux areas, B slots
+    const int a_bytes = a_buffer_bytes(rb);
+    const int aux_off = 2 * a_bytes;
+    const int b_off = aux_off + 2 * aux_bytes(P);
+    const int b_slot = b_slot_bytes(N), b_lo = b_tile_rows(N) * kRowBytes;
     const int by0 = row_tile[b.j0];
     const int nt = row_tile[b.j1 - 1] - by0 + 1;  // tile rows of the block
     if (nt < 1 || nt > max_block_tiles(P) || ni < 1 || nj < 1 || nj > kMaxRowBlocks * kM ||
@@ -292,6 +307,10 @@ __device__ __forceinline__ void decode_tc_body(
             mbar_init(&full_bar[q], kWarps);
             mbar_init(&empty_bar[q], 1);
             mbar_init(&aux_full[q], 32);  // every loader lane arrives once its copies land
+        }
+        for (int q = 0; q < kBRing; ++q) {
+            mbar_init(&b_full[q], 1);   // the TMA warp's arrival plus the copies' bytes
+            mbar_init(&b_empty[q], 1);  // the MMA warp's commit
         }
         mbar_init(&done_bar, 1);
         mbar_init(&never_bar, 1);  // nothing arrives on it (failure test only)
@@ -316,17 +335,20 @@ __device__ __forceinline__ void decode_tc_body(
         const uint32_t idesc = idesc_of<P>(N);
         const uint64_t d0 = desc_k_sw64(smem_addr(smem));
         for (int s = 0; s < n_stages; ++s) {
-            const int buf = s & 1;
+            const int buf = s & 1, bs = s % kBRing;
             if (!*abort_v && !mbar_wait(&full_bar[buf], (uint32_t)(s >> 1) & 1u, wait_ns))
+                atomicExch(&abort_s, 1);
+            if (!*abort_v && !mbar_wait(&b_full[bs], (uint32_t)(s / kBRing) & 1u, wait_ns))
                 atomicExch(&abort_s, 1);
             tc_fence_after_sync();
             if (lane == 0) {
-                const uint64_t ob = d0 + (uint64_t)((buf * stage_bytes) >> 4);
+                const uint64_t oa = d0 + (uint64_t)((buf * a_bytes) >> 4);
+                const uint64_t ob = d0 + (uint64_t)((b_off + bs * b_slot) >> 4);
 #pragma unroll
                 for (int kk = 0; kk < kRowBytes / 32; ++kk) {
-                    const uint64_t o = ob + (uint64_t)(kk * 2);
-                    const uint64_t dbh = o + (uint64_t)(kAArea >> 4);
-                    const uint64_t dbl = dbh + (uint64_t)(kBTile >> 4);
+                    const uint64_t o = oa + (uint64_t)(kk * 2);  // 32 bytes of each row
+                    const uint64_t dbh = ob + (uint64_t)(kk * 2);
+                    const uint64_t dbl = dbh + (uint64_t)(b_lo >> 4);
                     for (int r = 0; r < rb; ++r) {
 #pragma unroll
                         for (int c = 0; c < 2; ++c) {
@@ -340,6 +362,7 @@ __device__ __forceinline__ void decode_tc_body(
                     }
                 }
                 mma_commit(&empty_bar[buf]);
+                mma_commit(&b_empty[bs]);
             }
             __syncwarp();
         }
@@ -365,8 +388,7 @@ __device__ __forceinline__ void decode_tc_body(
             if (s >= 2 && !*abort_v &&
                 !mbar_wait(&full_bar[buf], (uint32_t)((s - 2) >> 1) & 1u, wait_ns))
                 atomicExch(&abort_s, 1);
-            float2 *aw = reinterpret_cast<float2 *>(smem + (size_t)buf * stage_bytes + kAArea +
-                                                    kBArea);
+            float2 *aw = reinterpret_cast<float2 *>(smem + aux_off + buf * aux_bytes(P));
             float2 *af = aw + max_block_tiles(P) * 2 * KS;
             const int k0 = k_begin + s * KS;
             for (int e = lane; e < n_w; e += 32) {
@@ -387,6 +409,39 @@ __device__ __forceinline__ void decode_tc_body(
             cp_async_mbar_arrive(&aux_full[buf]);
         }
         cp_async_wait_all();
+    } else if (warp == kBLoadWarp) {
+        // ------------------------------------------------ TMA warp (B operand)
+        // Slot s mod kBRing receives the x phasors (hi and lo tiles) of the
+        // block's N columns and stage s's frequencies, copied from the map's
+        // table by TMA boxes of 16 words x 64 rows (64-byte swizzle); rows past
+        // the map read as zeros and rows past N are never used.  It refills a
+        // slot once the MMAs that read it have completed (b_empty).
+        if (lane == 0 && n_stages > 0) {
+            const uint8_t *t_hi = xtmap, *t_lo = xtmap + 128;
+            tensormap_acquire(t_hi);
+            tensormap_acquire(t_lo);
+            const int nbox = b_tile_rows(N) / kBoxRows;
+            const uint32_t bytes = (uint32_t)(2 * nbox * kBoxRows * kRowBytes);
+            for (int s = 0; s < n_stages; ++s) {
+                const int bs = s % kBRing;
+                if (s >= kBRing && !*abort_v &&
+                    !mbar_wait(&b_empty[bs], (uint32_t)((s - kBRing) / kBRing) & 1u, wait_ns))
+                    atomicExch(&abort_s, 1);
+                uint8_t *dst = smem + b_off + bs * b_slot;
+                const int x = (k_begin + s * KS) / FPL;  // word of the stage's first frequency
+                mbar_arrive_expect_tx(&b_full[bs], bytes);
+                for (int j = 0; j < nbox; ++j) {
+                    tma_load_2d(dst + j * kBoxRows * kRowBytes, t_hi, x, b.i0 + j * kBoxRows,
+                                &b_full[bs]);
+                    tma_load_2d(dst + b_lo + j * kBoxRows * kRowBytes, t_lo, x,
+                                b.i0 + j * kBoxRows, &b_full[bs]);
+                }
+            }
+            // every copy issued has landed before the CTA may end (bounded)
+            for (int s = max(0, n_stages - kBRing); s < n_stages; ++s)
+                mbar_wait(&b_full[s % kBRing], (uint32_t)(s / kBRing) & 1u, kWaitNs);
+        }
+        __syncwarp();
     } else {
         // ------------------------------------------------------ producers
         const int wd = lane & (kWords - 1);  // word of the operand rows
@@ -402,7 +457,6 @@ __device__ __forceinline__ void decode_tc_body(
             const int t = v ? row_tile[b.j0 + m] - by0 : 0;
             tl[q] = VSAOGM_IN_BOUNDS(t >= 0 && t < nt) ? t : 0;  // staged memories exist for [0, nt)
         }
-        const float dx0 = r0 < ni ? col_off[b.i0 + r0] : 0.f;
         // byte of the thread's word in its first row: 64-byte swizzle phase w mod 4
         const uint32_t soff = (uint32_t)(r0 * kRowBytes +
                                          ((((wd >> 2) ^ (warp & 3)) << 4) | ((wd & 3) << 2)));
@@ -418,48 +472,22 @@ __device__ __forceinline__ void decode_tc_body(
             }
             if (!*abort_v && !mbar_wait(&aux_full[buf], (uint32_t)(s >> 1) & 1u, wait_ns))
                 atomicExch(&abort_s, 1);
-            uint8_t *st = smem + (size_t)buf * stage_bytes;
-            uint8_t *bh = st + kAArea, *bl = bh + kBTile;
-            const float2 *sw = reinterpret_cast<const float2 *>(bl + kBTile);
+            uint8_t *st = smem + buf * a_bytes;
+            const float2 *sw = reinterpret_cast<const float2 *>(smem + aux_off + buf * aux_bytes(P));
             const float2 *sf = sw + max_block_tiles(P) * 2 * KS;
-            float nux[FPL], nuy[FPL];
-            float2 rsx[FPL], rsy[FPL];
+            float nuy[FPL];
+            float2 rsy[FPL];
 #pragma unroll
             for (int j = 0; j < FPL; ++j) {
-                const float2 f = sf[FPL * wd + j];
-                nux[j] = f.x;
-                nuy[j] = f.y;
-                rsx[j] = sf[KS + FPL * wd + j];
+                nuy[j] = sf[FPL * wd + j].y;
                 rsy[j] = sf[2 * KS + FPL * wd + j];
             }
             // No masking below: frequencies past the slice's end have staged
             // memories 0, so their U and hence their products vanish; rows and
             // columns past the block (its MMA padding) are never written out.
             //
-            // B operand: x phasors of the N columns.  Column r0 + 32 (q + 1) is
-            // 32 cells right of column r0 + 32 q in the same tile, so its
-            // phasor is the previous one times exp(i 2 pi nu_x 32 res).
-            {
-                float2 a[FPL];
-#pragma unroll
-                for (int j = 0; j < FPL; ++j) a[j] = phasor(nux[j], dx0);
-#pragma unroll
-                for (int q = 0; q < kMaxN / kStep; ++q) {
-                    if (kStep * q >= N) break;  // every column of the warp is past N
-#pragma unroll
-                    for (int j = 0; j < FPL; ++j)
-                        if (q > 0) a[j] = cmul(a[j], rsx[j]);
-                    uint32_t hi, lo;
-                    if (FPL == 1)
-                        split_pair<P>(a[0].x, a[0].y, hi, lo);
-                    else
-                        split_quad_e4m3(a[0].x, a[0].y, a[FPL - 1].x, a[FPL - 1].y, hi, lo);
-                    if (r0 + kStep * q < N) {
-                        *reinterpret_cast<uint32_t *>(bh + q * kQBytes + soff) = hi;
-                        *reinterpret_cast<uint32_t *>(bl + q * kQBytes + soff) = lo;
-                    }
-                }
-            }
+            // (the B operand, the x phasors of the N columns, comes from the
+            // map's table by TMA)
             // A operands: (Re U_psi, -Im U_psi) with U_psi = conj(w_hat_psi) x
             // the y phasor, i.e. V_psi = conj(U_psi) = w_hat_psi x conj(phasor),
             // held for both classes as packed pairs X = (Re V_0, Re V_1), Y =
@@ -580,11 +608,12 @@ __global__ void __launch_bounds__(kThreads, 1) decode_tc_kernel(
     const float *__restrict__ nu, int D, int tiles_x, const int *__restrict__ row_tile, OutGeom og,
     const float *__restrict__ col_off, const float *__restrict__ row_off,
     const float2 *__restrict__ rot, int k_per_split, float u_scale,
-    float *__restrict__ partial, int *__restrict__ status, uint64_t debug_wait_ns)
+    float *__restrict__ partial, int *__restrict__ status, uint64_t debug_wait_ns,
+    const uint8_t *__restrict__ xtmap)
 {
     decode_tc_body<P>(blocks.b[blockIdx.x], blockIdx.y, omega, inv_norm, nu, D, tiles_x, row_tile,
                       og, col_off, row_off, rot, k_per_split, u_scale, partial, status,
-                      debug_wait_ns);
+                      debug_wait_ns, xtmap);
 }
 
 // Many maps in one launch: CTA q decodes item q of a device list of
@@ -597,7 +626,7 @@ __global__ void __launch_bounds__(kThreads, 1) decode_tc_batch_kernel(
     const BatchDecodeMap &M = tab.m[it.map];
     decode_tc_body<P>(it.b, it.split, M.omega, M.inv_norm, M.nu, M.D, M.tiles_x, M.row_tile,
                       OutGeom{0, 0, M.W, M.H}, M.col_off, M.row_off, M.rot, M.k_per_split,
-                      M.u_scale, M.partial, M.status, M.debug_wait_ns);
+                      M.u_scale, M.partial, M.status, M.debug_wait_ns, M.xtmap);
 }
 
 // rot[k] = exp(i 2 pi nu[k] step) for the x frequencies, then the y ones: the
@@ -617,6 +646,35 @@ __global__ void __launch_bounds__(256) tc_rot_kernel(const float *__restrict__ n
     float sn, cs;
     sincospif(2.f * f, &sn, &cs);
     rot[k] = make_float2(cs, sn);
+}
+
+// The x-phasor table of the B operand: plane 0 the hi parts, plane 1 the lo
+// parts, each [W columns][Dp words] with word w of column c holding the split
+// x phasor(s) exp(i 2 pi nu_x[k] dx_c) of frequency k = w (16-bit formats) or
+// k = 2w, 2w + 1 (FP8) in the layout of one operand row; words past D are 0.
+// Built once per map: it depends only on the frequencies and the geometry.
+template <int P>
+__global__ void __launch_bounds__(256) tc_xtab_kernel(const float *__restrict__ nu,
+                                                      const float *__restrict__ col_off, int D,
+                                                      int W, int Dp, uint32_t *__restrict__ tab)
+{
+    const size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    if (i >= (size_t)W * Dp) return;
+    constexpr int FW = P == kPrecFP8 ? 2 : 1;  // frequencies per word
+    const int c = (int)(i / Dp), w = (int)(i % Dp);
+    float2 v[FW];
+#pragma unroll
+    for (int j = 0; j < FW; ++j) {
+        const int k = FW * w + j;
+        v[j] = k < D ? phasor(nu[k], col_off[c]) : make_float2(0.f, 0.f);
+    }
+    uint32_t hi, lo;
+    if (FW == 1)
+        split_pair<P>(v[0].x, v[0].y, hi, lo);
+    else
+        split_quad_e4m3(v[0].x, v[0].y, v[FW - 1].x, v[FW - 1].y, hi, lo);
+    tab[i] = hi;
+    tab[(size_t)W * Dp + i] = lo;
 }
 
 int prec_of(int decode_prec)
@@ -720,7 +778,48 @@ int build_tc_tables(vsaogm_map *m)
     // the same float step as the kernel's rows and columns: kStep cells
     tc_rot_kernel<<<(2 * D + 255) / 256, 256>>>(m->nu, 2 * D, (float)kStep * m->cfg.resolution,
                                                 m->tc_rot);
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_error(e, "decode tables");
+    // the x-phasor table of the B operand and its two TMA tensor maps
+    const int P = prec_of(m->cfg.decode_prec);
+    const int W = m->cfg.grid_w;
+    const int words = P == kPrecFP8 ? (D + 1) / 2 : D;
+    const int Dp = (words + kWords - 1) / kWords * kWords;  // whole 64-byte boxes
+    const size_t plane = (size_t)W * Dp;
+    if ((e = dev_malloc((void **)&m->tc_xtab, sizeof(uint32_t) * 2 * plane)) != cudaSuccess)
+        return cuda_error(e, "decode tables");
+    const unsigned grid = (unsigned)((plane + 255) / 256);
+    if (P == kPrecFP8)
+        tc_xtab_kernel<kPrecFP8><<<grid, 256>>>(m->nu, m->col_off, D, W, Dp, m->tc_xtab);
+    else if (P == kPrecFP16)
+        tc_xtab_kernel<kPrecFP16><<<grid, 256>>>(m->nu, m->col_off, D, W, Dp, m->tc_xtab);
+    else
+        tc_xtab_kernel<kPrecBF16><<<grid, 256>>>(m->nu, m->col_off, D, W, Dp, m->tc_xtab);
     if ((e = cudaGetLastError()) != cudaSuccess || (e = cudaDeviceSynchronize()) != cudaSuccess)
+        return cuda_error(e, "decode tables");
+    PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", (void **)&encode, 12000,
+                                         cudaEnableDefault, &q);
+    if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !encode)
+        return set_error(VSAOGM_E_CUDA, "decode tables: cuTensorMapEncodeTiled unavailable");
+    CUtensorMap maps[2];
+    for (int h = 0; h < 2; ++h) {
+        // [W rows][Dp words] of 4 bytes; a box is one 64-byte operand row
+        // (16 words) by kBoxRows columns, written with the 64-byte swizzle
+        const cuuint64_t dims[2] = {(cuuint64_t)Dp, (cuuint64_t)W};
+        const cuuint64_t strides[1] = {(cuuint64_t)Dp * 4};
+        const cuuint32_t box[2] = {(cuuint32_t)kWords, (cuuint32_t)kBoxRows};
+        const cuuint32_t elem[2] = {1, 1};
+        CUresult r = encode(&maps[h], CU_TENSOR_MAP_DATA_TYPE_UINT32, 2,
+                            (void *)(m->tc_xtab + h * plane), dims, strides, box, elem,
+                            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
+                            CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS)
+            return set_error(VSAOGM_E_CUDA, "decode tables: tensor map (error %d)", (int)r);
+    }
+    if ((e = dev_malloc((void **)&m->tc_xtmap, sizeof(maps))) != cudaSuccess)
+        return cuda_error(e, "decode tables");
+    if ((e = cudaMemcpy(m->tc_xtmap, maps, sizeof(maps), cudaMemcpyHostToDevice)) != cudaSuccess)
         return cuda_error(e, "decode tables");
     return VSAOGM_OK;
 }
@@ -760,7 +859,7 @@ int decode_tensor_cores(vsaogm_map *m, Region r, float *heat, cudaStream_t st)
 #define VSAOGM_LAUNCH_TC(PP)                                                                   \
     decode_tc_kernel<PP><<<grid, kThreads, smem, st>>>(                                        \
         batch, m->omega, m->inv_norm, m->nu, D, m->cfg.tiles_x, m->row_tile, og, m->col_off,    \
-        m->row_off, m->tc_rot, kps, u_scale, part, m->status, m->debug_wait_ns)
+        m->row_off, m->tc_rot, kps, u_scale, part, m->status, m->debug_wait_ns, m->tc_xtmap)
         if (P == kPrecFP8)
             VSAOGM_LAUNCH_TC(kPrecFP8);
         else if (P == kPrecFP16)

@@ -183,16 +183,14 @@ struct BatchReduceTable {
 struct BatchDecodeMap {
     const float2 *omega;
     const float *inv_norm, *nu, *col_off, *row_off;
-    const float2 *rot;      // [2][D]: x then y phasor of a 16-cell step
+    const float2 *rot;      // [2][D]: x then y phasor of a 32-cell step
     const int *row_tile;    // tile row of each cell row
     float *partial;         // [slices][2][H][W]
     int *status;
     int D, k_per_split, W, H, tiles_x;
     float u_scale;
-    uint64_t debug_wait_ns;
-    // generation of the memories (bumped by every call that writes them) and
-    // the generation whose whole-map P ws.map_heat holds (~0: none)
-    uint64_t mem_gen, map_heat_gen;  // the failure-test wait limit (0: off)
+    uint64_t debug_wait_ns;  // the failure-test wait limit (0: off)
+    const uint8_t *xtmap;    // TMA tensor maps of the x-phasor table (hi, lo)
 };
 struct BatchDecodeTable {
     int n_maps;
@@ -284,7 +282,9 @@ struct vsaogm_map {
     int *col_tile, *row_tile;    // [W], [H]
     float *col_off, *row_off;    // [W], [H]
     unsigned *enc_cnt;           // [S][ceil(D / 512)]: the encode's finished-chunk counters
-    float2 *tc_rot;              // tensor-core decode: [2][D] phasors of a 16-cell step
+    float2 *tc_rot;              // tensor-core decode: [2][D] phasors of a 32-cell step
+    uint32_t *tc_xtab;           // tensor-core decode: x-phasor table, hi and lo planes [W][Dp]
+    uint8_t *tc_xtmap;           // tensor-core decode: the table's two TMA tensor maps (device)
     // failure test (VSAOGM_DEBUG_WAIT_NS at creation; 0: off): the tensor-core
     // decode's pipeline waits give up after this many nanoseconds and its
     // loader warp first stalls for four times as long, so that they do

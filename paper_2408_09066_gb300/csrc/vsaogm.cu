@@ -187,7 +187,7 @@ void free_map(vsaogm_map *m)
     void *ptrs[] = {m->nu, m->omega, m->inv_norm, m->maxima, m->rejected, m->enc_cnt, m->bnd_x_lo,
                     m->bnd_y_lo, m->centre_x, m->centre_y, m->col_tile, m->row_tile,
                     m->col_off, m->row_off, m->status, m->patch_cx[0], m->patch_cy[0],
-                    m->patch_cx[1], m->patch_cy[1], m->tc_rot};
+                    m->patch_cx[1], m->patch_cy[1], m->tc_rot, m->tc_xtab, m->tc_xtmap};
     for (void *p : ptrs)
         if (p) dev_free(p);
     free_scratch(m->ws);
