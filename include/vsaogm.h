@@ -86,7 +86,9 @@ extern "C" {
                                   vsaogm_query; see vsaogm_query_window     */
 
 /* Map parameters (Sec. III-B2 Initialization, Sec. III-B3 tiling, Table of
- * VSA-OGM parameters).  Memory per map: 2 * tiles_x * tiles_y * D * 8 bytes. */
+ * VSA-OGM parameters).  Memory per map: 2 * tiles_x * tiles_y * D * 8 bytes,
+ * plus, for a tensor-core decode_prec, the decode's x-phasor table of about
+ * grid_w * D * 8 bytes (half that for FP8X3), built once at creation. */
 typedef struct {
     int32_t D;            /* FHRR dimension (complex elements per memory), >= 1 */
     int32_t grid_w;       /* cells along x, >= 1                                  */

@@ -1,44 +1,50 @@
 // Decoding on the 5th-generation tensor cores (Eq. loc-query, split precision).
 //
-// For one block of up to 128 rows (y cells) x N columns (x cells) and a slice of
-// the frequencies k, both class maps are the real GEMM
+// For one block of rows (y cells) x N columns (x cells) and a slice of the
+// frequencies k, both class maps are the real GEMM
 //   P_psi[m][n] = sum_k' Aop_psi[m][k'] * Bop[n][k'],
 //   Aop_psi[m][2k] = Re U_psi(j_m, k),  Aop_psi[m][2k+1] = -Im U_psi(j_m, k),
 //   Bop[n][2k]     = Re A(i_n, k),      Bop[n][2k+1]     =  Im A(i_n, k),
 // with A(i, k) = exp(i 2 pi nu_x[k] dx_i) and U_psi = conj(w_hat_psi[k]) *
 // exp(i 2 pi nu_y[k] dy_j): the sum over k' is Re sum_k U A, i.e. Eq. loc-query
-// in its separable form.  Both operands are generated in shared memory (sin/cos
-// after an exact phase reduction for a thread's first row or column, a complex
-// multiply by the map's 16-cell step phasor for the next ones, then the
-// complex product with the memories), never read from HBM, in the
-// 128-byte-swizzled K-major layout the tensor cores read.
+// in its separable form.  The A operands depend on the memories and are
+// generated in shared memory every call (sin/cos after an exact phase
+// reduction for a thread's first row, a complex multiply by the map's 32-cell
+// step phasor for the next ones, the product with the memories); the B operand
+// depends only on the frequencies and the geometry, so it is computed once per
+// map into an x-phasor table in HBM (already split, in the operand layout) and
+// copied by TMA.  Both are read by the tensor cores in the 64-byte-swizzled
+// K-major layout: word kk of row m at byte m * 64 + ((kk / 4) xor ((m / 2) mod
+// 4)) * 16 + (kk mod 4) * 4.
 //
 // Precision: each operand is split x = hi + lo in BF16, FP16 or FP8 (e4m3) and
 // the product is hi*hi + hi*lo + lo*hi with FP32 accumulation in tensor memory:
 // about 16 significant bits per product with BF16 or FP16, about 7 with FP8.
 // U is scaled by a power of two for FP16 and FP8 to stay clear of their
-// subnormals.  A 128-byte operand row holds 32 complex frequencies in the
-// 16-bit formats (kind::f16 MMAs) and 64 in FP8 (kind::f8f6f4 MMAs).
+// subnormals.  A 64-byte operand row (one pipeline stage) holds 16 complex
+// frequencies in the 16-bit formats (kind::f16 MMAs) and 32 in FP8
+// (kind::f8f6f4 MMAs).
 //
-// Blocks: up to 128 columns inside one tile column by up to 128 rows that may
-// cross tile rows (each row multiplies the memories of its own tile), so the
-// 128-row MMA tile is filled even when tiles are short.
+// Blocks: in a tile column wider than 128 cells, one row block of up to 128
+// rows by up to 256 columns (MMA N = 256); in a narrower one, two row blocks
+// (up to 256 rows) by the tile column's width, sharing B.  Rows may cross tile
+// rows (each row multiplies the memories of its own tile), so the 128-row MMA
+// tiles are filled even when tiles are short.
 //
-// Pipeline per CTA (one CTA per SM): 16 producer warps generate stage s into one
-// of two shared-memory buffers while the tensor cores run stage s - 1 from the
-// other; a loader warp stages the memories, frequencies and step phasors of
-// each stage in the buffer's aux area ahead of the producers, and a further
-// warp issues the 24 MMAs of a stage (2 classes x 3 products x 4 K-steps of
-// 32 bytes) and commits them to the buffer's mbarrier; the warps hand stages
-// over through mbarriers only.  The
-// 128-byte swizzle puts 4-byte word kk of row m at byte
-// m * 128 + ((kk / 4) xor (m mod 8)) * 16 + (kk mod 4) * 4.  The epilogue reads
-// the two 128 x N FP32 accumulators from tensor memory, stages each warp's rows
-// in shared memory and writes per-slice partial maps in whole row segments; a
-// second kernel sums the slices in a fixed order and folds the
-// per-class maxima (Eq. non-linearities needs the map maximum).  Every wait is
-// bounded: on time-out the CTA records VSAOGM_E_TIMEOUT, drains its MMAs, frees
-// its tensor memory and returns.
+// Pipeline per CTA (one CTA per SM): 16 producer warps generate the A operands
+// of stage s into one of two buffers while the tensor cores run stage s - 1
+// from the other; a loader warp stages the memories, frequencies and step
+// phasors of each stage ahead of the producers; a TMA warp copies the B
+// operand of each stage into a ring of four slots; an MMA warp issues the
+// stage's MMAs (2 K-steps x row blocks x 2 classes x 3 products) and commits
+// them to the buffers' mbarriers.  The warps hand stages over through
+// mbarriers only.  The epilogue reads the FP32 accumulators from tensor memory
+// in 16-column chunks, stages them in shared memory and writes per-slice
+// partial maps in whole row segments; a second kernel sums the slices in a
+// fixed order and folds the per-class maxima (Eq. non-linearities needs the
+// map maximum).  Every wait is bounded: on time-out the CTA records
+// VSAOGM_E_TIMEOUT, drains its MMAs and copies, frees its tensor memory and
+// returns.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
@@ -220,14 +226,15 @@ __host__ __device__ constexpr uint32_t idesc_of(int N)
 }
 
 // One (block of cells, frequency slice) item, executed by the whole CTA: 16
-// producer warps generate the operands, one warp issues the MMAs and one warp
-// stages each stage's inputs.  The block's columns lie in tile column b.tile;
-// its rows may cross tile rows (at most max_block_tiles(P) of them), each row
-// using the memories of its own tile: row j of the A operand is U_psi of tile
-// (row_tile[j], b.tile).  A block has rb = 1 or 2 row blocks of up to 128
-// rows (rows j0 .. j0 + 127 and j0 + 128 .. j1 - 1) and N <= 256 / rb columns:
-// the tensor memory holds rb x 2 classes accumulators of N columns, and the B
-// operand (the x phasors) is shared by all of them.
+// producer warps generate the A operands, one warp stages each stage's inputs,
+// one copies the B operand by TMA and one issues the MMAs.  The block's columns
+// lie in tile column b.tile; its rows may cross tile rows (at most
+// max_block_tiles(P) of them), each row using the memories of its own tile:
+// row j of the A operand is U_psi of tile (row_tile[j], b.tile).  A block has
+// rb = 1 or 2 row blocks of up to 128 rows (rows j0 .. j0 + 127 and j0 + 128 ..
+// j1 - 1) and N <= 256 / rb columns: the tensor memory holds rb x 2 classes
+// accumulators of N columns, and the B operand (the x phasors) is shared by
+// all of them.
 //
 // Hand-offs, all through mbarriers (no CTA-wide barrier inside the loop):
 //  * the loader warp copies stage s's inputs (the memories of the block's
@@ -236,21 +243,25 @@ __host__ __device__ constexpr uint32_t idesc_of(int N)
 //    aux_full[buf]; it refills buf for stage s + 2 once every producer warp
 //    has arrived on full_bar[buf] for stage s (they read the aux area before
 //    arriving);
+//  * the TMA warp copies stage s's B tiles (hi and lo) from the x-phasor
+//    table into slot s mod 4, completing on b_full[slot]; it refills the slot
+//    for stage s + 4 once the MMAs of stage s have completed (b_empty[slot]);
 //  * producers wait on aux_full[buf] and, from stage 2 on, on empty_bar[buf]
-//    (the tensor cores have finished reading buf), generate stage s and
-//    arrive on full_bar[buf] (one arrival per warp, after a proxy fence);
-//  * the MMA warp waits on full_bar[buf], issues the stage's MMAs and
-//    commits them to empty_bar[buf].
+//    (the tensor cores have finished reading buf), generate stage s's A
+//    operands and arrive on full_bar[buf] (one arrival per warp, after a
+//    proxy fence);
+//  * the MMA warp waits on full_bar[buf] and b_full[slot], issues the stage's
+//    MMAs and commits them to empty_bar[buf] and b_empty[slot].
 // Producer warps therefore drift apart by up to a stage instead of meeting
 // at a barrier every stage.  Every wait is bounded; after a time-out the CTA
-// stops waiting, records VSAOGM_E_TIMEOUT, drains its MMAs and frees its
-// tensor memory.
+// stops waiting, records VSAOGM_E_TIMEOUT, drains its MMAs and TMA copies and
+// frees its tensor memory.
 //
 // Producer thread (warp w, lane l) owns word l mod 16 of every operand row it
 // writes (frequencies FPL (l mod 16) .. + FPL - 1 of the stage, FPL = 1 for
-// 16-bit operands, 2 for FP8), and the rows and columns 2 w + l / 16 + 32 q:
-// their 64-byte swizzle phase ((row / 2) mod 4) is w mod 4 for every q.  Each
-// thread carries the two classes' operand values of a row as packed pairs,
+// 16-bit operands, 2 for FP8), and the rows 2 w + l / 16 + 32 q: their 64-byte
+// swizzle phase ((row / 2) mod 4) is w mod 4 for every q.  Each thread
+// carries the two classes' operand values of a row as packed pairs,
 // (Re U_0, Re U_1) and (-Im U_0, -Im U_1), so one packed multiply-add
 // advances both classes.
 template <int P>
