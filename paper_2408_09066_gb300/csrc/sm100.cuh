@@ -93,10 +93,15 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, uint64
 template <int bytes>
 __device__ __forceinline__ void cp_async(void *dst_smem, const void *src, bool valid)
 {
-    static_assert(bytes == 4 || bytes == 8, "cp.async.ca copies 4, 8 or 16 bytes");
-    asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;" ::"r"(smem_addr(dst_smem)),
-                 "l"(src), "n"(bytes), "r"(valid ? bytes : 0)
-                 : "memory");
+    static_assert(bytes == 4 || bytes == 8 || bytes == 16, "cp.async copies 4, 8 or 16 bytes");
+    if (bytes == 16)  // 16-byte copies bypass L1 (both addresses 16-byte aligned)
+        asm volatile("cp.async.cg.shared.global [%0], [%1], %2, %3;" ::"r"(smem_addr(dst_smem)),
+                     "l"(src), "n"(bytes), "r"(valid ? bytes : 0)
+                     : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;" ::"r"(smem_addr(dst_smem)),
+                     "l"(src), "n"(bytes), "r"(valid ? bytes : 0)
+                     : "memory");
 }
 
 // Arrives on *bar once every cp.async this thread issued before has landed
@@ -204,6 +209,22 @@ __device__ __forceinline__ void tmem_ld_32x32b_x16(uint32_t taddr, float (&v)[16
     for (int q = 0; q < 16; ++q) v[q] = __uint_as_float(r[q]);
 }
 
+// 32 lanes x 32 bits x 8 consecutive columns: thread t of the warp writes
+// row (lane base + t), columns [col, col + 8).  Completion is waited for by
+// tmem_wait_st().
+__device__ __forceinline__ void tmem_st_32x32b_x8(uint32_t taddr, const uint32_t (&v)[8])
+{
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"r"(taddr),
+        "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7])
+        : "memory");
+}
+
+__device__ __forceinline__ void tmem_wait_st()
+{
+    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+}
+
 // ------------------------------------------------------------ descriptors
 // Shared-memory matrix descriptor for a K-major operand stored with the
 // 128-byte swizzle: rows of 128 bytes (64 16-bit elements), 8-row atoms of
@@ -261,6 +282,31 @@ __device__ __forceinline__ void mma_f8f6f4(uint32_t d_tmem, uint64_t a_desc, uin
         "setp.ne.b32 p, %4, 0;\n\t"
         "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
         "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+// The same two MMAs with the A operand in tensor memory (M = 128 lanes, K
+// along the columns: 32 bytes of a row per 32-bit column group of 8) and B in
+// shared memory.
+__device__ __forceinline__ void mma_f16_ta(uint32_t d_tmem, uint32_t a_tmem, uint64_t b_desc,
+                                           uint32_t idesc, uint32_t accumulate)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "r"(a_tmem), "l"(b_desc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_f8f6f4_ta(uint32_t d_tmem, uint32_t a_tmem, uint64_t b_desc,
+                                              uint32_t idesc, uint32_t accumulate)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "r"(a_tmem), "l"(b_desc), "r"(idesc), "r"(accumulate)
         : "memory");
 }
 
