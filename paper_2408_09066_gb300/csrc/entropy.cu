@@ -18,6 +18,7 @@
 #include <utility>
 
 #include "internal.cuh"
+#include "sm100.cuh"
 
 namespace vsaogm_impl {
 namespace {
@@ -174,29 +175,32 @@ __host__ __device__ constexpr int disk_hw(int r, int dy)
 }
 
 // Disk sums of four vertically adjacent output cells of one column, rows
-// ly0 .. ly0 + 3.  Staged row ly0 + T (T in [-R, R + 3]) enters output row Q at
-// offset dy = T - Q with the disk's half-width w at dy, as the difference of
-// two running sums; `base` points at the column of output row ly0.  Offsets
-// and half-widths are template constants, so a (row, half-width) difference
-// that several of the four outputs share is loaded once.
+// ly0 .. ly0 + 3, for both classes at once (the staged sums are float pairs:
+// class 0, class 1).  Staged row ly0 + T (T in [-R, R + 3]) enters output row
+// Q at offset dy = T - Q with the disk's half-width w at dy, as the difference
+// of two running sums; `base` points at the column of output row ly0.
+// Offsets and half-widths are template constants, so a (row, half-width)
+// difference that several of the four outputs share is loaded once.
 template <int R, int PITCH, int T, int Q>
-__device__ __forceinline__ void disk_term(const float *base, float (&h)[4])
+__device__ __forceinline__ void disk_term(const float2 *base, sm100::f32x2 (&h)[4])
 {
+    using namespace sm100;
     constexpr int dy = T - Q;
     if constexpr (dy >= -R && dy <= R) {
         constexpr int w = disk_hw(R, dy);
         static_assert(w >= 0, "rows of the disk only");
-        h[Q] += base[T * PITCH + w + 1] - base[T * PITCH - w];
+        const float2 hi = base[T * PITCH + w + 1], lo = base[T * PITCH - w];
+        h[Q] = add2(h[Q], sub2(pack2(hi.x, hi.y), pack2(lo.x, lo.y)));
     }
 }
 template <int R, int PITCH, int T, int... Q>
-__device__ __forceinline__ void disk_row4(const float *base, float (&h)[4],
+__device__ __forceinline__ void disk_row4(const float2 *base, sm100::f32x2 (&h)[4],
                                           std::integer_sequence<int, Q...>)
 {
     (disk_term<R, PITCH, T, Q>(base, h), ...);
 }
 template <int R, int PITCH, int... I>
-__device__ __forceinline__ void disk_sum4(const float *base, float (&h)[4],
+__device__ __forceinline__ void disk_sum4(const float2 *base, sm100::f32x2 (&h)[4],
                                           std::integer_sequence<int, I...>)
 {
     (disk_row4<R, PITCH, I - R>(base, h, std::make_integer_sequence<int, 4>{}), ...);
@@ -206,10 +210,12 @@ constexpr int kEntThreads = 256;  // threads per entropy CTA (8 warps)
 
 // The entropy stencil for the common case of one disk radius R (<= 8) for
 // both classes: the same computation as entropy_body with every loop bound,
-// staged extent and disk half-width known at compile time.  Staging walks the
-// (32 + 2R)^2 staged cells of both classes as one flat range (no lane idles on
-// a row's ragged end), and each thread sums the disks of four vertically
-// adjacent cells of one column, so the disk rows they share are read once.
+// staged extent and disk half-width known at compile time, and both classes
+// carried together as float pairs in shared memory and in packed f32x2
+// arithmetic (one instruction does each step for both).  Staging walks the
+// (32 + 2R)^2 staged cells as one flat range (no lane idles on a row's ragged
+// end), and each thread sums the disks of four vertically adjacent cells of
+// one column, so the disk rows they share are read once.
 template <int R>
 __device__ __forceinline__ void entropy_fixed_body(const float *__restrict__ heat, int W, int H,
                                                    int wx0, int wy0, int ww, int wh, int raw,
@@ -218,11 +224,13 @@ __device__ __forceinline__ void entropy_fixed_body(const float *__restrict__ hea
                                                    float *__restrict__ occ,
                                                    float *__restrict__ ogm,
                                                    uint8_t *__restrict__ cls, int bx0, int by0,
-                                                   float *sh)
+                                                   float *shf)
 {
+    using namespace sm100;
     constexpr int E = kTB + 2 * R, PITCH = E + 1, EE = E * E;
     constexpr int SLOTS = (EE + kEntThreads - 1) / kEntThreads;
     static_assert(kTB == 32 && kEntThreads == 256, "8 warps of 4 output rows each");
+    float2 *sh = reinterpret_cast<float2 *>(shf);  // [E][PITCH] pairs (class 0, class 1)
     const int x0 = wx0 + bx0, y0 = wy0 + by0;
     float inv[2] = {1.f, 1.f};
     const bool norm = raw && !(mode & VSAOGM_MODE_NO_NORM);
@@ -233,71 +241,92 @@ __device__ __forceinline__ void entropy_fixed_body(const float *__restrict__ hea
             inv[c] = m > 0.f ? 1.0f / m : 0.f;
         }
     }
+    const f32x2 INV = pack2(inv[0], inv[1]);
+    const f32x2 kNegLn2 = pack2(-0.69314718055994531f, -0.69314718055994531f);
     const size_t cells = (size_t)W * H;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    // Stage: staged cell e = ly * E + lx of both classes; every load of the
-    // thread is issued before any is used.  Off-grid cells read as 0, whose
-    // summand is 0.
+    // Stage: staged cell e = ly * E + lx; every load of the thread is issued
+    // before any is used.  Off-grid cells read as 0, whose summand is 0; when
+    // the whole staged square lies inside the grid (most blocks of a large
+    // map) no cell needs that test.
     float v0[SLOTS], v1[SLOTS];
+    int so[SLOTS];  // the cell's pair in shared memory
+    const bool inside = x0 - R >= 0 && y0 - R >= 0 && x0 - R + E <= W && y0 - R + E <= H;
+    if (inside) {
+        const float *g0 = heat + ((size_t)(y0 - R) * W + (x0 - R));
+        const float *g1 = g0 + cells;
 #pragma unroll
-    for (int i = 0; i < SLOTS; ++i) {
-        const int e = tid + kEntThreads * i;
-        const int ly = e / E, lx = e - ly * E;
-        const int y = y0 - R + ly, x = x0 - R + lx;
-        const bool ok = e < EE && x >= 0 && x < W && y >= 0 && y < H;
-        const size_t g = (size_t)y * W + x;
-        v0[i] = ok ? __ldg(heat + g) : 0.f;
-        v1[i] = ok ? __ldg(heat + cells + g) : 0.f;
-    }
-#pragma unroll
-    for (int i = 0; i < SLOTS; ++i) {
-        const int e = tid + kEntThreads * i;
-        if (e < EE) {
+        for (int i = 0; i < SLOTS; ++i) {
+            const int e = tid + kEntThreads * i;
             const int ly = e / E, lx = e - ly * E;
-            float a = v0[i], b = v1[i];
-            if (norm) {
-                a *= inv[0];
-                b *= inv[1];
-            }
-            if (square) {
-                a = a * a;
-                b = b * b;
-            }
-            sh[ly * PITCH + 1 + lx] = a > 0.f ? -a * __logf(a) : 0.f;
-            sh[(E + ly) * PITCH + 1 + lx] = b > 0.f ? -b * __logf(b) : 0.f;
+            const bool ok = (i + 1) * kEntThreads <= EE || e < EE;
+            const int off = ly * W + lx;
+            v0[i] = ok ? __ldg(g0 + off) : 0.f;
+            v1[i] = ok ? __ldg(g1 + off) : 0.f;
+            so[i] = ok ? ly * PITCH + 1 + lx : -1;
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < SLOTS; ++i) {
+            const int e = tid + kEntThreads * i;
+            const int ly = e / E, lx = e - ly * E;
+            const int y = y0 - R + ly, x = x0 - R + lx;
+            const bool ok = e < EE && x >= 0 && x < W && y >= 0 && y < H;
+            const size_t g = (size_t)y * W + x;
+            v0[i] = ok ? __ldg(heat + g) : 0.f;
+            v1[i] = ok ? __ldg(heat + cells + g) : 0.f;
+            so[i] = e < EE ? ly * PITCH + 1 + lx : -1;
         }
     }
-    if (tid < 2 * E) sh[tid * PITCH] = 0.f;
+#pragma unroll
+    for (int i = 0; i < SLOTS; ++i) {
+        if (so[i] >= 0) {
+            f32x2 a = pack2(v0[i], v1[i]);
+            if (norm) a = mul2(a, INV);
+            if (square) a = mul2(a, a);
+            // -a ln a = a log2(a) (-ln 2), 0 for a <= 0 (Eq. entropy summand)
+            const float2 af = unpack2(a);
+            const float2 h = unpack2(mul2(mul2(a, pack2(__log2f(af.x), __log2f(af.y))), kNegLn2));
+            sh[so[i]] = make_float2(af.x > 0.f ? h.x : 0.f, af.y > 0.f ? h.y : 0.f);
+        }
+    }
+    if (tid < E) sh[tid * PITCH] = make_float2(0.f, 0.f);
     __syncthreads();
-    if (tid < 2 * E) {
-        float *row = sh + tid * PITCH + 1;
-        float acc = 0.f;
+    // running sums along each staged row, one thread per row
+    if (tid < E) {
+        float2 *row = sh + tid * PITCH + 1;
+        f32x2 acc = pack2(0.f, 0.f);
 #pragma unroll
         for (int lx = 0; lx < E; ++lx) {
-            acc += row[lx];
-            row[lx] = acc;
+            const float2 t = row[lx];
+            acc = add2(acc, pack2(t.x, t.y));
+            row[lx] = unpack2(acc);
         }
     }
     __syncthreads();
     const int ly0 = 4 * warp;
-    float Hc[2][4] = {};
+    f32x2 Hc[4];
 #pragma unroll
-    for (int c = 0; c < 2; ++c)
-        disk_sum4<R, PITCH>(sh + (c * E + R + ly0) * PITCH + R + lane, Hc[c],
-                            std::make_integer_sequence<int, 2 * R + 4>{});
+    for (int q = 0; q < 4; ++q) Hc[q] = pack2(0.f, 0.f);
+    disk_sum4<R, PITCH>(sh + (R + ly0) * PITCH + R + lane, Hc,
+                        std::make_integer_sequence<int, 2 * R + 4>{});
     const int x = bx0 + lane;
+    // Eq. softmax for two classes: Pr(psi = 1) = 1 / (1 + e^(H0 - H1)) and
+    // Pr(psi = 0) = 1 - Pr(psi = 1), so the signed difference of Eq. psd is
+    // 2 Pr(psi = 1) - 1; then Eq. classification
+    float *occ_row = occ + ((size_t)(by0 + ly0) * ww + x);
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
         const int y = by0 + ly0 + q;
         if (x >= ww || y >= wh) continue;
-        const float pr1 = __fdividef(1.0f, 1.0f + __expf(Hc[0][q] - Hc[1][q]));
-        const float pr0 = __fdividef(1.0f, 1.0f + __expf(Hc[1][q] - Hc[0][q]));
-        const size_t o = (size_t)y * ww + x;
-        if (!VSAOGM_IN_BOUNDS(o < (size_t)ww * wh)) continue;
-        occ[o] = pr1;
-        const float d = pr1 - pr0;
-        if (ogm) ogm[o] = d;
-        if (cls) cls[o] = d >= rho ? 1 : 0;
+        const float2 hq = unpack2(Hc[q]);
+        const float pr1 = __fdividef(1.0f, 1.0f + __expf(hq.x - hq.y));
+        const float d = fmaf(2.0f, pr1, -1.0f);
+        const int o = q * ww;  // from the thread's first output cell
+        if (!VSAOGM_IN_BOUNDS((size_t)y * ww + x < (size_t)ww * wh)) continue;
+        occ_row[o] = pr1;
+        if (ogm) ogm[(occ_row - occ) + o] = d;
+        if (cls) cls[(occ_row - occ) + o] = d >= rho ? 1 : 0;
     }
 }
 
