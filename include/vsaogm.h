@@ -231,6 +231,18 @@ int vsaogm_query_window(vsaogm_map *map, int32_t x0, int32_t y0, int32_t w, int3
                         float *heat_dev, float *occ_dev, float *ogm_dev, uint8_t *cls_dev,
                         void *stream);
 
+/* Decoded map of the window of cells [x0, x0 + w) x [y0, y0 + h): Eqs.
+ * vector-normalization, loc-query and non-linearities restricted to the
+ * window.  heat_dev (float [2][h][w], row stride w) receives P_hat of both
+ * classes.  The maximum of Eq. non-linearities is the window's own (a local
+ * decode normalises by what it decodes; for the whole map this equals
+ * vsaogm_decode), or, with VSAOGM_FLAG_WINDOW_MAP_MAX, the whole map's, as the
+ * paper defines it: the whole map is then decoded into library-owned scratch
+ * as vsaogm_query_window does, and the window's cells equal the same cells of
+ * vsaogm_decode.  Errors: E_INVAL (window not inside the map, NULL), E_CUDA.  */
+int vsaogm_decode_window(vsaogm_map *map, int32_t x0, int32_t y0, int32_t w, int32_t h,
+                         float *heat_dev, void *stream);
+
 /* Floats of heat scratch vsaogm_query_window needs for that window.
  * No counterpart in the paper: a service of the library.
  * Errors: E_INVAL (NULL, window not inside the map). */

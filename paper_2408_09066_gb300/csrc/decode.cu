@@ -362,10 +362,10 @@ int sum_slices(vsaogm_map *m, const float *partial, int splits, size_t cells, fl
     return e == cudaSuccess ? VSAOGM_OK : cuda_error(e, "decode: slice sum");
 }
 
-int apply_nonlinearity(vsaogm_map *m, float *heat, cudaStream_t st)
+int apply_nonlinearity(vsaogm_map *m, float *heat, cudaStream_t st, size_t cells)
 {
     StageScope sc(m, VSAOGM_STAGE_NONLINEAR, st);
-    size_t cells = (size_t)m->cfg.grid_w * m->cfg.grid_h;
+    if (cells == 0) cells = (size_t)m->cfg.grid_w * m->cfg.grid_h;
     int blocks = (int)std::min<size_t>((2 * cells + 255) / 256, 152 * 16);
     nonlinear_kernel<<<blocks, 256, 0, st>>>(heat, cells, m->maxima, m->cfg.decode_mode);
     cudaError_t e = cudaGetLastError();

@@ -357,7 +357,8 @@ void region_blocks(const vsaogm_map *m, Region r, int bi, int bj, std::vector<De
 // P over region r into heat [2][r.h()][r.w()], and the maxima over r
 int decode_region(vsaogm_map *m, Region r, float *heat, cudaStream_t st);
 inline int decode_raw(vsaogm_map *m, float *heat, cudaStream_t st);
-int apply_nonlinearity(vsaogm_map *m, float *heat, cudaStream_t st); // P -> P_hat in place
+int apply_nonlinearity(vsaogm_map *m, float *heat, cudaStream_t st,
+                       size_t cells = 0);  // P -> P_hat in place ([2][cells]; 0: the map)
 int memory_norms(vsaogm_map *m, cudaStream_t st);
 // heat = inv_scale * sum over `splits` partial maps [splits][2][cells], plus maxima
 int sum_slices(vsaogm_map *m, const float *partial, int splits, size_t cells, float inv_scale,

@@ -603,6 +603,40 @@ int vsaogm_query_window(vsaogm_map *m, int32_t x0, int32_t y0, int32_t w, int32_
     return entropy(m, mh, full_region(m), win, true, occ, ogm, cls, st);
 }
 
+int vsaogm_decode_window(vsaogm_map *m, int32_t x0, int32_t y0, int32_t w, int32_t h,
+                         float *heat, void *stream)
+{
+    alloc_scope_begin();
+    int64_t need;
+    VSA_TRY(vsaogm_window_scratch(m, x0, y0, w, h, &need));
+    if (!heat) return set_error(VSAOGM_E_INVAL, "heat must not be NULL");
+    const Region win{x0, y0, x0 + w, y0 + h};
+    const size_t cells = (size_t)w * h;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (!(m->cfg.flags & VSAOGM_FLAG_WINDOW_MAP_MAX)) {
+        // P of the window, its per-class maxima, then the non-linearity by them
+        VSA_TRY(decode_region(m, win, heat, st));
+        return apply_nonlinearity(m, heat, st, cells);
+    }
+    // the whole map's P and maxima, decoded again only when the memories have
+    // changed since; the window's cells are copied out and normalised by the
+    // map's maxima
+    const size_t W = m->cfg.grid_w, H = m->cfg.grid_h;
+    VSA_TRY(ensure(m->ws.map_heat, sizeof(float) * 2 * W * H));
+    float *mh = (float *)m->ws.map_heat.ptr;
+    if (m->map_heat_gen != m->mem_gen) {
+        m->map_heat_gen = ~0ull;
+        VSA_TRY(decode_raw(m, mh, st));
+        m->map_heat_gen = m->mem_gen;
+    }
+    for (int c = 0; c < 2; ++c)
+        VSA_CUDA(cudaMemcpy2DAsync(heat + (size_t)c * cells, sizeof(float) * w,
+                                   mh + c * W * H + (size_t)y0 * W + x0, sizeof(float) * W,
+                                   sizeof(float) * w, h, cudaMemcpyDeviceToDevice, st),
+                 "decode_window");
+    return apply_nonlinearity(m, heat, st, cells);
+}
+
 int vsaogm_update_query_host(vsaogm_map *m, const float *xy_host, const uint8_t *lab_host,
                              int64_t n, float *occ_host, void *stream)
 {

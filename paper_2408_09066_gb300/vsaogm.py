@@ -61,6 +61,8 @@ _SIGNATURES = {
                                            ctypes.c_int32, _V, _V, _V, _V, _V]),
     "vsaogm_window_scratch": (ctypes.c_int, [_V, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                              ctypes.c_int32, _V]),
+    "vsaogm_decode_window": (ctypes.c_int, [_V, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                            ctypes.c_int32, _V, _V]),
     "vsaogm_rejected": (ctypes.c_int, [_V, _V, _V]),
     "vsaogm_reserve": (ctypes.c_int, [_V, ctypes.c_int64]),
     "vsaogm_get_memory": (ctypes.c_int, [_V, _V, _V]),
@@ -239,6 +241,13 @@ class Map:
             self._h, x0, y0, w, h, _V(heat.data_ptr()), _dev(occ, torch.float32, (h, w), "occ"),
             _dev(ogm, torch.float32, (h, w), "ogm") if ogm is not None else None,
             _dev(cls, torch.uint8, (h, w), "cls") if cls is not None else None, _stream(stream)))
+
+    def decode_window(self, x0: int, y0: int, w: int, h: int, heat, stream=None):
+        """P_hat of both classes for the window [x0, x0+w) x [y0, y0+h) into heat [2][h][w]."""
+        import torch
+        _check(lib().vsaogm_decode_window(self._h, x0, y0, w, h,
+                                          _dev(heat, torch.float32, (2, h, w), "heat"),
+                                          _stream(stream)))
 
     def update_query_host(self, xy: np.ndarray, labels: np.ndarray, occ: np.ndarray, stream=None):
         """Host arrays in and out: xy float32 [n][2], labels uint8 [n], occ float32 [H][W]."""

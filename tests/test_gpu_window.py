@@ -131,3 +131,72 @@ def test_map_max_windows_equal_the_map_query(prec):
                 rx1, ry1 = min(wl.W, x0 + ww + R), min(wl.H, y0 + hh + R)
                 P = wheat[:2 * (rx1 - rx0) * (ry1 - ry0)].view(2, ry1 - ry0, rx1 - rx0)
                 assert torch.equal(P, heat[:, ry0:ry1, rx0:rx1])
+
+
+@pytest.mark.parametrize("prec", [V.DECODE_FP32, V.DECODE_BF16X3])
+def test_decode_windows_match_oracle(prec):
+    """vsaogm_decode_window: P_hat of a window (Eqs. vector-normalization,
+    loc-query, non-linearities) normalised by the window's own per-class
+    maxima, against the oracle's decode of the same cells put through its
+    non-linearity; the whole map's window equals vsaogm_decode."""
+    import torch
+    wl = synth.small_scan(seed=82)
+    cfg = config_for(wl, tiles_x=2, tiles_y=2, decode_prec=prec)
+    dev = torch.device("cuda")
+    g = oracle_grid(cfg)
+    nx, ny = oracle.draw_nu(cfg.seed, cfg.D, float(np.float32(cfg.length_scale)))
+    om = oracle.memories(g, nx, ny, wl.xy, wl.labels, "tile")
+    with V.Map(cfg) as m:
+        m.encode_bundle(torch.from_numpy(wl.xy).to(dev), torch.from_numpy(wl.labels).to(dev))
+        for (x0, y0, w, h) in WINDOWS:
+            heat = torch.empty((2, h, w), dtype=torch.float32, device=dev)
+            m.decode_window(x0, y0, w, h, heat)
+            torch.cuda.synchronize()
+            m.status()
+            jj, ii = np.meshgrid(np.arange(y0, y0 + h), np.arange(x0, x0 + w), indexing="ij")
+            cells = np.stack([ii.ravel(), jj.ravel()], 1)
+            P = oracle.decode_cells(g, nx, ny, om, cells, "tile").T.reshape(2, h, w)
+            want, _ = oracle.nonlinear(P)
+            err = np.abs(heat.cpu().numpy() - want).max()
+            assert err <= 2e-4, (x0, y0, w, h, err)
+        full = torch.empty((2, wl.H, wl.W), dtype=torch.float32, device=dev)
+        m.decode(full)
+        whole = torch.empty((2, wl.H, wl.W), dtype=torch.float32, device=dev)
+        m.decode_window(0, 0, wl.W, wl.H, whole)
+        torch.cuda.synchronize()
+        assert torch.equal(full, whole)
+
+
+@pytest.mark.parametrize("prec", [V.DECODE_FP32, V.DECODE_BF16X3])
+def test_map_max_decode_windows_equal_the_map_decode(prec):
+    """With VSAOGM_FLAG_WINDOW_MAP_MAX a decoded window is normalised by the
+    whole map's maxima: bit for bit the same cells of vsaogm_decode, and after
+    more points are bundled the next window decodes the map again."""
+    import torch
+    wl = synth.small_scan(seed=83)
+    more = synth.small_scan(seed=84)
+    cfg = config_for(wl, tiles_x=2, tiles_y=2, decode_prec=prec, flags=V.FLAG_WINDOW_MAP_MAX)
+    dev = torch.device("cuda")
+    with V.Map(cfg) as m:
+        for w in (wl, more):
+            m.encode_bundle(torch.from_numpy(w.xy).to(dev), torch.from_numpy(w.labels).to(dev))
+            full = torch.empty((2, wl.H, wl.W), dtype=torch.float32, device=dev)
+            m.decode(full)
+            for (x0, y0, ww, hh) in WINDOWS:
+                heat = torch.empty((2, hh, ww), dtype=torch.float32, device=dev)
+                m.decode_window(x0, y0, ww, hh, heat)
+                torch.cuda.synchronize()
+                m.status()
+                assert torch.equal(heat, full[:, y0:y0 + hh, x0:x0 + ww]), (x0, y0, ww, hh)
+
+
+def test_decode_window_outside_the_map_is_rejected():
+    import torch
+    wl = synth.small_scan(seed=85)
+    dev = torch.device("cuda")
+    with V.Map(config_for(wl)) as m:
+        heat = torch.empty((2, 4, 4), dtype=torch.float32, device=dev)
+        for bad in [(-1, 0, 4, 4), (62, 0, 4, 4), (0, 61, 4, 4)]:
+            with pytest.raises(V.VsaogmError) as ei:
+                m.decode_window(*bad, heat)
+            assert ei.value.code == V.E_INVAL
