@@ -24,6 +24,15 @@ namespace vsaogm_impl {
 namespace {
 
 constexpr int kTB = 32;                       // output cells per block edge
+
+// Hardware log2 of a normal positive float (the approximate MUFU instruction,
+// subnormal inputs flushed; its callers never pass one).
+__device__ __forceinline__ float lg2_ftz(float x)
+{
+    float r;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
 constexpr int kSW = kTB + 2 * kMaxRadius;     // largest staged edge (64)
 
 struct DiskParams {
@@ -174,15 +183,17 @@ __host__ __device__ constexpr int disk_hw(int r, int dy)
     return w;
 }
 
-// Disk sums of four vertically adjacent output cells of one column, rows
-// ly0 .. ly0 + 3, for both classes at once (the staged sums are float pairs:
-// class 0, class 1).  Staged row ly0 + T (T in [-R, R + 3]) enters output row
-// Q at offset dy = T - Q with the disk's half-width w at dy, as the difference
-// of two running sums; `base` points at the column of output row ly0.
-// Offsets and half-widths are template constants, so a (row, half-width)
-// difference that several of the four outputs share is loaded once.
+// Disk sums of kRowsPerThread vertically adjacent output cells of one column,
+// rows ly0 .. ly0 + kRowsPerThread - 1, for both classes at once (the staged
+// sums are float pairs: class 0, class 1).  Staged row ly0 + T (T in [-R, R +
+// kRowsPerThread - 1]) enters output row Q at offset dy = T - Q with the
+// disk's half-width w at dy, as the difference of two running sums; `base`
+// points at the column of output row ly0.  Offsets and half-widths are
+// template constants, so a (row, half-width) difference that several of the
+// outputs share is loaded and formed once.
+constexpr int kRowsPerThread = 8;
 template <int R, int PITCH, int T, int Q>
-__device__ __forceinline__ void disk_term(const float2 *base, sm100::f32x2 (&h)[4])
+__device__ __forceinline__ void disk_term(const float2 *base, sm100::f32x2 (&h)[kRowsPerThread])
 {
     using namespace sm100;
     constexpr int dy = T - Q;
@@ -194,19 +205,21 @@ __device__ __forceinline__ void disk_term(const float2 *base, sm100::f32x2 (&h)[
     }
 }
 template <int R, int PITCH, int T, int... Q>
-__device__ __forceinline__ void disk_row4(const float2 *base, sm100::f32x2 (&h)[4],
-                                          std::integer_sequence<int, Q...>)
+__device__ __forceinline__ void disk_row(const float2 *base, sm100::f32x2 (&h)[kRowsPerThread],
+                                         std::integer_sequence<int, Q...>)
 {
     (disk_term<R, PITCH, T, Q>(base, h), ...);
 }
 template <int R, int PITCH, int... I>
-__device__ __forceinline__ void disk_sum4(const float2 *base, sm100::f32x2 (&h)[4],
+__device__ __forceinline__ void disk_sums(const float2 *base, sm100::f32x2 (&h)[kRowsPerThread],
                                           std::integer_sequence<int, I...>)
 {
-    (disk_row4<R, PITCH, I - R>(base, h, std::make_integer_sequence<int, 4>{}), ...);
+    (disk_row<R, PITCH, I - R>(base, h, std::make_integer_sequence<int, kRowsPerThread>{}), ...);
 }
 
-constexpr int kEntThreads = 256;  // threads per entropy CTA (8 warps)
+// threads per entropy CTA: 4 warps, each thread kRowsPerThread output rows of
+// one column of the 32 x 32 block
+constexpr int kEntThreads = 32 * (kTB / kRowsPerThread);
 
 // The entropy stencil for the common case of one disk radius R (<= 8) for
 // both classes: the same computation as entropy_body with every loop bound,
@@ -229,7 +242,8 @@ __device__ __forceinline__ void entropy_fixed_body(const float *__restrict__ hea
     using namespace sm100;
     constexpr int E = kTB + 2 * R, PITCH = E + 1, EE = E * E;
     constexpr int SLOTS = (EE + kEntThreads - 1) / kEntThreads;
-    static_assert(kTB == 32 && kEntThreads == 256, "8 warps of 4 output rows each");
+    static_assert(kTB == 32 && kEntThreads * kRowsPerThread == 32 * kTB,
+                  "each warp's lanes cover the block's 32 columns for kRowsPerThread rows");
     float2 *sh = reinterpret_cast<float2 *>(shf);  // [E][PITCH] pairs (class 0, class 1)
     const int x0 = wx0 + bx0, y0 = wy0 + by0;
     float inv[2] = {1.f, 1.f};
@@ -286,8 +300,18 @@ __device__ __forceinline__ void entropy_fixed_body(const float *__restrict__ hea
             if (square) a = mul2(a, a);
             // -a ln a = a log2(a) (-ln 2), 0 for a <= 0 (Eq. entropy summand)
             const float2 af = unpack2(a);
-            const float2 h = unpack2(mul2(mul2(a, pack2(__log2f(af.x), __log2f(af.y))), kNegLn2));
-            sh[so[i]] = make_float2(af.x > 0.f ? h.x : 0.f, af.y > 0.f ? h.y : 0.f);
+            if (square) {
+                // a >= 0: log2 of max(a, 2^-100) is finite, and for a = 0 the
+                // product is 0 (below 2^-100 the summand is under 1e-28 anyway)
+                const float2 h = unpack2(mul2(mul2(a, pack2(lg2_ftz(fmaxf(af.x, 7.9e-31f)),
+                                                            lg2_ftz(fmaxf(af.y, 7.9e-31f)))),
+                                              kNegLn2));
+                sh[so[i]] = h;
+            } else {
+                const float2 h =
+                    unpack2(mul2(mul2(a, pack2(__log2f(af.x), __log2f(af.y))), kNegLn2));
+                sh[so[i]] = make_float2(af.x > 0.f ? h.x : 0.f, af.y > 0.f ? h.y : 0.f);
+            }
         }
     }
     if (tid < E) sh[tid * PITCH] = make_float2(0.f, 0.f);
@@ -304,19 +328,19 @@ __device__ __forceinline__ void entropy_fixed_body(const float *__restrict__ hea
         }
     }
     __syncthreads();
-    const int ly0 = 4 * warp;
-    f32x2 Hc[4];
+    const int ly0 = kRowsPerThread * warp;
+    f32x2 Hc[kRowsPerThread];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) Hc[q] = pack2(0.f, 0.f);
-    disk_sum4<R, PITCH>(sh + (R + ly0) * PITCH + R + lane, Hc,
-                        std::make_integer_sequence<int, 2 * R + 4>{});
+    for (int q = 0; q < kRowsPerThread; ++q) Hc[q] = pack2(0.f, 0.f);
+    disk_sums<R, PITCH>(sh + (R + ly0) * PITCH + R + lane, Hc,
+                        std::make_integer_sequence<int, 2 * R + kRowsPerThread>{});
     const int x = bx0 + lane;
     // Eq. softmax for two classes: Pr(psi = 1) = 1 / (1 + e^(H0 - H1)) and
     // Pr(psi = 0) = 1 - Pr(psi = 1), so the signed difference of Eq. psd is
     // 2 Pr(psi = 1) - 1; then Eq. classification
     float *occ_row = occ + ((size_t)(by0 + ly0) * ww + x);
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
+    for (int q = 0; q < kRowsPerThread; ++q) {
         const int y = by0 + ly0 + q;
         if (x >= ww || y >= wh) continue;
         const float2 hq = unpack2(Hc[q]);
