@@ -48,13 +48,14 @@ MUFU_PER_SM_CLK = 16          # sin/cos ops per SM per clock (measured 15.2 at m
 FP32_FMA_PER_SM_CLK = 128
 # FMA-pipe lane-ops per complex exponential in encode_chunk_x2_kernel (counted
 # from its code) for chunks whose phases stay below 4 turns, which bundling
-# patches make every chunk inside the map: phase 2 (mul, fma) + 2 pi scale 1 +
-# MUFU argument scaling 1 + accumulate 2, no reduction (MUFU's own costs it
-# less than 5e-6 rad there); polynomial path: phase with reduction 5 +
-# half-angle Taylor and complex square 19 + accumulate 2.  Chunks beyond 4
-# turns (points outside the map, or patches capped by the segment limit)
-# reduce first: 9 lane-ops on the MUFU path.
-MUFU_PATH_FMA = 6
+# patches make every chunk inside the map: phase 2 (mul, fma; the frequencies
+# come pre-scaled by 2 pi, once per chunk) + MUFU argument scaling 1 +
+# accumulate 2, no reduction (MUFU's own costs it less than 5e-6 rad there);
+# polynomial path: phase with reduction 5 + half-angle Taylor and complex
+# square 19 + accumulate 2.  Chunks beyond 4 turns (points outside the map, or
+# patches capped by the segment limit) reduce first: 9 lane-ops on the MUFU
+# path.
+MUFU_PATH_FMA = 5
 POLY_PATH_FMA = 26
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 CLOCK_FIELDS = ("index,pci.bus_id,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -376,7 +377,7 @@ DATA = ("synthetic: seeded 100-scan lidar trajectory in a walled 40 m world with
 # DRAM traffic of one encode launch on this workload from an ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum = 25.38 MB + 114.57 MB), valid
 # only for the kernel source it was taken on (sha1 of csrc/encode.cu).
-ENCODE_TRAFFIC = {"sha1": "9232b331fa1b503db4a92451303ac68dcf922fdb", "bytes": 139954176}
+ENCODE_TRAFFIC = {"sha1": "df79b1531151e419358283f2fa36bfb2aba12fd4", "bytes": 139911424}
 
 
 def data_of(name: str, wl) -> str:

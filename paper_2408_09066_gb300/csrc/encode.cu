@@ -643,25 +643,35 @@ __device__ __forceinline__ void encode_points_x2(const float2 *sp, int len,
     const f32x2 c8 = pack2(1.0f / 40320.0f, 1.0f / 40320.0f);
     const f32x2 c10 = pack2(-1.0f / 3628800.0f, -1.0f / 3628800.0f);
     const f32x2 c12 = pack2(1.0f / 479001600.0f, 1.0f / 479001600.0f);
+    // Tier 0's MUFU pairs take the phase in radians straight from frequencies
+    // scaled by 2 pi once per chunk (one multiply per exponential fewer); the
+    // polynomial pairs and the reducing tiers keep turns.
+    f32x2 rx[NP], ry[NP];
+#pragma unroll
+    for (int j = 0; j < NP; ++j) {
+        const bool rad = TIER == 0 && j >= NPOLY;
+        rx[j] = rad ? mul2(nx[j], kTwoPi) : nx[j];
+        ry[j] = rad ? mul2(ny[j], kTwoPi) : ny[j];
+    }
 #pragma unroll 2
     for (int p = 0; p < len; ++p) {
         const float2 q = sp[p];
         const f32x2 qx = pack2(q.x, q.x), qy = pack2(q.y, q.y);
 #pragma unroll
         for (int j = 0; j < NP; ++j) {
-            f32x2 p2 = mul2(ny[j], qy);
+            f32x2 p2 = mul2(ry[j], qy);
             f32x2 f, t;
             if (TIER == 2) {
                 // as encode_points: f_i = fl(nu_i d_i - rint(p_i)) with one FMA
-                f32x2 p1 = mul2(nx[j], qx);
+                f32x2 p1 = mul2(rx[j], qx);
                 f32x2 n1 = sub2(kM, add2(p1, kM)), n2 = sub2(kM, add2(p2, kM));
-                f32x2 g = add2(fma2(nx[j], qx, n1), fma2(ny[j], qy, n2));
+                f32x2 g = add2(fma2(rx[j], qx, n1), fma2(ry[j], qy, n2));
                 f = sub2(g, sub2(add2(g, kM), kM));
             } else {
                 // t = nu_x dx + nu_y dy with one rounding of the sum (FMA);
                 // t - rint(t) is exact.  Error at most ulp(64)/2 + ulp(32)/2
                 // = 2.9e-6 turns for |t| < 64 (3.6e-7 for |t| < 8).
-                t = fma2(nx[j], qx, p2);
+                t = fma2(rx[j], qx, p2);
                 if (TIER == 1 || j < NPOLY) f = sub2(t, sub2(add2(t, kM), kM));
             }
             f32x2 cr, si;
@@ -682,7 +692,8 @@ __device__ __forceinline__ void encode_points_x2(const float2 *sp, int len,
                 cr = mul2(sub2(c, s), add2(c, s));  // cos 2x = (c - s)(c + s)
                 si = mul2(add2(c, c), s);           // sin 2x = 2 c s
             } else {
-                float2 a = unpack2(mul2(TIER == 0 ? t : f, kTwoPi));
+                // tier 0: t is already in radians
+                float2 a = unpack2(TIER == 0 ? t : mul2(f, kTwoPi));
                 float s0, c0, s1, c1;
                 __sincosf(a.x, &s0, &c0);
                 __sincosf(a.y, &s1, &c1);
@@ -775,7 +786,12 @@ __device__ __forceinline__ void encode_chunk_x2_body(const float2 *__restrict__ 
 #pragma unroll
     for (int j = 0; j < NP; ++j) {
         const float2 cr = unpack2(ac[j]), si = unpack2(as[j]);
-        const float2 vx = unpack2(nx[j]), vy = unpack2(ny[j]);
+        // the frequencies again, from memory (registers held no turn-valued
+        // copy of the MUFU pairs through the point loop)
+        const int k0 = kbase + (2 * j) * 256, k1 = k0 + 256;
+        const float2 vx = make_float2(k0 < D ? __ldg(nu + k0) : 0.f, k1 < D ? __ldg(nu + k1) : 0.f);
+        const float2 vy = make_float2(k0 < D ? __ldg(nu + D + k0) : 0.f,
+                                      k1 < D ? __ldg(nu + D + k1) : 0.f);
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
             int k = kbase + (2 * j + h) * 256;
