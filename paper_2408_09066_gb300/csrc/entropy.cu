@@ -227,8 +227,8 @@ constexpr int kEntThreads = 32 * (kTB / kRowsPerThread);
 // carried together as float pairs in shared memory and in packed f32x2
 // arithmetic (one instruction does each step for both).  Staging walks the
 // (32 + 2R)^2 staged cells as one flat range (no lane idles on a row's ragged
-// end), and each thread sums the disks of four vertically adjacent cells of
-// one column, so the disk rows they share are read once.
+// end), and each thread sums the disks of kRowsPerThread vertically adjacent
+// cells of one column, so the disk rows they share are read once.
 template <int R>
 __device__ __forceinline__ void entropy_fixed_body(const float *__restrict__ heat, int W, int H,
                                                    int wx0, int wy0, int ww, int wh, int raw,
