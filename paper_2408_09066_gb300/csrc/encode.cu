@@ -238,6 +238,42 @@ __device__ __forceinline__ void seg_meta_body(int *__restrict__ meta, int S, int
             chunks[cbeg[s] + c] = make_int4(s, b, min(b + chunk, base[s] + total[s]), 0);
         }
     }
+    // Launch order, in the table's spare field: entry i's .w is the chunk the
+    // encode's i-th CTA (or work item) takes.  Full chunks come first, then the
+    // partial ones by length, longest first (in buckets of 1/32 of the chunk
+    // length), so a launch ends on its shortest chunks instead of on whichever
+    // chunks the segment order puts last.  Inside a bucket the order is
+    // whatever the atomics give: a chunk's partial memory goes to its own slot
+    // whenever it runs, so no result depends on it.
+    __shared__ int ocnt[33];
+    __syncthreads();  // every entry above is written before its .w is
+    if (threadIdx.x < 33) ocnt[threadIdx.x] = 0;
+    __syncthreads();
+    for (int s = threadIdx.x; s < S; s += blockDim.x) {
+        const int nc = (total[s] + chunk - 1) / chunk;
+        for (int c = 0; c < nc; ++c) {
+            const int sz = min(chunk, total[s] - c * chunk);
+            atomicAdd(&ocnt[sz >= chunk ? 32 : (int)((long long)sz * 32 / chunk)], 1);
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int run = 0;
+        for (int bk = 32; bk >= 0; --bk) {
+            const int n = ocnt[bk];
+            ocnt[bk] = run;
+            run += n;
+        }
+    }
+    __syncthreads();
+    for (int s = threadIdx.x; s < S; s += blockDim.x) {
+        const int nc = (total[s] + chunk - 1) / chunk;
+        for (int c = 0; c < nc; ++c) {
+            const int sz = min(chunk, total[s] - c * chunk);
+            const int pos = atomicAdd(&ocnt[sz >= chunk ? 32 : (int)((long long)sz * 32 / chunk)], 1);
+            chunks[pos].w = cbeg[s] + c;
+        }
+    }
 }
 
 __global__ void __launch_bounds__(kScanThreads) seg_meta_kernel(int *__restrict__ meta, int S,
@@ -870,8 +906,11 @@ __global__ void __launch_bounds__(256) encode_chunk_x2_kernel(const float2 *__re
     __shared__ float2 sp[kMaxChunk];
     __shared__ unsigned s_bound[2];
     __shared__ int s_tail[3];
-    const int c = blockIdx.x;
-    if (c >= *n_chunks) return;
+    const int nch = *n_chunks;
+    if ((int)blockIdx.x >= nch) return;
+    // the chunk of this launch position (longest first, see seg_meta_body)
+    const int w = chunks[blockIdx.x].w;
+    const int c = VSAOGM_IN_BOUNDS(w >= 0 && w < nch) ? w : (int)blockIdx.x;
     encode_chunk_x2_body<NP, NPOLY, ATOMIC, FUSED>(pts, chunks[c], c, blockIdx.y, nu, D,
                                                    nu_max_x, nu_max_y, poly_warps, pt, out, tail,
                                                    sp, s_bound, s_tail);
@@ -901,8 +940,12 @@ __global__ void __launch_bounds__(256) encode_batch_kernel(const __grid_constant
         }
         const BatchEncodeMap &M = tab.m[lo];
         const long long local = it - M.item_begin;
-        const int c = (int)(local / M.slices), slice = (int)(local % M.slices);
-        if (c < *M.n_chunks)
+        const int ci = (int)(local / M.slices), slice = (int)(local % M.slices);
+        const int nch = *M.n_chunks;
+        // the chunk of this position in the map's launch order (longest first)
+        const int w = ci < nch ? M.chunks[ci].w : 0;
+        const int c = VSAOGM_IN_BOUNDS(w >= 0 && w < nch) ? w : ci;
+        if (ci < nch)
             encode_chunk_x2_body<4, -1, false, true>(M.pts, M.chunks[c], c, slice, M.nu, M.D,
                                                      M.nu_max_x, M.nu_max_y, M.poly_warps,
                                                      M.pt, M.out, M.tail, sp, s_bound, s_tail);
