@@ -51,12 +51,12 @@ FP32_FMA_PER_SM_CLK = 128
 # patches make every chunk inside the map: phase 2 (mul, fma; the frequencies
 # come pre-scaled by 2 pi, once per chunk) + MUFU argument scaling 1 +
 # accumulate 2, no reduction (MUFU's own costs it less than 5e-6 rad there);
-# polynomial path: phase with reduction 5 + half-angle Taylor and complex
-# square 19 + accumulate 2.  Chunks beyond 4 turns (points outside the map, or
-# patches capped by the segment limit) reduce first: 9 lane-ops on the MUFU
-# path.
+# polynomial path: phase with reduction 5 + half-angle polynomials (five
+# coefficients each) and complex square 16 + accumulate 2.  Chunks beyond 4
+# turns (points outside the map, or patches capped by the segment limit)
+# reduce first: 9 lane-ops on the MUFU path.
 MUFU_PATH_FMA = 5
-POLY_PATH_FMA = 26
+POLY_PATH_FMA = 23
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 CLOCK_FIELDS = ("index,pci.bus_id,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -377,7 +377,7 @@ DATA = ("synthetic: seeded 100-scan lidar trajectory in a walled 40 m world with
 # DRAM traffic of one encode launch on this workload from an ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum = 25.38 MB + 114.57 MB), valid
 # only for the kernel source it was taken on (sha1 of csrc/encode.cu).
-ENCODE_TRAFFIC = {"sha1": "72a7b814af7f174cdd0f1656e84da3a8dce2d4cf", "bytes": 138323968}
+ENCODE_TRAFFIC = {"sha1": "7611bd8798b52d24e33e5c5e1703d6b8b64f67f0", "bytes": 138601472}
 
 
 def data_of(name: str, wl) -> str:

@@ -35,7 +35,7 @@ using namespace vsaogm_impl;
 namespace {
 
 struct Tuning {
-    int poly_warps = 8;       // warps (of 8) evaluating one frequency pair by polynomial,
+    int poly_warps = 9;       // polynomial pairs per CTA (warp w takes (w < p) + (w < p - 8)),
                               // for maps whose phases stay below 4 turns (2 fewer otherwise)
     int fine_min = 512;       // points per segment that warrant the fine bundling patches
     int items_per_cta = 8;    // encode work items per persistent CTA (sets the chunk size)
@@ -519,7 +519,7 @@ int vsaogm_batch_autotune(vsaogm_batch *b, const float *const *xy, const uint8_t
     Tuning best = b->tune;
     float best_ms = 1e30f;
     // encode shape first (decode fixed), then the decode slicing
-    const int pws[] = {6, 7, 8}, ipcs[] = {8, 16, 32};
+    const int pws[] = {7, 8, 9, 10}, ipcs[] = {8, 16, 32};
     for (int pw : pws)
         for (int ipc : ipcs) {
             if (rc) break;

@@ -648,10 +648,11 @@ __global__ void __launch_bounds__(256) encode_chunk_kernel(const float2 *__restr
 // 5'. The same encode + bundle with packed FP32 pairs (two frequencies per
 //     instruction) and part of the unit phasors evaluated on the FMA pipe.
 //     Of the NP frequency pairs a thread holds, NPOLY pairs use
-//     exp(i 2 pi f) = (exp(i pi f))^2 with exp(i pi f) from its Taylor series
-//     on |pi f| <= pi/2 (sin to x^11, cos to x^12: truncation below 6e-8),
-//     squared as a complex number; the other pairs use MUFU sin/cos.  The
-//     phase reduction is the one of encode_points, lane by lane.
+//     exp(i 2 pi f) = (exp(i pi f))^2 with exp(i pi f) from polynomials on
+//     |pi f| <= pi/2 (sin and cos, five coefficients each, fitted
+//     near-minimax by phasor_poly.py: errors 3.3e-9 and 4.7e-8, about 1.5e-7
+//     in float32), squared as a complex number; the other pairs use MUFU
+//     sin/cos.  The phase reduction is the one of encode_points, lane by lane.
 
 // TIER 0 (every |nu d| of the chunk below 4 turns): the MUFU lanes take
 // sin/cos of 2 pi t without reducing t (MUFU's own argument reduction costs it
@@ -668,17 +669,18 @@ __device__ __forceinline__ void encode_points_x2(const float2 *sp, int len,
     const f32x2 kM = pack2(12582912.0f, 12582912.0f);
     const f32x2 kTwoPi = pack2(6.28318530717958647692f, 6.28318530717958647692f);
     const f32x2 kPi = pack2(3.14159265358979323846f, 3.14159265358979323846f);
-    const f32x2 kOne = pack2(1.0f, 1.0f);
-    // Taylor coefficients: sin x = x sum (-1)^n x^2n / (2n+1)!, cos x = sum (-1)^n x^2n / (2n)!
-    const f32x2 s3 = pack2(-1.0f / 6.0f, -1.0f / 6.0f), s5 = pack2(1.0f / 120.0f, 1.0f / 120.0f);
-    const f32x2 s7 = pack2(-1.0f / 5040.0f, -1.0f / 5040.0f);
-    const f32x2 s9 = pack2(1.0f / 362880.0f, 1.0f / 362880.0f);
-    const f32x2 s11 = pack2(-1.0f / 39916800.0f, -1.0f / 39916800.0f);
-    const f32x2 c2 = pack2(-0.5f, -0.5f), c4 = pack2(1.0f / 24.0f, 1.0f / 24.0f);
-    const f32x2 c6 = pack2(-1.0f / 720.0f, -1.0f / 720.0f);
-    const f32x2 c8 = pack2(1.0f / 40320.0f, 1.0f / 40320.0f);
-    const f32x2 c10 = pack2(-1.0f / 3628800.0f, -1.0f / 3628800.0f);
-    const f32x2 c12 = pack2(1.0f / 479001600.0f, 1.0f / 479001600.0f);
+    // sin x ~ x (a0 + a1 x^2 + ... + a4 x^8), cos x ~ b0 + b1 x^2 + ... + b4 x^8
+    // on |x| <= pi/2 (the near-minimax fit of phasor_poly.py)
+    const f32x2 a0 = pack2(9.999999766e-01f, 9.999999766e-01f);
+    const f32x2 a1 = pack2(-1.666664763e-01f, -1.666664763e-01f);
+    const f32x2 a2 = pack2(8.332899816e-03f, 8.332899816e-03f);
+    const f32x2 a3 = pack2(-1.980089730e-04f, -1.980089730e-04f);
+    const f32x2 a4 = pack2(2.590487534e-06f, 2.590487534e-06f);
+    const f32x2 b0 = pack2(9.999999535e-01f, 9.999999535e-01f);
+    const f32x2 b1 = pack2(-4.999990535e-01f, -4.999990535e-01f);
+    const f32x2 b2 = pack2(4.166358468e-02f, 4.166358468e-02f);
+    const f32x2 b3 = pack2(-1.385370418e-03f, -1.385370418e-03f);
+    const f32x2 b4 = pack2(2.315392824e-05f, 2.315392824e-05f);
     // Tier 0's MUFU pairs take the phase in radians straight from frequencies
     // scaled by 2 pi once per chunk (one multiply per exponential fewer); the
     // polynomial pairs and the reducing tiers keep turns.
@@ -713,18 +715,15 @@ __device__ __forceinline__ void encode_points_x2(const float2 *sp, int len,
             f32x2 cr, si;
             if (j < NPOLY) {
                 f32x2 x = mul2(f, kPi), x2 = mul2(x, x);
-                f32x2 s = fma2(x2, s11, s9);
-                s = fma2(x2, s, s7);
-                s = fma2(x2, s, s5);
-                s = fma2(x2, s, s3);
-                s = fma2(x2, s, kOne);
+                f32x2 s = fma2(x2, a4, a3);
+                s = fma2(x2, s, a2);
+                s = fma2(x2, s, a1);
+                s = fma2(x2, s, a0);
                 s = mul2(s, x);
-                f32x2 c = fma2(x2, c12, c10);
-                c = fma2(x2, c, c8);
-                c = fma2(x2, c, c6);
-                c = fma2(x2, c, c4);
-                c = fma2(x2, c, c2);
-                c = fma2(x2, c, kOne);
+                f32x2 c = fma2(x2, b4, b3);
+                c = fma2(x2, c, b2);
+                c = fma2(x2, c, b1);
+                c = fma2(x2, c, b0);
                 cr = mul2(sub2(c, s), add2(c, s));  // cos 2x = (c - s)(c + s)
                 si = mul2(add2(c, c), s);           // sin 2x = 2 c s
             } else {
@@ -742,9 +741,10 @@ __device__ __forceinline__ void encode_points_x2(const float2 *sp, int len,
     }
 }
 
-// NPOLY < 0 selects the mixed form: warps below poly_warps use one polynomial
-// pair, the others none, so the polynomial share is poly_warps / (8 NP) of the
-// exponentials (warps of an SM share its MUFU and FMA pipes).
+// NPOLY < 0 selects the mixed form: warp w uses (w < poly_warps) + (w <
+// poly_warps - 8) polynomial pairs, the others none, so the polynomial share is
+// poly_warps / (8 NP) of the exponentials for poly_warps in 0 .. 16 (warps of an
+// SM share its MUFU and FMA pipes).
 // One (chunk, frequency slice) work item, executed by the whole CTA (256
 // threads; contains __syncthreads).  sp and s_bound are the CTA's shared
 // staging buffers; out receives the chunk's partial memory (or, with ATOMIC,
@@ -805,6 +805,11 @@ __device__ __forceinline__ void encode_chunk_x2_body(const float2 *__restrict__ 
         // the exact reduction leaves the FMA pipe no room for polynomial
         // exponentials: every warp takes the MUFU path
         encode_points_x2<NP, 0, 2>(sp, len, nx, ny, ac, as);
+    } else if ((int)(threadIdx.x >> 5) < poly_warps - 8) {
+        if (tier == 0)
+            encode_points_x2<NP, 2, 0>(sp, len, nx, ny, ac, as);
+        else
+            encode_points_x2<NP, 2, 1>(sp, len, nx, ny, ac, as);
     } else if ((int)(threadIdx.x >> 5) < poly_warps) {
         if (tier == 0)
             encode_points_x2<NP, 1, 0>(sp, len, nx, ny, ac, as);
@@ -894,7 +899,7 @@ __device__ __forceinline__ void encode_chunk_x2_body(const float2 *__restrict__ 
 }
 
 template <int NP, int NPOLY, bool ATOMIC, bool FUSED>
-__global__ void __launch_bounds__(256) encode_chunk_x2_kernel(const float2 *__restrict__ pts,
+__global__ void __launch_bounds__(256, 4) encode_chunk_x2_kernel(const float2 *__restrict__ pts,
                                                               const int4 *__restrict__ chunks,
                                                               const int *__restrict__ n_chunks,
                                                               const float *__restrict__ nu, int D,
@@ -1008,7 +1013,7 @@ __global__ void __launch_bounds__(256) reduce_partials_kernel(const float2 *__re
 // pipe to the FMA pipe that balanced the two pipes on GB300 (measured sweeps).
 // Chunks whose phases stay below 4 turns spend fewer FMA operations on the MUFU
 // path, so more exponentials go to the polynomial there.
-constexpr int kAutoPolyWarps4Near = 8;  // 4 pairs per thread, phases below 4 turns: 8/32
+constexpr int kAutoPolyWarps4Near = 9;  // 4 pairs per thread, phases below 4 turns: 9/32
 constexpr int kAutoPolyWarps4 = 6;      // 4 pairs per thread otherwise: 6/32
 constexpr int kAutoPolyWarps2 = 3;      // 2 pairs per thread: 3/16
 

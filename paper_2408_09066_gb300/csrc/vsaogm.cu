@@ -388,7 +388,7 @@ int vsaogm_create(const vsaogm_config *cfg, vsaogm_map **out)
         if (const char *v = getenv("VSAOGM_ENCODE_POLY"))
             m->encode_poly_pairs = std::max(0, std::min(3, atoi(v)));
         if (const char *v = getenv("VSAOGM_ENCODE_POLY_WARPS"))
-            m->encode_poly_warps = std::max(-1, std::min(8, atoi(v)));
+            m->encode_poly_warps = std::max(-1, std::min(16, atoi(v)));
         // failure test of the bounded waits (see vsaogm_status)
         m->debug_wait_ns = 0;
         m->mem_gen = 0;

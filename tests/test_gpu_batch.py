@@ -250,7 +250,7 @@ def test_autotune_keeps_parity():
     r = _Run(wls, V.DECODE_BF16X3)
     try:
         t = r.batch.autotune(r.xy, r.lab, r.heat, r.occ)
-        assert t["poly_warps"] in (6, 7, 8)
+        assert t["poly_warps"] in (7, 8, 9, 10)
         assert t["items_per_cta"] in (8, 16, 32)
         assert t["decode_waves"] in (1, 2, 4)
         r.batch.step(r.xy, r.lab, r.heat, r.occ, r.ogm)

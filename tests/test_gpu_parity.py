@@ -125,12 +125,13 @@ def test_single_point_phasors_anywhere(x, y):
 
 @pytest.mark.parametrize("packed,poly,poly_warps",
                          [(0, 0, 0), (1, 0, 0), (1, 1, 0), (1, 2, 0), (1, 3, 0), (1, 0, 3),
-                          (1, 0, 8), (1, 0, -1)])
+                          (1, 0, 8), (1, 0, 12), (1, 0, -1)])
 @pytest.mark.parametrize("D", [1000, 8192])
 def test_encode_kernel_variants(monkeypatch, packed, poly, poly_warps, D):
     """The scalar encode kernel and the f32x2 one with 0..3 frequency pairs per
-    thread on the FMA-pipe polynomial (or one pair in some warps only; -1 is
-    the automatic share) match the oracle, near and far points."""
+    thread on the FMA-pipe polynomial (or one pair in some warps only, two in
+    some with 12 of 32 pairs; -1 is the automatic share) match the oracle,
+    near and far points."""
     monkeypatch.setenv("VSAOGM_ENCODE_PACKED", str(packed))
     monkeypatch.setenv("VSAOGM_ENCODE_POLY", str(poly))
     monkeypatch.setenv("VSAOGM_ENCODE_POLY_WARPS", str(poly_warps))
