@@ -958,10 +958,45 @@ __global__ void __launch_bounds__(256) encode_batch_kernel(const __grid_constant
     }
 }
 
+// 6. omega[s][k] += the sum of the partial memories of memory s (the chunks
+//    c0 .. c1 - 1 of its `patches` segments, which are contiguous), for the
+//    kReduceFreqs frequencies k0 .. of one CTA, in a fixed order: warp w adds
+//    chunks c0 + w, c0 + w + 8, ... (lane l frequency k0 + l), then warp 0
+//    adds the eight warps' sums in warp order.  Spreading one memory's chunks
+//    over eight warps keeps the heaviest memory from setting the time alone.
+constexpr int kReduceFreqs = 32;
+__device__ __forceinline__ void chunk_sum(const float2 *__restrict__ partial, int c0, int c1,
+                                          int D, int k0, float2 *__restrict__ omega_row)
+{
+    __shared__ float2 part[8][kReduceFreqs];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, k = k0 + lane;
+    float sr = 0.f, si = 0.f;
+    if (k < D) {
+#pragma unroll 4
+        for (int c = c0 + warp; c < c1; c += 8) {
+            const float2 v = partial[(size_t)c * D + k];
+            sr += v.x;
+            si += v.y;
+        }
+    }
+    part[warp][lane] = make_float2(sr, si);
+    __syncthreads();
+    if (warp == 0 && k < D) {
+        float tr = 0.f, ti = 0.f;
+#pragma unroll
+        for (int w = 0; w < 8; ++w) {
+            tr += part[w][lane].x;
+            ti += part[w][lane].y;
+        }
+        const float2 o = omega_row[k];
+        omega_row[k] = make_float2(o.x + tr, o.y + ti);
+    }
+}
+
 // 6'. The fixed-order partial sums of many maps in one launch (maps whose
 //     memories hold many chunks each): blockIdx.x is a global memory (maps'
 //     memories numbered one after the other; beyond the 65535 limit of a
-//     grid's y extent).
+//     grid's y extent), blockIdx.y a range of kReduceFreqs frequencies.
 __global__ void __launch_bounds__(256) reduce_batch_kernel(const __grid_constant__ BatchReduceTable tab)
 {
     const int gs = blockIdx.x;
@@ -972,40 +1007,25 @@ __global__ void __launch_bounds__(256) reduce_batch_kernel(const __grid_constant
     }
     const BatchReduceMap &M = tab.m[lo];
     const int s = gs - M.seg_begin;  // memory of this map; its patches' chunks are contiguous
-    const int k = blockIdx.y * blockDim.x + threadIdx.x;
-    if (k >= M.D) return;
+    const int k0 = blockIdx.y * kReduceFreqs;
+    if (k0 >= M.D) return;  // the whole CTA: the map's D ends before this range
     const int c0 = M.cbeg[s * M.patches], c1 = M.cbeg[(s + 1) * M.patches];
     if (c0 == c1 || !VSAOGM_IN_BOUNDS(c0 >= 0 && c1 > c0)) return;
-    float sr = 0.f, si = 0.f;
-    for (int c = c0; c < c1; ++c) {
-        float2 v = M.partial[(size_t)c * M.D + k];
-        sr += v.x;
-        si += v.y;
-    }
-    float2 w = M.omega[(size_t)s * M.D + k];
-    M.omega[(size_t)s * M.D + k] = make_float2(w.x + sr, w.y + si);
+    chunk_sum(M.partial, c0, c1, M.D, k0, M.omega + (size_t)s * M.D);
 }
 
-// 6. omega[s][k] += sum of the partial memories of memory s (the chunks of its
-//    `patches` segments, which are contiguous), in chunk order.
+// 6. The same for one map: blockIdx.y is the memory, blockIdx.x a range of
+//    kReduceFreqs frequencies.
 __global__ void __launch_bounds__(256) reduce_partials_kernel(const float2 *__restrict__ partial,
                                                               const int *__restrict__ cbeg, int D,
                                                               int patches,
                                                               float2 *__restrict__ omega)
 {
     const int s = blockIdx.y;
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= D) return;
+    const int k0 = blockIdx.x * kReduceFreqs;
     const int c0 = cbeg[s * patches], c1 = cbeg[(s + 1) * patches];
     if (c0 == c1 || !VSAOGM_IN_BOUNDS(c0 >= 0 && c1 > c0)) return;
-    float sr = 0.f, si = 0.f;
-    for (int c = c0; c < c1; ++c) {
-        float2 v = partial[(size_t)c * D + k];
-        sr += v.x;
-        si += v.y;
-    }
-    float2 w = omega[(size_t)s * D + k];
-    omega[(size_t)s * D + k] = make_float2(w.x + sr, w.y + si);
+    chunk_sum(partial, c0, c1, D, k0, omega + (size_t)s * D);
 }
 
 // Warps per CTA (of 8) that evaluate one frequency pair by polynomial when the
@@ -1321,7 +1341,8 @@ void batch_reduce_entry(const vsaogm_map *m, const Scratch &ws, const PatchDev &
 
 int launch_reduce_batch(const BatchReduceTable &tab, int d_max, cudaStream_t st)
 {
-    reduce_batch_kernel<<<dim3(tab.total_segs, (d_max + 255) / 256), 256, 0, st>>>(tab);
+    reduce_batch_kernel<<<dim3(tab.total_segs, (d_max + kReduceFreqs - 1) / kReduceFreqs), 256, 0,
+                          st>>>(tab);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? VSAOGM_OK : cuda_error(e, "batch reduce");
 }
@@ -1403,7 +1424,7 @@ int encode_bundle(vsaogm_map *m, const float *xy_f, const uint8_t *lab, int64_t 
     }
     if (!atomic && !fused) {
         StageScope sc(m, VSAOGM_STAGE_REDUCE, st);
-        dim3 grid((D + 255) / 256, m->S);
+        dim3 grid((D + kReduceFreqs - 1) / kReduceFreqs, m->S);
         reduce_partials_kernel<<<grid, 256, 0, st>>>((const float2 *)m->ws.partial.ptr, cbeg, D,
                                                      pt.n, m->omega);
         if ((e = cudaGetLastError()) != cudaSuccess) return cuda_error(e, "encode: reduce");
