@@ -546,7 +546,7 @@ int vsaogm_batch_autotune(vsaogm_batch *b, const float *const *xy, const uint8_t
     }
     b->tune = best;
     // how dense a map's points must be for the fine bundling patches
-    const int fines[] = {16, 64, 128, 2048};
+    const int fines[] = {16, 64, 128, 256, 1024, 2048};
     for (int f : fines) {
         if (rc) break;
         b->tune.fine_min = f;

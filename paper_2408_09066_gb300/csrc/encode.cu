@@ -173,19 +173,32 @@ __device__ __forceinline__ void seg_scan_body(int *__restrict__ hist, int nb, in
     const bool col = s < S1;
     const int per = (nb + kScanWarps - 1) / kScanWarps;
     const int b0 = min(nb, warp * per), b1 = min(nb, b0 + per);
+    // both passes read eight rows ahead into registers, so that eight loads are
+    // in flight per thread (pass 2's stores would otherwise hold back each next load)
+    constexpr int kAhead = 8;
     int sum = 0;
     if (col)
-        for (int b = b0; b < b1; ++b) sum += hist[(size_t)b * S1 + s];
+        for (int b = b0; b < b1; b += kAhead) {
+            int v[kAhead];
+#pragma unroll
+            for (int j = 0; j < kAhead; ++j) v[j] = b + j < b1 ? hist[(size_t)(b + j) * S1 + s] : 0;
+#pragma unroll
+            for (int j = 0; j < kAhead; ++j) sum += v[j];
+        }
     wsum[warp][lane] = sum;
     __syncthreads();
     int carry = 0;
     for (int w = 0; w < warp; ++w) carry += wsum[w][lane];
     if (col) {
-        for (int b = b0; b < b1; ++b) {
-            const size_t i = (size_t)b * S1 + s;
-            const int v = hist[i];
-            hist[i] = carry;
-            carry += v;
+        for (int b = b0; b < b1; b += kAhead) {
+            int v[kAhead];
+#pragma unroll
+            for (int j = 0; j < kAhead; ++j) v[j] = b + j < b1 ? hist[(size_t)(b + j) * S1 + s] : 0;
+#pragma unroll
+            for (int j = 0; j < kAhead; ++j) {
+                if (b + j < b1) hist[(size_t)(b + j) * S1 + s] = carry;
+                carry += v[j];
+            }
         }
         if (warp == kScanWarps - 1) total[s] = carry;  // the last run ends at the column sum
     }
