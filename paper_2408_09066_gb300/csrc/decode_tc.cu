@@ -9,7 +9,7 @@
 // exp(i 2 pi nu_y[k] dy_j): the sum over k' is Re sum_k U A, i.e. Eq. loc-query
 // in its separable form.  The A operands depend on the memories and are
 // generated in shared memory every call (sin/cos after an exact phase
-// reduction for a thread's first row, a complex multiply by the map's 32-cell
+// reduction for a thread's first row, a complex multiply by the map's 2-cell
 // step phasor for the next ones, the product with the memories); the B operand
 // depends only on the frequencies and the geometry, so it is computed once per
 // map into an x-phasor table in HBM (already split, in the operand layout) and
@@ -72,7 +72,7 @@ constexpr int kMmaWarp = kWarps;       // ... one issues the MMAs ...
 constexpr int kLoadWarp = kWarps + 1;  // ... one stages each stage's inputs ...
 constexpr int kBLoadWarp = kWarps + 2; // ... and one copies the B operand by TMA
 constexpr int kThreads = kProducers + 96;
-constexpr int kStep = 32;          // cells between a thread's rows
+constexpr int kStep = 2;           // cells between a thread's consecutive rows
 constexpr int kMaxRowBlocks = 2;   // 128-row blocks per CTA
 constexpr int kMaxN = 256;         // MMA N of a one-row-block CTA (128 with two)
 constexpr int kATile = kM * kRowBytes;           // one A operand tile (8 KB)
@@ -225,6 +225,56 @@ __host__ __device__ constexpr uint32_t idesc_of(int N)
     return idesc_f16(kM, N, P == kPrecBF16);
 }
 
+// The MMA warp's stage loop for RB row blocks.  Every descriptor is a base
+// descriptor whose low word (the 14-bit start-address field, shared memory
+// below 256 KB, so never carrying into the rest) gets a compile-time offset
+// per buffer, K-step, row block, class and hi/lo tile added, so that an MMA
+// costs its issue and one 32-bit add instead of a chain of 64-bit arithmetic.
+template <int P, int RB>
+__device__ __forceinline__ void mma_stages(int n_stages, int lane, uint32_t tmem, uint32_t idesc,
+                                           uint64_t d0, int b_off, int b_slot, int b_lo,
+                                           uint64_t *full_bar, uint64_t *empty_bar,
+                                           uint64_t *b_full, uint64_t *b_empty,
+                                           volatile int *abort_v, int *abort_s, uint64_t wait_ns)
+{
+    constexpr int kAcc = kTmemCols / (2 * RB);            // columns per accumulator
+    constexpr uint32_t kABuf = a_buffer_bytes(RB) >> 4;   // buffer 1's offset
+    const uint32_t lo0 = (uint32_t)d0, hi0 = (uint32_t)(d0 >> 32);
+    const auto desc = [hi0](uint32_t lo) { return ((uint64_t)hi0 << 32) | lo; };
+    for (int s = 0; s < n_stages; ++s) {
+        const int buf = s & 1, bs = s % kBRing;
+        if (!*abort_v && !mbar_wait(&full_bar[buf], (uint32_t)(s >> 1) & 1u, wait_ns))
+            atomicExch(abort_s, 1);
+        if (!*abort_v && !mbar_wait(&b_full[bs], (uint32_t)(s / kBRing) & 1u, wait_ns))
+            atomicExch(abort_s, 1);
+        tc_fence_after_sync();
+        if (lane == 0) {
+            const uint32_t a0 = lo0 + (buf ? kABuf : 0u);
+            const uint32_t bh0 = lo0 + (uint32_t)((b_off + bs * b_slot) >> 4);
+            const uint32_t bl0 = bh0 + (uint32_t)(b_lo >> 4);
+            const uint32_t first = s > 0 ? 1u : 0u;  // the first stage's first K-step starts the sums
+#pragma unroll
+            for (int kk = 0; kk < kRowBytes / 32; ++kk) {
+#pragma unroll
+                for (int r = 0; r < RB; ++r) {
+#pragma unroll
+                    for (int c = 0; c < 2; ++c) {
+                        constexpr uint32_t kT = kATile >> 4;
+                        const uint32_t ah = a0 + (uint32_t)((r * 2 + c) * 2) * kT + 2u * kk;
+                        const uint32_t d = tmem + (uint32_t)((2 * r + c) * kAcc);
+                        mma<P>(d, desc(ah), desc(bh0 + 2u * kk), idesc, kk > 0 ? 1u : first);
+                        mma<P>(d, desc(ah), desc(bl0 + 2u * kk), idesc, 1u);
+                        mma<P>(d, desc(ah + kT), desc(bh0 + 2u * kk), idesc, 1u);
+                    }
+                }
+            }
+            mma_commit(&empty_bar[buf]);
+            mma_commit(&b_empty[bs]);
+        }
+        __syncwarp();
+    }
+}
+
 // One (block of cells, frequency slice) item, executed by the whole CTA: 16
 // producer warps generate the A operands, one warp stages each stage's inputs,
 // one copies the B operand by TMA and one issues the MMAs.  The block's columns
@@ -238,7 +288,7 @@ __host__ __device__ constexpr uint32_t idesc_of(int N)
 //
 // Hand-offs, all through mbarriers (no CTA-wide barrier inside the loop):
 //  * the loader warp copies stage s's inputs (the memories of the block's
-//    tiles, the frequencies and the 32-cell step phasors) into the aux area of
+//    tiles, the frequencies and the row-step phasors) into the aux area of
 //    buffer buf = s & 1 with per-thread async copies that land on
 //    aux_full[buf]; it refills buf for stage s + 2 once every producer warp
 //    has arrived on full_bar[buf] for stage s (they read the aux area before
@@ -259,10 +309,12 @@ __host__ __device__ constexpr uint32_t idesc_of(int N)
 //
 // Producer thread (warp w, lane l) owns word l mod 16 of every operand row it
 // writes (frequencies FPL (l mod 16) .. + FPL - 1 of the stage, FPL = 1 for
-// 16-bit operands, 2 for FP8), and the rows 2 w + l / 16 + 32 q: their 64-byte
-// swizzle phase ((row / 2) mod 4) is w mod 4 for every q.  Each thread
-// carries the two classes' operand values of a row as packed pairs,
-// (Re U_0, Re U_1) and (-Im U_0, -Im U_1), so one packed multiply-add
+// 16-bit operands, 2 for FP8), and the rows 8 rb w + l / 16 + 2 q, q < 4 rb:
+// a warp's rows are consecutive and lie in one row block, a thread's rows
+// cross into the next tile row at most once for tiles of 8 rb rows or more,
+// and one store instruction of the warp fills two adjacent 64-byte rows.
+// Each thread carries the two classes' operand values of a row as packed
+// pairs, (Re U_0, Re U_1) and (-Im U_0, -Im U_1), so one packed multiply-add
 // advances both classes.
 template <int P>
 __device__ __forceinline__ void decode_tc_body(
@@ -345,38 +397,12 @@ __device__ __forceinline__ void decode_tc_body(
         // start-address field.
         const uint32_t idesc = idesc_of<P>(N);
         const uint64_t d0 = desc_k_sw64(smem_addr(smem));
-        for (int s = 0; s < n_stages; ++s) {
-            const int buf = s & 1, bs = s % kBRing;
-            if (!*abort_v && !mbar_wait(&full_bar[buf], (uint32_t)(s >> 1) & 1u, wait_ns))
-                atomicExch(&abort_s, 1);
-            if (!*abort_v && !mbar_wait(&b_full[bs], (uint32_t)(s / kBRing) & 1u, wait_ns))
-                atomicExch(&abort_s, 1);
-            tc_fence_after_sync();
-            if (lane == 0) {
-                const uint64_t oa = d0 + (uint64_t)((buf * a_bytes) >> 4);
-                const uint64_t ob = d0 + (uint64_t)((b_off + bs * b_slot) >> 4);
-#pragma unroll
-                for (int kk = 0; kk < kRowBytes / 32; ++kk) {
-                    const uint64_t o = oa + (uint64_t)(kk * 2);  // 32 bytes of each row
-                    const uint64_t dbh = ob + (uint64_t)(kk * 2);
-                    const uint64_t dbl = dbh + (uint64_t)(b_lo >> 4);
-                    for (int r = 0; r < rb; ++r) {
-#pragma unroll
-                        for (int c = 0; c < 2; ++c) {
-                            const uint64_t dah = o + (uint64_t)((((r * 2 + c) * 2) * kATile) >> 4);
-                            const uint64_t dal = dah + (uint64_t)(kATile >> 4);
-                            const uint32_t d = tmem + (uint32_t)((2 * r + c) * acc_cols);
-                            mma<P>(d, dah, dbh, idesc, (s > 0 || kk > 0) ? 1u : 0u);
-                            mma<P>(d, dah, dbl, idesc, 1u);
-                            mma<P>(d, dal, dbh, idesc, 1u);
-                        }
-                    }
-                }
-                mma_commit(&empty_bar[buf]);
-                mma_commit(&b_empty[bs]);
-            }
-            __syncwarp();
-        }
+        if (rb == 1)
+            mma_stages<P, 1>(n_stages, lane, tmem, idesc, d0, b_off, b_slot, b_lo, full_bar,
+                             empty_bar, b_full, b_empty, abort_v, &abort_s, wait_ns);
+        else
+            mma_stages<P, 2>(n_stages, lane, tmem, idesc, d0, b_off, b_slot, b_lo, full_bar,
+                             empty_bar, b_full, b_empty, abort_v, &abort_s, wait_ns);
         // one more commit arrives when every MMA issued above has finished
         if (lane == 0) mma_commit(&done_bar);
         __syncwarp();
@@ -456,22 +482,32 @@ __device__ __forceinline__ void decode_tc_body(
     } else {
         // ------------------------------------------------------ producers
         const int wd = lane & (kWords - 1);  // word of the operand rows
-        const int r0 = 2 * warp + (lane >> 4);  // first row and first column of the thread
-        // rows r0 + 32 q of the block, q < 4 rb: row block q / 4, row r0 + 32 (q mod 4)
+        // the warp's rows: 8 rb consecutive ones from w0, all in row block
+        // w0 / 128; the thread's are r0 + 2 q, q < nq
+        const int w0 = 8 * rb * warp;
+        const int r0 = w0 + (lane >> 4);
+        const int nq = max(0, min(4 * rb, (nj - r0 + 1) / 2));  // rows inside the block
         float dy[2 * 4];
         int tl[2 * 4];  // tile row of each A row, relative to by0
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
             const int m = r0 + kStep * q;
-            const bool v = q < 4 * rb && m < nj;
+            const bool v = q < nq;
             dy[q] = v ? row_off[b.j0 + m] : 0.f;
             const int t = v ? row_tile[b.j0 + m] - by0 : 0;
             tl[q] = VSAOGM_IN_BOUNDS(t >= 0 && t < nt) ? t : 0;  // staged memories exist for [0, nt)
         }
-        // byte of the thread's word in its first row: 64-byte swizzle phase w mod 4
-        const uint32_t soff = (uint32_t)(r0 * kRowBytes +
-                                         ((((wd >> 2) ^ (warp & 3)) << 4) | ((wd & 3) << 2)));
-        constexpr int kQBytes = kStep * kRowBytes;  // 32 rows further on
+        // byte of the thread's word in its row r0 + 2 q: the 64-byte swizzle
+        // phase of that row, (row / 2) mod 4, is q mod 4 (w0 / 2 is a multiple of 4)
+        uint32_t soff[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            soff[j] = (uint32_t)((w0 / kM) * 4 * kATile + (r0 & (kM - 1)) * kRowBytes +
+                                 ((((wd >> 2) ^ j) << 4) | ((wd & 3) << 2)));
+        constexpr int kQBytes = kStep * kRowBytes;  // the thread's next row
+        // a warp whose rows all lie past the block writes nothing: those A
+        // rows only reach accumulator rows that are never written out
+        const bool gen = w0 < nj;
         uint32_t phase_bits = 0u;  // bit b: parity to wait for on empty_bar[b]
 
         for (int s = 0; s < n_stages; ++s) {
@@ -484,6 +520,12 @@ __device__ __forceinline__ void decode_tc_body(
             if (!*abort_v && !mbar_wait(&aux_full[buf], (uint32_t)(s >> 1) & 1u, wait_ns))
                 atomicExch(&abort_s, 1);
             uint8_t *st = smem + buf * a_bytes;
+            if (!gen) {
+                fence_async_shared();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&full_bar[buf]);
+                continue;
+            }
             const float2 *sw = reinterpret_cast<const float2 *>(smem + aux_off + buf * aux_bytes(P));
             const float2 *sf = sw + max_block_tiles(P) * 2 * KS;
             float nuy[FPL];
@@ -502,8 +544,8 @@ __device__ __forceinline__ void decode_tc_body(
             // A operands: (Re U_psi, -Im U_psi) with U_psi = conj(w_hat_psi) x
             // the y phasor, i.e. V_psi = conj(U_psi) = w_hat_psi x conj(phasor),
             // held for both classes as packed pairs X = (Re V_0, Re V_1), Y =
-            // (Im V_0, Im V_1).  Rows step by 32 cells: V times conj(exp(i 2 pi
-            // nu_y 32 res)), except where a row enters the next tile: there the
+            // (Im V_0, Im V_1).  Rows step by 2 cells: V times conj(exp(i 2 pi
+            // nu_y 2 res)), except where a row enters the next tile: there the
             // phasor and the memories are reloaded.
             {
                 f32x2 X[FPL], Y[FPL], R2[FPL], I2[FPL], NI2[FPL];
@@ -528,7 +570,7 @@ __device__ __forceinline__ void decode_tc_body(
                 start_row(0);
 #pragma unroll
                 for (int q = 0; q < 8; ++q) {
-                    if (q >= 4 * rb) break;
+                    if (q >= nq) break;
                     if (q > 0) {
                         if (tl[q] != tl[q - 1]) {
                             start_row(q);
@@ -542,8 +584,8 @@ __device__ __forceinline__ void decode_tc_body(
                             }
                         }
                     }
-                    // tiles [row block q / 4][class][hi, lo]
-                    uint8_t *ra = st + (q >> 2) * 4 * kATile + (q & 3) * kQBytes + soff;
+                    // tiles [row block w0 / 128][class][hi, lo]
+                    uint8_t *ra = st + q * kQBytes + soff[q & 3];
                     uint32_t h0, l0, h1, l1;
                     if (FPL == 1) {
                         split_classes<P>(X[0], Y[0], h0, l0, h1, l1);
@@ -641,7 +683,7 @@ __global__ void __launch_bounds__(kThreads, 1) decode_tc_batch_kernel(
 }
 
 // rot[k] = exp(i 2 pi nu[k] step) for the x frequencies, then the y ones: the
-// phasor of one step of a thread's columns / rows (16 cells).  The phase is
+// phasor of one step between a producer thread's rows (kStep cells).  The phase is
 // reduced exactly and sin / cos taken of the reduced turn (sincospi).
 __global__ void __launch_bounds__(256) tc_rot_kernel(const float *__restrict__ nu, int n,
                                                      float step, float2 *__restrict__ rot)

@@ -183,7 +183,7 @@ struct BatchReduceTable {
 struct BatchDecodeMap {
     const float2 *omega;
     const float *inv_norm, *nu, *col_off, *row_off;
-    const float2 *rot;      // [2][D]: x then y phasor of a 32-cell step
+    const float2 *rot;      // [2][D]: x then y phasor of a producer row step
     const int *row_tile;    // tile row of each cell row
     float *partial;         // [slices][2][H][W]
     int *status;
@@ -282,7 +282,7 @@ struct vsaogm_map {
     int *col_tile, *row_tile;    // [W], [H]
     float *col_off, *row_off;    // [W], [H]
     unsigned *enc_cnt;           // [S][ceil(D / 512)]: the encode's finished-chunk counters
-    float2 *tc_rot;              // tensor-core decode: [2][D] phasors of a 32-cell step
+    float2 *tc_rot;              // tensor-core decode: [2][D] phasors of a producer row step
     uint32_t *tc_xtab;           // tensor-core decode: x-phasor table, hi and lo planes [W][Dp]
     uint8_t *tc_xtmap;           // tensor-core decode: the table's two TMA tensor maps (device)
     // failure test (VSAOGM_DEBUG_WAIT_NS at creation; 0: off): the tensor-core
